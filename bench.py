@@ -1,0 +1,500 @@
+#!/usr/bin/env python3
+"""Benchmark of the sparse grid characteristics hot path on GB300.
+
+One step = one pass of the whole path on the level-4 6-D attitude workload:
+  Step I    sparse grid, d = 6, level 4 (1457 CGL nodes) on [-pi/4, pi/4]^6
+  Step II   one characteristic BVP per node, T in {10, 20, 40} with N = 64 / 128
+            / 256 Lobatto intervals, Newton to |F|_inf <= 1e-8 (mixed precision:
+            FP32 Jacobian / elimination / direction, FP64 residual and update)
+  Step III  surpluses of u*(x) at the nodes
+  on-line   u*(x) at 1e6 query states (half uniform, half N(0, 0.2^2) clipped)
+The headline value is converged BVP solves per second of whole-step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
+
+Multi-GPU (torchrun): every rank runs its own independent instance (weak
+scaling, no collective on the data path); value = all ranks' solves / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "converged BVP solves/s at 1e-8 residual"
+UNIT = "solves/s"
+LEVEL, D = 4, 6
+N_QUERIES = 1_000_000
+TOL = 1e-8
+WORKLOAD = ("attitude6d_L4_1457nodes_T{10,20,40}_N{64,128,256}_mixedprec"
+            "+surplus+1e6queries_fp64eval")
+
+# Derived ALU peaks (unit counts x maximum SM clock, 2070 MHz, 152 SMs):
+#   FP32: 128 FMA lanes/SM x 2 flops = 80.6 TFLOP/s
+#   FP64: the nominal 1.25 TFLOP/s of GB300 (about 2 FMA/clk/SM)
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+PEAK_FP64_TFLOPS = 1.25
+
+
+# ------------------------------------------------------------------ work model
+def flops_condense_interval() -> float:
+    """Per interval: build of the 36 x 49 system (1728 scaled Jacobian entries,
+    36 residual rows of 4 FMA + 2) and Gaussian elimination of 24 columns with
+    multipliers: sum_k (35-k) + 2 (35-k)(48-k), plus 24 reciprocals."""
+    ge = sum((35 - k) + 2 * (35 - k) * (48 - k) for k in range(24)) + 24
+    return 1728 + 36 * 10 + ge
+
+
+def flops_abd_interval() -> float:
+    """Per interval: elimination of 12 columns of the 18 x 25 panel, plus the
+    back substitution (12 x 12 product and triangular solve)."""
+    ge = sum((17 - k) + 2 * (17 - k) * (24 - k) for k in range(12)) + 12
+    return ge + 2 * 144 + 144 + 12
+
+
+def flops_recover_interval() -> float:
+    """Per interval: 24 x 24 product and 24 x 24 triangular solve."""
+    return 2 * 576 + 576 + 24
+
+
+def bytes_point(tsize: int) -> float:
+    """Per collocation point: read y (12 f64), write F (12 f64) and J (144 x tsize)."""
+    return 12 * 8 + 12 * 8 + 144 * tsize
+
+
+def flops_eval_query(M: int, k: int) -> float:
+    """Per query: the contraction (2 k flops per node) and one product per node."""
+    return M * (2 * k + 1)
+
+
+# ------------------------------------------------------------------ helpers
+def _rank_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ oracle worker
+def cpu_worker(n_nodes: int, seed: int) -> dict:
+    """Times the oracle on a bounded sample of the workload: n_nodes BVP solves
+    drawn from the level-4 nodes with their horizons (single thread)."""
+    from oracle import bvp as obvp
+    from oracle import grid as ogrid
+    from oracle import problems as oprob
+    lo, hi = synth.box(D)
+    g = ogrid.Grid(D, LEVEL, lo, hi)
+    T, N = synth.mixed_horizons(g.M, seed=2)
+    idx = np.random.default_rng(seed).choice(g.M, n_nodes, replace=False)
+    pr = oprob.make(synth.attitude_params(0))
+    t0 = time.perf_counter()
+    conv = 0
+    for i in idx:
+        s = obvp.solve(pr, g.x[i], float(T[i]), int(N[i]), tol=TOL, polish=False)
+        conv += int(s.status == obvp.CONVERGED)
+    dt = time.perf_counter() - t0
+    return {"converged": conv, "seconds": dt, "nodes": int(n_nodes), "N": [int(N[i]) for i in idx]}
+
+
+def run_cpu_baseline(n_nodes: int, seed: int = 123) -> dict:
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    for v in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(v, None)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(n_nodes), str(seed)],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------ reference arm
+def reference_arm(args):
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return 0
+    per_step = 4
+    times, conv = [], 0
+    for s in range(args.warmup + args.steps):
+        r = run_cpu_baseline(per_step, seed=1000 + s)
+        if s >= args.warmup:
+            times.append(r["seconds"])
+            conv += r["converged"]
+    total = sum(times)
+    value = conv / total
+    sample = (f"{per_step} oracle BVP solves per step (level-4 nodes with their T/N draws), "
+              f"single thread, tol 1e-8")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def gpu_arm(args):
+    import torch
+    rank, world, local = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1507_04769_gb300 import sg
+
+    prec = sg.PREC_MIXED if args.precision == "mixed" else sg.PREC_FP64
+    lo, hi = synth.box(D)
+    params = synth.attitude_params(0)
+    prob = sg.problem_from(params)
+    g0 = sg.Grid(D, LEVEL, lo, hi)
+    M = g0.M
+    T_h, N_h = synth.mixed_horizons(M, seed=2)
+    xq_h = synth.mixed_queries(N_QUERIES, lo, hi, seed=1 + rank)
+    T_d = torch.as_tensor(T_h, device=dev)
+    N_d = torch.as_tensor(N_h, dtype=torch.int32, device=dev)
+    xq_d = torch.as_tensor(xq_h, device=dev)
+    n_max = int(N_h.max())
+    ws = torch.empty(sg.workspace_bytes(M, n_max, prec), dtype=torch.uint8, device=dev)
+    u_out = torch.empty((N_QUERIES, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        if events:
+            events[0].record(stream)
+        g = sg.Grid(D, LEVEL, lo, hi)
+        if events:
+            events[1].record(stream)
+        res = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=prec, workspace=ws, n_max=n_max)
+        if events:
+            events[2].record(stream)
+        S = sg.Surplus(g, res["u0"])
+        if events:
+            events[3].record(stream)
+        sg.eval_feedback(S, xq_d, out=u_out)
+        if events:
+            events[4].record(stream)
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    status = res["status"].cpu().numpy()
+    iters = res["iters"].cpu().numpy().astype(np.int64)
+    conv_per_step = int(np.sum(status == sg.CONVERGED))
+
+    # ---------------- timed region
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = sg.LIB.sg_kernel_launches()
+    sg.LIB.sg_timing_enable(1)
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            res = step(ev[s])
+            flush.zero_()
+        torch.cuda.synchronize()
+    sg.LIB.sg_timing_enable(0)
+    launches = sg.LIB.sg_kernel_launches() - launches0
+    kt = collect_kernel_times(sg)
+    step_ms = [ev[s][0].elapsed_time(ev[s][4]) for s in range(args.steps)]
+    phase_ms = {name: sum(ev[s][i].elapsed_time(ev[s][i + 1]) for s in range(args.steps)) / args.steps
+                for i, name in enumerate(["grid", "solve", "surplus", "eval"])}
+    t_local = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    total_solves = conv_per_step * args.steps * world
+    value = total_solves / t_max
+
+    # ---------------- end to end through the public API with host buffers
+    T_pin = torch.as_tensor(T_h).pin_memory()
+    N_pin = torch.as_tensor(N_h, dtype=torch.int32).pin_memory()
+    xq_pin = torch.as_tensor(xq_h).pin_memory()
+    u_pin = torch.empty((N_QUERIES, 3), dtype=torch.float64).pin_memory()
+    node_pin = {k: torch.empty((M,) + shp, dtype=dt).pin_memory()
+                for k, shp, dt in (("lambda0", (6,), torch.float64), ("u0", (3,), torch.float64),
+                                   ("V", (), torch.float64), ("status", (), torch.int32))}
+
+    def e2e_step():
+        T_d.copy_(T_pin, non_blocking=True)
+        N_d.copy_(N_pin, non_blocking=True)
+        xq_d.copy_(xq_pin, non_blocking=True)
+        r = step()
+        u_pin.copy_(u_out, non_blocking=True)
+        for k in node_pin:
+            node_pin[k].copy_(r[k], non_blocking=True)
+        return r
+
+    for _ in range(2):
+        e2e_step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for s in range(args.steps):
+        e2e_ev[s][0].record(stream)
+        e2e_step()
+        e2e_ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        flush.zero_()
+    torch.cuda.synchronize()
+    e2e_t = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
+    h2d = T_pin.numel() * 8 + N_pin.numel() * 4 + xq_pin.numel() * 8
+    d2h = u_pin.numel() * 8 + sum(t.numel() * t.element_size() for t in node_pin.values())
+    e2e_value = conv_per_step * args.steps * world / e2e_t  # max over ranks not needed per-rank equal
+
+    # ---------------- FP64 form on the same GPU (speedup of the mixed form)
+    fp64 = None
+    if prec == sg.PREC_MIXED and not args.skip_fp64:
+        ws64 = torch.empty(sg.workspace_bytes(M, n_max, sg.PREC_FP64), dtype=torch.uint8, device=dev)
+        g = sg.Grid(D, LEVEL, lo, hi)
+        r64 = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=sg.PREC_FP64, workspace=ws64,
+                            n_max=n_max)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            r64 = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=sg.PREC_FP64, workspace=ws64,
+                                n_max=n_max)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b) / 1e3 / args.steps
+        c64 = int((r64["status"] == sg.CONVERGED).sum().item())
+        mixed_solve_s = phase_ms["solve"] / 1e3
+        dl = (r64["lambda0"] - res["lambda0"]).abs().max().item() / r64["lambda0"].abs().max().item()
+        fp64 = {"solves_per_s": c64 / t64, "solve_ms": 1e3 * t64,
+                "mixed_solve_ms": 1e3 * mixed_solve_s, "speedup_mixed_over_fp64": t64 / mixed_solve_s,
+                "max_rel_diff_lambda0_mixed_vs_fp64": dl,
+                "newton_iters_hist_fp64": np.bincount(r64["iters"].cpu().numpy()).tolist()}
+        del ws64
+
+    # ---------------- roofline of the dominant kernel
+    roof, kernels = roofline(kt, iters, N_h, M, prec)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return 0
+
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        nodes = args.cpu_nodes
+        r = run_cpu_baseline(nodes)
+        cpu = {"value": r["converged"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nodes} level-4 nodes (N = {sorted(r['N'])}) solved by the oracle to "
+                         f"|F|_inf <= 1e-8, single thread, {r['seconds']:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32" if prec == sg.PREC_MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": M, "grid_level": LEVEL, "d": D,
+                   "horizons": "T in {10,20,40}, N = 6.4 T", "queries": N_QUERIES, "tol": TOL,
+                   "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"{world} independent instance(s), no collective"},
+        "feedback_evals_per_s": N_QUERIES / (phase_ms["eval"] / 1e3),
+        "breakdown_ms": phase_ms,
+        "newton_iters_hist": np.bincount(iters).tolist(),
+        "converged_per_step": conv_per_step,
+        "roofline": roof,
+        "kernels": kernels,
+        "fp64_form": fp64,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_t / args.steps},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def collect_kernel_times(sg):
+    import ctypes as C
+    n_max, name_len = 64, 64
+    names = C.create_string_buffer(n_max * name_len)
+    ms = (C.c_double * n_max)()
+    cnt = (C.c_int64 * n_max)()
+    nk = C.c_int()
+    sg.LIB.sg_timing_collect.argtypes = [C.c_int, C.c_char_p, C.c_int, C.c_void_p, C.c_void_p,
+                                         C.POINTER(C.c_int)]
+    rc = sg.LIB.sg_timing_collect(n_max, names, name_len, C.cast(ms, C.c_void_p), C.cast(cnt, C.c_void_p),
+                                  C.byref(nk))
+    if rc != 0:
+        raise RuntimeError(sg.LIB.sg_last_error().decode())
+    out = {}
+    raw = names.raw
+    for i in range(nk.value):
+        nm = raw[i * name_len:(i + 1) * name_len].split(b"\0", 1)[0].decode()
+        out[nm] = (ms[i], cnt[i])
+    return out
+
+
+def roofline(kt, iters, N_h, M, prec):
+    """Per-kernel algorithmic work / measured time; the dominant kernel's entry
+    is the roofline object."""
+    suffix = "_fp32" if prec == 1 else "_fp64"
+    tsize = 4 if prec == 1 else 8
+    peak_lin = PEAK_FP32_TFLOPS if prec == 1 else PEAK_FP64_TFLOPS
+    int_units = float(np.sum(iters * N_h))           # interval-iterations per solve
+    pt_units = float(np.sum(iters * (3 * N_h + 1)))  # point-iterations per solve
+    steps_timed = None
+    models = {
+        "k_condense" + suffix: ("alu", flops_condense_interval() * int_units, peak_lin, "TFLOP/s"),
+        "k_abd" + suffix: ("alu", flops_abd_interval() * int_units, peak_lin, "TFLOP/s"),
+        "k_recover" + suffix: ("alu", flops_recover_interval() * int_units, peak_lin, "TFLOP/s"),
+        "k_point" + suffix: ("hbm", bytes_point(tsize) * pt_units, None, "GB/s"),
+        "k_eval_fp64": ("alu", flops_eval_query(M, 3) * N_QUERIES, PEAK_FP64_TFLOPS, "TFLOP/s"),
+    }
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak = 6785.9
+    if os.path.exists(peaks_path):
+        try:
+            hbm_peak = float(json.load(open(peaks_path))["hbm_gbs"])
+        except (KeyError, ValueError):
+            pass
+    kernels = {}
+    total_ms = sum(v[0] for v in kt.values()) or 1.0
+    for name, (ms, n) in sorted(kt.items(), key=lambda kv: -kv[1][0]):
+        entry = {"total_ms": ms, "launches": int(n), "share": ms / total_ms}
+        if name in models and n > 0:
+            bound, work_per_solve, peak, unit = models[name]
+            # every timed step repeats the same solve (work per step = work_per_solve)
+            if name == "k_eval_fp64":
+                work_total = work_per_solve * n
+            else:
+                steps_timed = steps_timed or max(1, round(kt.get("k_outputs", (0, 1))[1]))
+                work_total = work_per_solve * steps_timed
+            sec = ms / 1e3
+            if unit == "TFLOP/s":
+                achieved = work_total / sec / 1e12
+            else:
+                achieved = work_total / sec / 1e9
+                peak = hbm_peak
+            entry.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                          "frac": achieved / peak})
+        kernels[name] = entry
+    dom = next((k for k in kernels if "achieved" in kernels[k]), None)
+    roof = None
+    if dom:
+        e = kernels[dom]
+        roof = {"kernel": dom, "bound": e["bound"], "achieved": e["achieved"], "peak": e["peak"],
+                "unit": e["unit"], "frac": e["frac"], "traffic": None,
+                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if e["unit"] == "TFLOP/s"
+                                and e["peak"] == PEAK_FP32_TFLOPS else
+                                "nominal GB300 FP64 1.25 TFLOP/s" if e["unit"] == "TFLOP/s" else
+                                "MEASURED_PEAKS.json hbm_gbs"),
+                "share_of_gpu_time": e["share"]}
+    return roof, kernels
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--cpu-nodes", type=int, default=40)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--cpu-worker", nargs=2, type=int, default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.cpu_worker is not None:
+        print(json.dumps(cpu_worker(*args.cpu_worker)))
+        return 0
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

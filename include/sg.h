@@ -1,0 +1,215 @@
+/*
+ * sg.h - C ABI of the GB300 sparse grid characteristics library.
+ *
+ * The method (Kang & Wilcox, "Sparse grid characteristics method for optimal
+ * feedback control and HJB equations"):
+ *   Step I   build a Smolyak sparse grid on nested Chebyshev-Gauss-Lobatto
+ *            (CGL) sets                                  (Section 3.2, Eq. CGL)
+ *   Step II  at every node solve the two-point BVP of Pontryagin's
+ *            characteristics                             (Section 3.1, Eq. hamchar)
+ *   Step III form hierarchical surpluses                 (Section 3.3, Eq. interpo)
+ *   on-line  evaluate the interpolant of the feedback u* (Section 3.3, Eq. optuv)
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named d_* are DEVICE pointers on the current CUDA device;
+ *     pointers named h_* or without prefix are HOST pointers.  All arrays are
+ *     dense, row-major, C order, with the row (node or query) index slowest.
+ *   - Device buffers passed in are owned by the caller and must stay alive until
+ *     the work queued on `stream` has finished.  Handles (sg_grid, sg_surplus)
+ *     own their own device memory and are freed with the matching *_free call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are asynchronous on that stream unless stated otherwise.
+ *   - Return value: SG_OK, or an error code; sg_last_error() then returns a
+ *     thread-local message.  No C++ exception crosses this interface.  Per-node
+ *     convergence failures are NOT errors: they are reported in d_status.
+ *   - Requires a device of compute capability 10.3 (sm_103a).
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+enum {
+  SG_OK = 0,
+  SG_EINVAL = 1,        /* bad argument (size, pointer, enum value)        */
+  SG_ENOMEM = 2,        /* a handle could not allocate device memory       */
+  SG_ECUDA = 3,         /* a CUDA call failed; message has the CUDA error  */
+  SG_EUNSUPPORTED = 4   /* valid but not supported (e.g. dimension > 8)    */
+};
+
+enum { SG_PROBLEM_ATTITUDE = 0, SG_PROBLEM_LQ = 1 };
+
+/* Precision of the Newton solve.
+ * FP64:  everything in FP64.
+ * MIXED: Jacobian, stage condensation, block elimination and the search
+ *        direction in FP32; collocation residual, line search, update,
+ *        terminal costate condition and outputs in FP64.  Newton then converges
+ *        to the same FP64 root (the FP32 direction only slows the final rate). */
+enum { SG_PREC_FP64 = 0, SG_PREC_MIXED = 1 };
+
+/* Per-node Newton status written to d_status.  SG_BADINPUT: N outside
+ * 1..n_max_intervals, T not positive and finite, or a non-finite x0 (that node
+ * is skipped and its outputs are NaN). */
+enum { SG_CONVERGED = 0, SG_MAXITER = 1, SG_NONFINITE = 2, SG_SINGULAR = 3, SG_BADINPUT = 4 };
+
+/* Interpolant evaluation mode. */
+enum { SG_EVAL_FP64 = 0, SG_EVAL_TF32X3 = 1 };
+
+/* ---------------------------------------------------------------- problem
+ * The optimal control problem of Section 2 for the two families built in:
+ *
+ * SG_PROBLEM_ATTITUDE (Section 5, Eq. sat_model): x = (phi, theta, psi, w1, w2, w3),
+ *   v' = E(v) w,  J w' = S(w) R(v) hmom + B u   with 3-2-1 Euler angles,
+ *   E the Euler-rate matrix, R = Rx(phi) Ry(theta) Rz(psi) (inertial -> body),
+ *   S(w) a = a x w.  Running cost 0.5 (wv |v|^2 + ww |w|^2 + r |u|^2),
+ *   terminal cost 0.5 (tv |v(T)|^2 + tw |w(T)|^2).
+ * SG_PROBLEM_LQ: x' = A x + Blq u, running cost 0.5 (x'Qx + u'Ru),
+ *   terminal 0.5 x'QT x; R must be symmetric positive definite.
+ * Unused fields of the other family are ignored. */
+typedef struct sg_problem {
+  int32_t kind;
+  int32_t _pad;
+  /* attitude */
+  double J[3];       /* diagonal inertia                       */
+  double hmom[3];    /* total angular momentum, inertial frame */
+  double B[9];       /* 3x3 control matrix, row-major          */
+  double wv, ww, r, tv, tw;
+  /* LQ */
+  double A[36];      /* 6x6 */
+  double Blq[18];    /* 6x3 */
+  double Q[36];      /* 6x6 */
+  double R[9];       /* 3x3 */
+  double QT[36];     /* 6x6 */
+} sg_problem;
+
+typedef struct sg_solve_opts {
+  double tol;          /* converged when |F|_inf <= tol (stage rows in state units,
+                          boundary rows raw); default 1e-8                      */
+  int32_t max_iter;    /* Newton iteration cap per node; default 50             */
+  int32_t precision;   /* SG_PREC_FP64 or SG_PREC_MIXED                          */
+  int32_t damping;     /* 1: Armijo backtracking alpha = 1, 1/2, ..., 2^-10;
+                          0: full Newton steps                                  */
+  int32_t _pad;
+} sg_solve_opts;
+
+/* ---------------------------------------------------------------- errors */
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* sg_last_error(void);
+
+/* ---------------------------------------------------------------- Step I
+ * sg_build_grid - Smolyak sparse grid G^q = union_{|i| <= q} dX^{i_1} x ... x dX^{i_d}
+ * with q = d + level, on the nested CGL sets of Eq. CGL (Section 3.2), mapped
+ * affinely from [0,1]^d to the box [h_lo, h_hi].
+ *   d      1..8 dimensions;   level 0..10 (level = q - d)
+ *   h_lo, h_hi  host arrays of d doubles, h_lo[k] < h_hi[k]
+ *   out    receives a new handle (owned by the caller, free with sg_grid_free)
+ * Nodes are ordered by |i|, then i lexicographically, then the 1-D indices
+ * lexicographically; node 0 is the box centre.  Increment sets: dX^1 = {1/2},
+ * dX^2 = {0, 1}, dX^i = the even-indexed points of X^i for i >= 3.
+ * Synchronous (the coordinates are computed by a kernel on the default stream
+ * and the call waits for it).  Errors: SG_EINVAL, SG_EUNSUPPORTED, SG_ENOMEM, SG_ECUDA. */
+typedef struct sg_grid sg_grid;
+int sg_build_grid(int d, int level, const double* h_lo, const double* h_hi, sg_grid** out);
+
+/* Borrowed views of a grid.  d_coords: M x d doubles (box coordinates);
+ * d_levels: M x d int8 levels i_k; d_index: M x d int16 index of the node's
+ * coordinate in X^{i_k} (0-based).  Any output pointer may be NULL. */
+int sg_grid_info(const sg_grid* g, int64_t* n_nodes, int* d, int* level,
+                 const double** d_coords, const int8_t** d_levels, const int16_t** d_index);
+void sg_grid_free(sg_grid* g);
+
+/* ---------------------------------------------------------------- Step II
+ * sg_solve_bvps - solve the characteristic BVP of Eq. hamchar at n initial states,
+ *   x' = H_lambda', lambda' = -H_x', x(0) = x0, lambda(T) = grad h(x(T)),
+ * by four-stage Lobatto IIIA collocation on N equal intervals (Section 3.1)
+ * and damped Newton; outputs per Eq. optuv.
+ *
+ *   prob            host pointer to the problem
+ *   d_x0            n x 6 initial states
+ *   n               number of BVPs (>= 0; 0 is a no-op)
+ *   d_T             n horizons (> 0)
+ *   d_N             n interval counts, 1 <= N[i] <= n_max_intervals
+ *   n_max_intervals the maximum of d_N (host value; sizes the workspace slots)
+ *   opts            host pointer (NULL = defaults)
+ *   d_work, work_bytes  caller-owned device workspace of at least
+ *                   sg_solve_workspace_bytes(n, n_max_intervals, precision) bytes,
+ *                   256-byte aligned; its contents on entry are ignored
+ *   outputs         d_lambda0 n x 6, d_u0 n x 3, d_V n, d_status n (SG_CONVERGED ...),
+ *                   d_iters n (Newton iterations used); d_Y may be NULL or
+ *                   n x (3*n_max_intervals+1) x 12 to receive the collocation
+ *                   solution (point p of node i at row p; unused rows untouched)
+ * The initial guess is lambda = 0 (zero control) with x held at x0.
+ * The call returns when every node has converged or hit max_iter (the host
+ * reads one counter per iteration), so it synchronises `stream`.
+ * Errors: SG_EINVAL (sizes, workspace too small, misaligned), SG_ECUDA. */
+size_t sg_solve_workspace_bytes(int64_t n, int n_max_intervals, int precision);
+int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t n,
+                  const double* d_T, const int32_t* d_N, int n_max_intervals,
+                  const sg_solve_opts* opts, void* d_work, size_t work_bytes,
+                  double* d_lambda0, double* d_u0, double* d_V,
+                  int32_t* d_status, int32_t* d_iters, double* d_Y, void* stream);
+
+/* ---------------------------------------------------------------- Step III
+ * sg_build_surpluses - hierarchical surpluses of values at the grid nodes,
+ * Eq. interpo: level by level, w_n = f(x_n) - I^{|i_n|-1}(f)(x_n).
+ *   d_values  M x k doubles (row n = node n of the grid), 1 <= k <= 16
+ *   out       new handle owning W (M x k FP64) and the evaluation tables;
+ *             it keeps no reference to d_values or to g after the call returns
+ * Synchronises `stream` before returning.  Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA. */
+typedef struct sg_surplus sg_surplus;
+int sg_build_surpluses(const sg_grid* g, const double* d_values, int k,
+                       sg_surplus** out, void* stream);
+/* Borrowed view of the surpluses: d_W is M x k doubles. */
+int sg_surplus_info(const sg_surplus* s, int64_t* n_nodes, int* k, const double** d_W);
+void sg_surplus_free(sg_surplus* s);
+
+/* ---------------------------------------------------------------- on-line
+ * sg_eval_feedback - evaluate the sparse-grid interpolant (Eq. interpo, the
+ * surplus form) at Q query states.  With values u*(x_n) at the nodes this is
+ * the on-line feedback of Section 3.3; with lambda(0) it is the costate.
+ *   d_xq   Q x d query states (box coordinates; points outside the box are
+ *          evaluated by the same polynomial)
+ *   mode   SG_EVAL_FP64, or SG_EVAL_TF32X3 (contraction on tensor cores with
+ *          split-TF32 operands; error bound stated with the kernel)
+ *   d_out  Q x k doubles
+ * Asynchronous on `stream`; the handle is read-only, so concurrent calls on
+ * different streams are safe.  Errors: SG_EINVAL, SG_EUNSUPPORTED, SG_ECUDA. */
+int sg_eval_feedback(const sg_surplus* s, const double* d_xq, int64_t Q, int mode,
+                     double* d_out, void* stream);
+
+/* ---------------------------------------------------------------- diagnostics
+ * Not part of the method: launch accounting and timing used by the benchmark. */
+
+/* Number of kernels this library has launched in this process. */
+uint64_t sg_kernel_launches(void);
+
+/* Enable (1) or disable (0) per-kernel timing: while enabled, every launch is
+ * bracketed by two CUDA events recorded on its own stream. */
+void sg_timing_enable(int on);
+
+/* Waits for the recorded events, then reports per kernel name the summed
+ * duration in milliseconds and the number of timed launches, and clears the
+ * totals.  names: max_kernels rows of name_len chars (host); total_ms,
+ * launches: max_kernels entries (host); n_kernels: number of rows written. */
+int sg_timing_collect(int max_kernels, char* names, int name_len, double* total_ms,
+                      int64_t* launches, int* n_kernels);
+
+/* Launches one FMA-chain kernel of `blocks` x `threads` threads, each running
+ * 8 independent chains of 16 x iters fused multiply-adds in FP64
+ * (precision = SG_PREC_FP64) or FP32 (SG_PREC_MIXED), and writes the flop
+ * count of the launch to *flops_per_launch.  d_scratch: device buffer of at
+ * least blocks*threads elements.  Used to measure the FP64 / FP32 pipe peaks
+ * that bound the solver kernels.  Asynchronous on `stream`. */
+int sg_fma_probe(int precision, void* d_scratch, size_t scratch_bytes, int blocks, int threads,
+                 int iters, double* flops_per_launch, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SG_H */

@@ -1,0 +1,373 @@
+// Step III and the on-line phase: hierarchical surpluses and evaluation of the
+// sparse-grid interpolant (Section 3.3, Eq. interpo).
+//
+// The 1-D hierarchical basis a^i_j is the Lagrange polynomial on the CGL set
+// X^i that is 1 at its point of dX^i.  It is evaluated in barycentric form
+// with the Chebyshev-Lobatto weights w_m = (-1)^m delta_m (delta = 1/2 at the
+// two ends), which needs the reciprocals 1/(x - x_m) of the finest set only:
+// every coarser X^i is a subset of it.
+//
+// Distinct 1-D functions are numbered per dimension: id 0 = a^1 (constant),
+// then level 2 (points 0 and 1), level 3 (2 points), level 4 (4), ..., so a
+// node is a tuple of d ids and its basis function is the product of d table
+// entries.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "diag.cuh"
+#include "grid.cuh"
+#include "interp.cuh"
+
+namespace sg {
+
+// Number of 1-D functions for levels 1..L+1.
+int n_functions(int level) {
+  int nf = 0;
+  for (int l = 1; l <= level + 1; ++l) nf += delta_count(l);
+  return nf;
+}
+
+int function_id(int l, int kidx) {
+  int off = 0;
+  for (int m = 1; m < l; ++m) off += delta_count(m);
+  const int j = l == 1 ? 0 : (l == 2 ? kidx / 2 : (kidx - 1) / 2);
+  return off + j;
+}
+
+// All 1-D basis values at one coordinate u in [0, 1] for levels 1..L+1,
+// written to tab[id * stride].  xf holds the fine_n + 1 = 2^L + 1 points of
+// the finest set X^{L+1}.  Exact Kronecker values when u coincides with a
+// point of the level's set.
+__device__ void basis_row(double u, int level, const double* __restrict__ xf, double* tab, int stride) {
+  tab[0] = 1.0;   // a^1 = 1
+  if (level == 0) return;
+  const int fine_n = 1 << level;
+  double rinv[kMaxFine + 1];
+  int hit = -1;
+  for (int p = 0; p <= fine_n; ++p) {
+    const double diff = u - xf[p];
+    if (diff == 0.0) hit = p;
+    rinv[p] = diff == 0.0 ? 0.0 : 1.0 / diff;
+  }
+  int id = 1;
+  for (int l = 2; l <= level + 1; ++l) {
+    const int n = 1 << (l - 1);            // X^l has n + 1 points
+    const int sf = fine_n / n;             // point m of X^l is fine point m * sf
+    const bool exact = hit >= 0 && (hit % sf) == 0;
+    double denom = 0.0;
+    if (!exact) {
+      for (int m = 0; m <= n; ++m) {
+        double wm = (m & 1) ? -1.0 : 1.0;
+        if (m == 0 || m == n) wm *= 0.5;
+        denom += wm * rinv[m * sf];
+      }
+    }
+    const double inv_denom = exact ? 0.0 : 1.0 / denom;
+    // increment points of X^l: level 2 -> m = 0, n; level >= 3 -> odd m
+    const int cnt = l == 2 ? 2 : (n >> 1);
+    for (int j = 0; j < cnt; ++j) {
+      const int m = l == 2 ? j * n : 2 * j + 1;
+      double v;
+      if (exact) {
+        v = (m * sf == hit) ? 1.0 : 0.0;
+      } else {
+        double wm = (m & 1) ? -1.0 : 1.0;
+        if (m == 0 || m == n) wm *= 0.5;
+        v = wm * rinv[m * sf] * inv_denom;
+      }
+      tab[(id + j) * stride] = v;
+    }
+    id += cnt;
+  }
+}
+
+// Points of the finest set X^{L+1} on [0, 1]: x_p = (1 - cos(p pi / 2^L)) / 2
+// = sin^2(p pi / 2^(L+1)) (Eq. CGL).
+__global__ void k_fine_coords(int level, double* xf) {
+  const int fine_n = 1 << level;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > fine_n) return;
+  if (level == 0) {
+    xf[p] = 0.5;
+    return;
+  }
+  const double s = sinpi(static_cast<double>(p) / static_cast<double>(2 * fine_n));
+  xf[p] = s * s;
+}
+
+// Basis values of every 1-D function at every point of the finest set:
+// tab1[id * (fine_n+1) + p].  Used by the surplus build, whose nodes sit on it.
+__global__ void k_fine_table(int level, const double* xf, double* tab1) {
+  const int fine_n = 1 << level;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > fine_n) return;
+  basis_row(level == 0 ? 0.5 : xf[p], level, xf, tab1 + p, fine_n + 1);
+}
+
+// One level of Eq. interpo: for the nodes n in [n0, n1) (all with |i| = s),
+// w_n = f_n - sum over coarser nodes m < n0 of phi_m(x_n) w_m.
+__global__ void k_surplus_level(int64_t n0, int64_t n1, int d, int k, int fine_n,
+                                const uint8_t* __restrict__ fid, const int16_t* __restrict__ fpt,
+                                const double* __restrict__ tab1, const double* __restrict__ f,
+                                double* __restrict__ W) {
+  const int64_t n = n0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (n >= n1) return;
+  double acc[kMaxOut];
+  for (int c = 0; c < k; ++c) acc[c] = f[n * k + c];
+  int pts[kMaxDim];
+  for (int dim = 0; dim < d; ++dim) pts[dim] = fpt[n * d + dim];
+  for (int64_t m = 0; m < n0; ++m) {
+    double phi = 1.0;
+    for (int dim = 0; dim < d && phi != 0.0; ++dim)
+      phi *= tab1[int(fid[m * d + dim]) * (fine_n + 1) + pts[dim]];
+    if (phi != 0.0)
+      for (int c = 0; c < k; ++c) acc[c] -= phi * W[m * k + c];
+  }
+  for (int c = 0; c < k; ++c) W[n * k + c] = acc[c];
+}
+
+// Gather rows of W into the evaluation order.
+__global__ void k_gather_rows(int64_t M, int k, const int32_t* __restrict__ order,
+                              const double* __restrict__ W, double* __restrict__ Ws) {
+  const int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (e >= M * k) return;
+  const int64_t r = e / k, c = e % k;
+  Ws[e] = W[int64_t(order[r]) * k + c];
+}
+
+// FP64 evaluation: thread per query.  The d x nf basis table of each query
+// lives in shared memory (query index fastest, so a warp's accesses are
+// consecutive); the node loop is uniform across the block, and nodes in
+// lexicographic id order reuse the prefix products of their predecessor
+// from dimension start[m] on.
+template <int D>
+__global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(EvalArgs e) {
+  extern __shared__ double tabs_s[];
+  const int tid = threadIdx.x;
+  const int64_t q = blockIdx.x * int64_t(kEvalThreads) + tid;
+  const bool live = q < e.Q;
+  const int nf = e.nf;
+  // tab[(dim * nf + id) * kEvalThreads + tid]
+  if (live) {
+    for (int dim = 0; dim < D; ++dim) {
+      const double u = (e.xq[q * D + dim] - e.lo[dim]) * e.inv_width[dim];
+      basis_row(u, e.level, e.xf, tabs_s + (dim * nf) * kEvalThreads + tid, kEvalThreads);
+    }
+  }
+  __syncthreads();
+  double acc[kMaxOut];
+#pragma unroll
+  for (int c = 0; c < kMaxOut; ++c) acc[c] = 0.0;
+  double pp[D + 1];
+  pp[0] = 1.0;
+#pragma unroll
+  for (int j = 1; j <= D; ++j) pp[j] = 1.0;
+  const int k = e.k;
+  for (int64_t m = 0; m < e.M; ++m) {
+    const int start = e.start[m];
+    const uint8_t* ids = e.fid + m * D;
+#pragma unroll
+    for (int dim = 0; dim < D; ++dim) {
+      if (dim >= start) pp[dim + 1] = pp[dim] * tabs_s[(dim * nf + ids[dim]) * kEvalThreads + tid];
+    }
+    const double phi = pp[D];
+    const double* w = e.W + m * k;
+#pragma unroll
+    for (int c = 0; c < kMaxOut; ++c)
+      if (c < k) acc[c] = fma(phi, w[c], acc[c]);
+  }
+  if (live)
+    for (int c = 0; c < k; ++c) e.out[q * k + c] = acc[c];
+}
+
+template <int D>
+static int launch_eval_fp64(const EvalArgs& e, cudaStream_t st) {
+  const size_t smem = sizeof(double) * D * e.nf * kEvalThreads;
+  if (smem > 200 * 1024) return fail(SG_EUNSUPPORTED, "sg_eval_feedback: grid level too high for the FP64 kernel");
+  SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_fp64<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(smem)));
+  const unsigned blocks = static_cast<unsigned>(ceil_div(e.Q, kEvalThreads));
+  SG_TIMED("k_eval_fp64", st, (k_eval_fp64<D><<<blocks, kEvalThreads, smem, st>>>(e)));
+  SG_LAUNCH_CHECK("k_eval_fp64");
+  return SG_OK;
+}
+
+int eval_fp64(const EvalArgs& e, int d, cudaStream_t st) {
+  switch (d) {
+    case 1: return launch_eval_fp64<1>(e, st);
+    case 2: return launch_eval_fp64<2>(e, st);
+    case 3: return launch_eval_fp64<3>(e, st);
+    case 4: return launch_eval_fp64<4>(e, st);
+    case 5: return launch_eval_fp64<5>(e, st);
+    case 6: return launch_eval_fp64<6>(e, st);
+    case 7: return launch_eval_fp64<7>(e, st);
+    case 8: return launch_eval_fp64<8>(e, st);
+    default: return fail(SG_EUNSUPPORTED, "sg_eval_feedback: d must be 1..8");
+  }
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int k, sg_surplus** out,
+                                  void* stream) {
+  clear_error();
+  if (!g || !d_values || !out) return fail(SG_EINVAL, "sg_build_surpluses: null pointer");
+  *out = nullptr;
+  if (k < 1 || k > kMaxOut) return fail(SG_EINVAL, "sg_build_surpluses: k must be 1..16");
+  if (g->level > kMaxLevel) return fail(SG_EUNSUPPORTED, "sg_build_surpluses: level above 7");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int d = g->d, L = g->level, fine_n = 1 << L;
+  const int64_t M = g->M;
+  auto* s = new sg_surplus();
+  s->d = d;
+  s->level = L;
+  s->k = k;
+  s->M = M;
+  s->nf = n_functions(L);
+  // host: integer structure (function ids, fine positions, level ranges, order)
+  std::vector<uint8_t> fid(M * d);
+  std::vector<int16_t> fpt(M * d);
+  std::vector<int64_t> level_start;
+  int prev_sum = -1;
+  for (int64_t n = 0; n < M; ++n) {
+    int sum = 0;
+    for (int dim = 0; dim < d; ++dim) {
+      const int l = g->h_lev[n * d + dim], kk = g->h_kidx[n * d + dim];
+      sum += l;
+      fid[n * d + dim] = static_cast<uint8_t>(function_id(l, kk));
+      fpt[n * d + dim] = static_cast<int16_t>(l == 1 ? fine_n / 2 : kk * (fine_n >> (l - 1)));
+    }
+    if (sum != prev_sum) {
+      level_start.push_back(n);
+      prev_sum = sum;
+    }
+  }
+  level_start.push_back(M);
+  std::vector<int32_t> order(M);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    for (int dim = 0; dim < d; ++dim) {
+      if (fid[a * d + dim] != fid[b * d + dim]) return fid[a * d + dim] < fid[b * d + dim];
+    }
+    return false;
+  });
+  std::vector<uint8_t> fid_sorted(M * d), start(M);
+  for (int64_t r = 0; r < M; ++r) {
+    const int32_t n = order[r];
+    for (int dim = 0; dim < d; ++dim) fid_sorted[r * d + dim] = fid[int64_t(n) * d + dim];
+    int st0 = 0;
+    if (r > 0) {
+      while (st0 < d && fid_sorted[r * d + st0] == fid_sorted[(r - 1) * d + st0]) ++st0;
+      if (st0 == d) st0 = d - 1;
+    }
+    start[r] = static_cast<uint8_t>(st0);
+  }
+
+  uint8_t* d_fid = nullptr;
+  int16_t* d_fpt = nullptr;
+  double* d_tab1 = nullptr;
+  int32_t* d_order = nullptr;
+  auto cleanup = [&](cudaError_t e, const char* what) {
+    if (d_fid) cudaFree(d_fid);
+    if (d_fpt) cudaFree(d_fpt);
+    if (d_tab1) cudaFree(d_tab1);
+    if (d_order) cudaFree(d_order);
+    sg_surplus_free(s);
+    return e == cudaErrorMemoryAllocation ? fail(SG_ENOMEM, what) : cuda_fail(e, what);
+  };
+  cudaError_t e;
+#define SG_TRY_CLEAN(expr)                                  \
+  if ((e = (expr)) != cudaSuccess) return cleanup(e, #expr);
+  SG_TRY_CLEAN(cudaMalloc(&s->W, M * k * sizeof(double)));
+  SG_TRY_CLEAN(cudaMalloc(&s->Ws, M * k * sizeof(double)));
+  SG_TRY_CLEAN(cudaMalloc(&s->fid_sorted, M * d));
+  SG_TRY_CLEAN(cudaMalloc(&s->start, M));
+  SG_TRY_CLEAN(cudaMalloc(&s->box, 2 * d * sizeof(double)));
+  SG_TRY_CLEAN(cudaMalloc(&s->xf, (fine_n + 1) * sizeof(double)));
+  SG_TRY_CLEAN(cudaMalloc(&d_fid, M * d));
+  SG_TRY_CLEAN(cudaMalloc(&d_fpt, M * d * sizeof(int16_t)));
+  SG_TRY_CLEAN(cudaMalloc(&d_tab1, size_t(s->nf) * (fine_n + 1) * sizeof(double)));
+  SG_TRY_CLEAN(cudaMalloc(&d_order, M * sizeof(int32_t)));
+  std::vector<double> box(2 * d);
+  for (int dim = 0; dim < d; ++dim) {
+    box[dim] = g->h_lo[dim];
+    box[d + dim] = 1.0 / (g->h_hi[dim] - g->h_lo[dim]);
+  }
+  SG_TRY_CLEAN(cudaMemcpyAsync(s->box, box.data(), 2 * d * sizeof(double), cudaMemcpyHostToDevice, st));
+  SG_TRY_CLEAN(cudaMemcpyAsync(d_fid, fid.data(), M * d, cudaMemcpyHostToDevice, st));
+  SG_TRY_CLEAN(cudaMemcpyAsync(d_fpt, fpt.data(), M * d * sizeof(int16_t), cudaMemcpyHostToDevice, st));
+  SG_TRY_CLEAN(cudaMemcpyAsync(s->fid_sorted, fid_sorted.data(), M * d, cudaMemcpyHostToDevice, st));
+  SG_TRY_CLEAN(cudaMemcpyAsync(s->start, start.data(), M, cudaMemcpyHostToDevice, st));
+  SG_TRY_CLEAN(cudaMemcpyAsync(d_order, order.data(), M * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  SG_TIMED("k_fine_coords", st, (k_fine_coords<<<static_cast<unsigned>(ceil_div(fine_n + 1, 64)), 64, 0, st>>>(L, s->xf)));
+  SG_TIMED("k_fine_table", st, (k_fine_table<<<static_cast<unsigned>(ceil_div(fine_n + 1, 64)), 64, 0, st>>>(L, s->xf, d_tab1)));
+  SG_TRY_CLEAN(cudaGetLastError());
+  for (size_t lv = 0; lv + 1 < level_start.size(); ++lv) {
+    const int64_t n0 = level_start[lv], n1 = level_start[lv + 1];
+    SG_TIMED("k_surplus_level", st, (k_surplus_level<<<static_cast<unsigned>(ceil_div(n1 - n0, 128)), 128, 0, st>>>(
+        n0, n1, d, k, fine_n, d_fid, d_fpt, d_tab1, d_values, s->W)));
+    SG_TRY_CLEAN(cudaGetLastError());
+  }
+  SG_TIMED("k_gather_rows", st, (k_gather_rows<<<static_cast<unsigned>(ceil_div(M * k, 256)), 256, 0, st>>>(M, k, d_order, s->W, s->Ws)));
+  SG_TRY_CLEAN(cudaGetLastError());
+  SG_TRY_CLEAN(cudaStreamSynchronize(st));
+#undef SG_TRY_CLEAN
+  cudaFree(d_fid);
+  cudaFree(d_fpt);
+  cudaFree(d_tab1);
+  cudaFree(d_order);
+  *out = s;
+  return SG_OK;
+}
+
+extern "C" int sg_surplus_info(const sg_surplus* s, int64_t* n_nodes, int* k, const double** d_W) {
+  clear_error();
+  if (!s) return fail(SG_EINVAL, "sg_surplus_info: null handle");
+  if (n_nodes) *n_nodes = s->M;
+  if (k) *k = s->k;
+  if (d_W) *d_W = s->W;
+  return SG_OK;
+}
+
+extern "C" void sg_surplus_free(sg_surplus* s) {
+  if (!s) return;
+  if (s->W) cudaFree(s->W);
+  if (s->Ws) cudaFree(s->Ws);
+  if (s->fid_sorted) cudaFree(s->fid_sorted);
+  if (s->start) cudaFree(s->start);
+  if (s->box) cudaFree(s->box);
+  if (s->xf) cudaFree(s->xf);
+  delete s;
+}
+
+extern "C" int sg_eval_feedback(const sg_surplus* s, const double* d_xq, int64_t Q, int mode, double* d_out,
+                                void* stream) {
+  clear_error();
+  if (!s) return fail(SG_EINVAL, "sg_eval_feedback: null handle");
+  if (Q < 0) return fail(SG_EINVAL, "sg_eval_feedback: Q < 0");
+  if (Q == 0) return SG_OK;
+  if (!d_xq || !d_out) return fail(SG_EINVAL, "sg_eval_feedback: null device pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  EvalArgs e{};
+  e.xq = d_xq;
+  e.Q = Q;
+  e.M = s->M;
+  e.k = s->k;
+  e.nf = s->nf;
+  e.level = s->level;
+  e.fid = s->fid_sorted;
+  e.start = s->start;
+  e.W = s->Ws;
+  e.lo = s->box;
+  e.inv_width = s->box + s->d;
+  e.xf = s->xf;
+  e.out = d_out;
+  if (mode == SG_EVAL_FP64) return eval_fp64(e, s->d, st);
+  if (mode == SG_EVAL_TF32X3) return eval_tf32x3(e, s, st);
+  return fail(SG_EINVAL, "sg_eval_feedback: unknown mode");
+}

@@ -1,0 +1,49 @@
+// Surplus handle and evaluation arguments shared by the interpolant kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace sg {
+constexpr int kMaxLevel = 7;                 // finest 1-D set has 2^7 + 1 points
+constexpr int kMaxFine = 1 << kMaxLevel;
+constexpr int kMaxOut = 16;
+constexpr int kEvalThreads = 128;
+
+struct EvalArgs {
+  const double* xq;
+  int64_t Q;
+  int64_t M;
+  int k;
+  int nf;
+  int level;
+  const uint8_t* fid;     // M x d, evaluation order
+  const uint8_t* start;   // M
+  const double* W;        // M x k, evaluation order
+  const double* lo;       // d
+  const double* inv_width;// d
+  const double* xf;       // 2^L + 1 points of the finest 1-D set
+  double* out;            // Q x k
+};
+
+int n_functions(int level);
+int function_id(int l, int kidx);
+__device__ void basis_row(double u, int level, const double* xf, double* tab, int stride);
+}  // namespace sg
+
+struct sg_surplus {
+  int d = 0;
+  int level = 0;
+  int k = 0;
+  int nf = 0;
+  int64_t M = 0;
+  double* W = nullptr;            // M x k, grid order
+  double* Ws = nullptr;           // M x k, evaluation order
+  uint8_t* fid_sorted = nullptr;  // M x d
+  uint8_t* start = nullptr;       // M
+  double* box = nullptr;          // lo[d], 1/(hi-lo)[d]
+  double* xf = nullptr;           // finest 1-D set, 2^L + 1 points
+};
+
+namespace sg {
+int eval_tf32x3(const EvalArgs& e, const sg_surplus* s, cudaStream_t st);
+}

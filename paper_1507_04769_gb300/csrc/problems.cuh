@@ -1,0 +1,387 @@
+// Device-side optimal control problems and their characteristic equations.
+//
+// Section 2: H = L + lambda' f, u* = argmin_u H.  Eq. hamchar: x' = H_lambda',
+// lambda' = -H_x'.  Both families are control-affine with cost 0.5 u'Ru, so
+//   u*      = -G lambda                 (G = R^-1 Bf')
+//   x'      = f0(x) - K lambda          (K = Bf R^-1 Bf')
+//   lambda' = -grad l(x) - f0_x(x)' lambda
+// The Jacobian dF/dy of the 12-dimensional right-hand side is the Hamiltonian
+// matrix [[f0_x, -K], [-(l_xx + d2(lambda' f0)/dx2), -f0_x']]; f0_x and the
+// second derivative come from one forward-mode pass with dual numbers carrying
+// the six state directions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sg {
+
+// Problem data with the derived matrices precomputed on the host.
+struct DevProblem {
+  int kind;
+  // attitude (Section 5, Eq. sat_model)
+  double Jinv[3];
+  double hm[3];
+  double Kw[9];   // (J^-1 B)(J^-1 B)' / r : K restricted to the w block
+  double Gw[9];   // B' J^-1 / r : u* = -Gw lambda_w
+  double wv, ww, r, tv, tw;
+  // LQ
+  double A[36];
+  double K[36];   // B R^-1 B'
+  double Q[36];
+  double QT[36];
+  double G[18];   // R^-1 B' (3 x 6)
+  double R[9];
+};
+
+// ------------------------------------------------------------------ duals
+__device__ __forceinline__ void dsincos(double a, double* s, double* c) { sincos(a, s, c); }
+__device__ __forceinline__ void dsincos(float a, float* s, float* c) { sincosf(a, s, c); }
+__device__ __forceinline__ double recip(double a) { return 1.0 / a; }
+__device__ __forceinline__ float recip(float a) { return 1.0f / a; }
+
+template <typename T, int N>
+struct Dual {
+  T v;
+  T d[N];
+};
+
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> dconst(T a) {
+  Dual<T, N> r;
+  r.v = a;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = T(0);
+  return r;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator+(const Dual<T, N>& a, const Dual<T, N>& b) {
+  Dual<T, N> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator-(const Dual<T, N>& a, const Dual<T, N>& b) {
+  Dual<T, N> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator-(const Dual<T, N>& a) {
+  Dual<T, N> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator*(const Dual<T, N>& a, const Dual<T, N>& b) {
+  Dual<T, N> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator*(const Dual<T, N>& a, T s) {
+  Dual<T, N> r;
+  r.v = a.v * s;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * s;
+  return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator*(T s, const Dual<T, N>& a) { return a * s; }
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator+(const Dual<T, N>& a, T s) {
+  Dual<T, N> r = a;
+  r.v += s;
+  return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> recip(const Dual<T, N>& a) {
+  Dual<T, N> r;
+  r.v = T(1) / a.v;
+  T m = -r.v * r.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * m;
+  return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ void dsincos(const Dual<T, N>& a, Dual<T, N>* s, Dual<T, N>* c) {
+  T sv, cv;
+  dsincos(a.v, &sv, &cv);
+  s->v = sv;
+  c->v = cv;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    s->d[i] = cv * a.d[i];
+    c->d[i] = -sv * a.d[i];
+  }
+}
+
+
+// ------------------------------------------------------------------ attitude
+// f0(x) and g = grad_x(lambda' f0(x)) for x of scalar type S (plain or dual)
+// and lambda of plain type T.
+//   v' = E(v) w with 3-2-1 Euler angles,
+//   w' = J^-1 (g x w), g = R(v) h, R = Rx(phi) Ry(theta) Rz(psi).
+//   lambda' f0 = lv' E(v) w + p . (g x w), p = J^-1 lw:
+//     d/dw   = E(v)' lv + p x g
+//     d/dv_k = lv' (dE/dv_k) w + (dg/dv_k) . (w x p)
+template <typename S, typename T>
+__device__ __forceinline__ void attitude_f0_grad(const DevProblem& P, const S* x, const T* lam,
+                                                 S* f0, S* g) {
+  const S& ph = x[0];
+  const S& th = x[1];
+  const S& ps = x[2];
+  const S& w1 = x[3];
+  const S& w2 = x[4];
+  const S& w3 = x[5];
+  S sp, cp, st, ct, ss, cs;
+  dsincos(ph, &sp, &cp);
+  dsincos(th, &st, &ct);
+  dsincos(ps, &ss, &cs);
+  S sec = recip(ct);
+  S tt = st * sec;
+  S a = sp * w2 + cp * w3;          // sp w2 + cp w3
+  S b = cp * w2 - sp * w3;          // cp w2 - sp w3
+  // E(v) w
+  f0[0] = w1 + tt * a;
+  f0[1] = b;
+  f0[2] = sec * a;
+  // g = Rx Ry Rz h
+  const T h0 = T(P.hm[0]), h1 = T(P.hm[1]), h2 = T(P.hm[2]);
+  S az0 = cs * h0 + ss * h1;
+  S az1 = cs * h1 - ss * h0;
+  // Ry applied to (az0, az1, h2)
+  S ay0 = ct * az0 - st * h2;
+  S ay2 = st * az0 + ct * h2;
+  // Rx applied to (ay0, az1, ay2)
+  S g0 = ay0;
+  S g1 = cp * az1 + sp * ay2;
+  S g2 = cp * ay2 - sp * az1;
+  const T j0 = T(P.Jinv[0]), j1 = T(P.Jinv[1]), j2 = T(P.Jinv[2]);
+  // g x w
+  f0[3] = (g1 * w3 - g2 * w2) * j0;
+  f0[4] = (g2 * w1 - g0 * w3) * j1;
+  f0[5] = (g0 * w2 - g1 * w1) * j2;
+
+  // ---- gradient of lambda' f0
+  const T lv0 = lam[0], lv1 = lam[1], lv2 = lam[2];
+  const T p0 = lam[3] * j0, p1 = lam[4] * j1, p2 = lam[5] * j2;
+  // w x p
+  S q0 = w2 * p2 - w3 * p1;
+  S q1 = w3 * p0 - w1 * p2;
+  S q2 = w1 * p1 - w2 * p0;
+  // dg/dphi = dRx (ay0, az1, ay2) = (0, -sp az1 + cp ay2, -cp az1 - sp ay2)
+  S dphi1 = cp * ay2 - sp * az1;
+  S dphi2 = -(cp * az1 + sp * ay2);
+  // dg/dtheta = Rx dRy (az0, az1, h2); dRy a = (-st a0 - ct a2, 0, ct a0 - st a2)
+  S e0 = -(st * az0 + ct * h2);
+  S e2 = ct * az0 - st * h2;
+  S dth0 = e0;
+  S dth1 = sp * e2;
+  S dth2 = cp * e2;
+  // dg/dpsi = Rx Ry dRz h; dRz h = (-ss h0 + cs h1, -cs h0 - ss h1, 0) = (az1, -az0, 0)
+  S f0y = ct * az1;           // Ry (az1, -az0, 0): (ct az1, -az0, st az1)
+  S f2y = st * az1;
+  S dps0 = f0y;
+  S dps1 = sp * f2y - cp * az0;
+  S dps2 = cp * f2y + sp * az0;
+  // dE/dphi w = (tt b', -a, sec b')  with b' = cp w2 - sp w3 = b, a as above
+  // dE/dtheta w = (sec^2 a, 0, sec^2 st a)
+  S sec2a = sec * sec * a;
+  g[0] = (tt * b) * lv0 - a * lv1 + (sec * b) * lv2 + dphi1 * q1 + dphi2 * q2;
+  g[1] = sec2a * lv0 + (st * sec2a) * lv2 + dth0 * q0 + dth1 * q1 + dth2 * q2;
+  g[2] = dps0 * q0 + dps1 * q1 + dps2 * q2;
+  // E' lv + p x g
+  g[3] = (g2 * p1 - g1 * p2) + lv0;
+  g[4] = (sp * tt) * lv0 + cp * lv1 + (sp * sec) * lv2 + (p2 * g0 - p0 * g2);
+  g[5] = (cp * tt) * lv0 - sp * lv1 + (cp * sec) * lv2 + (p0 * g1 - p1 * g0);
+}
+
+
+// ------------------------------------------------------------------ RHS and Jacobian
+// F(y) for y = (x, lambda) in FP64.
+__device__ __forceinline__ void char_rhs(const DevProblem& P, const double* y, double* F) {
+  if (P.kind == SG_PROBLEM_ATTITUDE) {
+    double f0[6], g[6];
+    attitude_f0_grad<double, double>(P, y, y + 6, f0, g);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[i] = f0[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      F[3 + i] = f0[3 + i] - (P.Kw[3 * i] * y[9] + P.Kw[3 * i + 1] * y[10] + P.Kw[3 * i + 2] * y[11]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[6 + i] = -P.wv * y[i] - g[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[9 + i] = -P.ww * y[3 + i] - g[3 + i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      double ax = 0.0, kl = 0.0, qx = 0.0, atl = 0.0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        ax += P.A[6 * i + j] * y[j];
+        kl += P.K[6 * i + j] * y[6 + j];
+        qx += P.Q[6 * i + j] * y[j];
+        atl += P.A[6 * j + i] * y[6 + j];
+      }
+      F[i] = ax - kl;
+      F[6 + i] = -qx - atl;
+    }
+  }
+}
+
+// Jacobian dF/dy (12 x 12, row-major) in precision T, from one dual pass over
+// the six state directions.  If Fout is non-null and T is double, the FP64
+// right-hand side from the value parts is written there as well.
+template <typename T>
+__device__ __forceinline__ void char_jacobian(const DevProblem& P, const double* y, T* Jm,
+                                              double* Fout) {
+  if (P.kind == SG_PROBLEM_ATTITUDE) {
+    using D = Dual<T, 6>;
+    D x[6], f0[6], g[6];
+    T lam[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      x[i] = dconst<T, 6>(T(y[i]));
+      x[i].d[i] = T(1);
+      lam[i] = T(y[6 + i]);
+    }
+    attitude_f0_grad<D, T>(P, x, lam, f0, g);
+    const T wdiag[6] = {T(P.wv), T(P.wv), T(P.wv), T(P.ww), T(P.ww), T(P.ww)};
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        Jm[12 * r + c] = f0[r].d[c];                         // f0_x
+        Jm[12 * (6 + r) + c] = -g[r].d[c] - (r == c ? wdiag[r] : T(0));  // -(l_xx + phi_xx)
+        Jm[12 * (6 + r) + 6 + c] = -f0[c].d[r];              // -f0_x'
+        T k = T(0);
+        if (r >= 3 && c >= 3) k = T(P.Kw[3 * (r - 3) + (c - 3)]);
+        Jm[12 * r + 6 + c] = -k;                              // -K
+      }
+    }
+    if (Fout) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Fout[i] = double(f0[i].v);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        Fout[3 + i] = double(f0[3 + i].v) -
+                      (P.Kw[3 * i] * y[9] + P.Kw[3 * i + 1] * y[10] + P.Kw[3 * i + 2] * y[11]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Fout[6 + i] = -P.wv * y[i] - double(g[i].v);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Fout[9 + i] = -P.ww * y[3 + i] - double(g[3 + i].v);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        Jm[12 * r + c] = T(P.A[6 * r + c]);
+        Jm[12 * r + 6 + c] = T(-P.K[6 * r + c]);
+        Jm[12 * (6 + r) + c] = T(-P.Q[6 * r + c]);
+        Jm[12 * (6 + r) + 6 + c] = T(-P.A[6 * c + r]);
+      }
+    }
+    if (Fout) char_rhs(P, y, Fout);
+  }
+}
+
+// Running cost L(x, u*(x, lambda)) (Section 2) at y = (x, lambda).
+__device__ __forceinline__ double running_cost(const DevProblem& P, const double* y) {
+  if (P.kind == SG_PROBLEM_ATTITUDE) {
+    double u[3], su = 0.0, sv = 0.0, sw = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      u[i] = -(P.Gw[3 * i] * y[9] + P.Gw[3 * i + 1] * y[10] + P.Gw[3 * i + 2] * y[11]);
+      su += u[i] * u[i];
+      sv += y[i] * y[i];
+      sw += y[3 + i] * y[3 + i];
+    }
+    return 0.5 * (P.wv * sv + P.ww * sw + P.r * su);
+  }
+  double u[3], xqx = 0.0, uru = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) s += P.G[6 * i + j] * y[6 + j];
+    u[i] = -s;
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) s += P.Q[6 * i + j] * y[j];
+    xqx += y[i] * s;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s += P.R[3 * i + j] * u[j];
+    uru += u[i] * s;
+  }
+  return 0.5 * (xqx + uru);
+}
+
+// Terminal cost h(x(T)), its gradient and Hessian.
+__device__ __forceinline__ double terminal_cost(const DevProblem& P, const double* x) {
+  if (P.kind == SG_PROBLEM_ATTITUDE)
+    return 0.5 * (P.tv * (x[0] * x[0] + x[1] * x[1] + x[2] * x[2]) +
+                  P.tw * (x[3] * x[3] + x[4] * x[4] + x[5] * x[5]));
+  double v = 0.0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) s += P.QT[6 * i + j] * x[j];
+    v += x[i] * s;
+  }
+  return 0.5 * v;
+}
+
+__device__ __forceinline__ double terminal_grad(const DevProblem& P, const double* x, int i) {
+  if (P.kind == SG_PROBLEM_ATTITUDE) return (i < 3 ? P.tv : P.tw) * x[i];
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) s += P.QT[6 * i + j] * x[j];
+  return s;
+}
+
+__device__ __forceinline__ double terminal_hess(const DevProblem& P, int i, int j) {
+  if (P.kind == SG_PROBLEM_ATTITUDE) return i == j ? (i < 3 ? P.tv : P.tw) : 0.0;
+  return P.QT[6 * i + j];
+}
+
+// u*(x, lambda) = -G lambda.
+__device__ __forceinline__ void optimal_control(const DevProblem& P, const double* lam, double* u) {
+  if (P.kind == SG_PROBLEM_ATTITUDE) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      u[i] = -(P.Gw[3 * i] * lam[3] + P.Gw[3 * i + 1] * lam[4] + P.Gw[3 * i + 2] * lam[5]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) s += P.G[6 * i + j] * lam[j];
+      u[i] = -s;
+    }
+  }
+}
+
+// Host: derive the device problem from the ABI struct.  Returns false if R is singular.
+bool make_dev_problem(const sg_problem& in, DevProblem* out);
+
+}  // namespace sg

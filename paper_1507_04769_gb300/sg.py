@@ -1,0 +1,224 @@
+"""Python binding of the libsg C ABI (include/sg.h): argument marshalling only.
+
+Device memory and streams come from PyTorch; every step of the method runs in
+the library's CUDA kernels.  Importing this module loads the shared library
+and fails loudly if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+# --------------------------------------------------------------- constants
+SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_EUNSUPPORTED = 0, 1, 2, 3, 4
+PROBLEM_ATTITUDE, PROBLEM_LQ = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+CONVERGED, MAXITER, NONFINITE, SINGULAR, BADINPUT = 0, 1, 2, 3, 4
+EVAL_FP64, EVAL_TF32X3 = 0, 1
+
+
+class Problem(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("_pad", C.c_int32),
+                ("J", C.c_double * 3), ("hmom", C.c_double * 3), ("B", C.c_double * 9),
+                ("wv", C.c_double), ("ww", C.c_double), ("r", C.c_double),
+                ("tv", C.c_double), ("tw", C.c_double),
+                ("A", C.c_double * 36), ("Blq", C.c_double * 18), ("Q", C.c_double * 36),
+                ("R", C.c_double * 9), ("QT", C.c_double * 36)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
+                ("damping", C.c_int32), ("_pad", C.c_int32)]
+
+
+class SGError(RuntimeError):
+    pass
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise SGError(f"libsg.so not built ({path}); run __graft_entry__.build() first")
+    lib = C.CDLL(path)
+    P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    lib.sg_last_error.restype = C.c_char_p
+    lib.sg_build_grid.argtypes = [I32, I32, P, P, C.POINTER(P)]
+    lib.sg_grid_info.argtypes = [P, C.POINTER(I64), C.POINTER(I32), C.POINTER(I32),
+                                 C.POINTER(P), C.POINTER(P), C.POINTER(P)]
+    lib.sg_grid_free.argtypes = [P]
+    lib.sg_grid_free.restype = None
+    lib.sg_solve_workspace_bytes.argtypes = [I64, I32, I32]
+    lib.sg_solve_workspace_bytes.restype = C.c_size_t
+    lib.sg_solve_bvps.argtypes = [C.POINTER(Problem), P, I64, P, P, I32, C.POINTER(SolveOpts),
+                                  P, C.c_size_t, P, P, P, P, P, P, P]
+    lib.sg_build_surpluses.argtypes = [P, P, I32, C.POINTER(P), P]
+    lib.sg_surplus_info.argtypes = [P, C.POINTER(I64), C.POINTER(I32), C.POINTER(P)]
+    lib.sg_surplus_free.argtypes = [P]
+    lib.sg_surplus_free.restype = None
+    lib.sg_eval_feedback.argtypes = [P, P, I64, I32, P, P]
+    for name in ("sg_build_grid", "sg_grid_info", "sg_solve_bvps", "sg_build_surpluses",
+                 "sg_surplus_info", "sg_eval_feedback"):
+        getattr(lib, name).restype = C.c_int
+    return lib
+
+
+LIB = _load()
+
+
+def _check(rc: int):
+    if rc != SG_OK:
+        raise SGError(f"libsg error {rc}: {LIB.sg_last_error().decode()}")
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype, device="cuda"):
+    t = torch.as_tensor(t, dtype=dtype, device=device)
+    return t.contiguous()
+
+
+class _DevView:
+    """__cuda_array_interface__ wrapper for a borrowed device pointer."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"data": (ptr, False), "shape": tuple(shape),
+                                         "typestr": typestr, "version": 3, "strides": None}
+
+
+# --------------------------------------------------------------- problems
+def problem_from(params) -> Problem:
+    """Builds the ABI struct from synthetic parameters (AttitudeParams / LQParams)."""
+    p = Problem()
+    if params.kind == PROBLEM_ATTITUDE:
+        p.kind = PROBLEM_ATTITUDE
+        p.J[:] = [float(v) for v in np.asarray(params.J).ravel()]
+        p.hmom[:] = [float(v) for v in np.asarray(params.hmom).ravel()]
+        p.B[:] = [float(v) for v in np.asarray(params.B).ravel()]
+        p.wv, p.ww, p.r, p.tv, p.tw = params.wv, params.ww, params.r, params.tv, params.tw
+    else:
+        p.kind = PROBLEM_LQ
+        p.A[:] = [float(v) for v in np.asarray(params.A).ravel()]
+        p.Blq[:] = [float(v) for v in np.asarray(params.B).ravel()]
+        p.Q[:] = [float(v) for v in np.asarray(params.Q).ravel()]
+        p.R[:] = [float(v) for v in np.asarray(params.R).ravel()]
+        p.QT[:] = [float(v) for v in np.asarray(params.QT).ravel()]
+    return p
+
+
+# --------------------------------------------------------------- Step I
+class Grid:
+    """sg_build_grid handle: CGL sparse grid of dimension d and level L on a box."""
+
+    def __init__(self, d: int, level: int, lo, hi):
+        lo = np.ascontiguousarray(lo, dtype=np.float64)
+        hi = np.ascontiguousarray(hi, dtype=np.float64)
+        h = C.c_void_p()
+        _check(LIB.sg_build_grid(d, level, lo.ctypes.data_as(C.c_void_p),
+                                 hi.ctypes.data_as(C.c_void_p), C.byref(h)))
+        self._h = h
+        n = C.c_int64()
+        dd, ll = C.c_int(), C.c_int()
+        pc, pl, pi = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        _check(LIB.sg_grid_info(h, C.byref(n), C.byref(dd), C.byref(ll),
+                                C.byref(pc), C.byref(pl), C.byref(pi)))
+        self.M, self.d, self.level = n.value, dd.value, ll.value
+        self.lo, self.hi = lo.copy(), hi.copy()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.coords = torch.as_tensor(_DevView(pc.value, (self.M, self.d), "<f8"), device=dev)
+        self.levels = torch.as_tensor(_DevView(pl.value, (self.M, self.d), "|i1"), device=dev)
+        self.index = torch.as_tensor(_DevView(pi.value, (self.M, self.d), "<i2"), device=dev)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and LIB is not None:
+            LIB.sg_grid_free(self._h)
+            self._h = None
+
+
+# --------------------------------------------------------------- Step II
+def workspace_bytes(n: int, n_max: int, precision: int = PREC_FP64) -> int:
+    return int(LIB.sg_solve_workspace_bytes(n, n_max, precision))
+
+
+def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=50,
+               precision=PREC_FP64, damping=True, n_max=None, return_Y=False,
+               workspace: torch.Tensor | None = None, stream=None):
+    """sg_solve_bvps on device tensors.  x0 (n, 6) f64; T (n,) f64; N (n,) int32."""
+    x0 = _dev(x0, torch.float64).reshape(-1, 6)
+    n = x0.shape[0]
+    dev = x0.device
+    T = _dev(T, torch.float64, dev).reshape(-1).expand(n).contiguous()
+    N = _dev(N, torch.int32, dev).reshape(-1).expand(n).contiguous()
+    if n_max is None:
+        n_max = int(N.max().item()) if n else 1
+    if workspace is None:
+        workspace = torch.empty(max(workspace_bytes(n, n_max, precision), 1), dtype=torch.uint8,
+                                device=dev)
+    out = {
+        "lambda0": torch.empty((n, 6), dtype=torch.float64, device=dev),
+        "u0": torch.empty((n, 3), dtype=torch.float64, device=dev),
+        "V": torch.empty((n,), dtype=torch.float64, device=dev),
+        "status": torch.empty((n,), dtype=torch.int32, device=dev),
+        "iters": torch.empty((n,), dtype=torch.int32, device=dev),
+    }
+    Y = torch.zeros((n, 3 * n_max + 1, 12), dtype=torch.float64, device=dev) if return_Y else None
+    opts = SolveOpts(tol=tol, max_iter=max_iter, precision=precision, damping=int(bool(damping)))
+    _check(LIB.sg_solve_bvps(C.byref(problem), _ptr(x0), n, _ptr(T), _ptr(N), n_max, C.byref(opts),
+                             _ptr(workspace), workspace.numel(), _ptr(out["lambda0"]), _ptr(out["u0"]),
+                             _ptr(out["V"]), _ptr(out["status"]), _ptr(out["iters"]),
+                             _ptr(Y) if Y is not None else None, _stream(stream)))
+    if Y is not None:
+        out["Y"] = Y
+    return out
+
+
+# --------------------------------------------------------------- Step III
+class Surplus:
+    """sg_build_surpluses handle: hierarchical surpluses of values at the nodes."""
+
+    def __init__(self, grid: Grid, values: torch.Tensor, stream=None):
+        values = _dev(values, torch.float64).reshape(grid.M, -1)
+        h = C.c_void_p()
+        _check(LIB.sg_build_surpluses(grid.handle, _ptr(values), values.shape[1], C.byref(h),
+                                      _stream(stream)))
+        self._h = h
+        n, k, pw = C.c_int64(), C.c_int(), C.c_void_p()
+        _check(LIB.sg_surplus_info(h, C.byref(n), C.byref(k), C.byref(pw)))
+        self.M, self.k = n.value, k.value
+        self.d = grid.d
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.W = torch.as_tensor(_DevView(pw.value, (self.M, self.k), "<f8"), device=dev)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and LIB is not None:
+            LIB.sg_surplus_free(self._h)
+            self._h = None
+
+
+def eval_feedback(surplus: Surplus, xq: torch.Tensor, mode: int = EVAL_FP64,
+                  out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    xq = _dev(xq, torch.float64).reshape(-1, surplus.d)
+    Q = xq.shape[0]
+    if out is None:
+        out = torch.empty((Q, surplus.k), dtype=torch.float64, device=xq.device)
+    _check(LIB.sg_eval_feedback(surplus.handle, _ptr(xq), Q, mode, _ptr(out), _stream(stream)))
+    return out

@@ -1,0 +1,252 @@
+"""GPU parity: every CUDA step against the CPU oracle on the same seeded inputs.
+
+Tolerances: 1e-8 relative (max |gpu - oracle| / max |oracle| over the batch)
+for lambda(0), u*(x0) and V from the FP64 and mixed solvers, which both
+iterate to the same FP64 root; 1e-10 for the interpolant, whose FP64 path is
+an exact linear identity up to rounding; bit-exact for integer structure.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import synth  # noqa: E402
+from oracle import bvp as obvp  # noqa: E402
+from oracle import grid as ogrid  # noqa: E402
+from oracle import interp as ointerp  # noqa: E402
+from oracle import problems as oprob  # noqa: E402
+from oracle import riccati  # noqa: E402
+from paper_1507_04769_gb300 import sg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+LO, HI = synth.box(6)
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def cuda(x, dtype=torch.float64):
+    return torch.as_tensor(np.asarray(x), dtype=dtype, device="cuda")
+
+
+# ------------------------------------------------------------------ grid
+@pytest.mark.parametrize("d,L", [(6, 0), (6, 1), (6, 2), (6, 4), (2, 6), (3, 5), (1, 7)])
+def test_grid_matches_oracle(d, L):
+    lo, hi = -np.arange(1, d + 1) * 0.3, np.arange(1, d + 1) * 0.5
+    g = sg.Grid(d, L, lo, hi)
+    og = ogrid.Grid(d, L, lo, hi)
+    assert g.M == og.M == ogrid.count_nodes(d, d + L)
+    assert np.array_equal(g.levels.cpu().numpy(), og.lev)
+    assert np.array_equal(g.index.cpu().numpy(), og.kidx)
+    assert np.max(np.abs(g.coords.cpu().numpy() - og.x)) <= 4e-16 * np.max(np.abs(hi - lo))
+
+
+# ------------------------------------------------------------------ surpluses + eval
+@pytest.mark.parametrize("d,L,k", [(6, 2, 3), (6, 3, 1), (3, 5, 2), (2, 6, 4), (1, 7, 1), (6, 0, 2)])
+def test_surpluses_match_oracle(d, L, k):
+    lo, hi = synth.box(d)
+    g = sg.Grid(d, L, lo, hi)
+    og = ogrid.Grid(d, L, lo, hi)
+    f = np.random.default_rng(10 + L).standard_normal((og.M, k))
+    S = sg.Surplus(g, cuda(f))
+    w = ointerp.surpluses(og, f)
+    assert rel(S.W.cpu().numpy(), w) <= 1e-11
+
+
+@pytest.mark.parametrize("d,L", [(6, 2), (6, 3), (3, 5), (2, 6)])
+def test_eval_matches_oracle(d, L):
+    lo, hi = synth.box(d)
+    g = sg.Grid(d, L, lo, hi)
+    og = ogrid.Grid(d, L, lo, hi)
+    f = np.random.default_rng(20 + L).standard_normal((og.M, 3))
+    S = sg.Surplus(g, cuda(f))
+    w = ointerp.surpluses(og, f)
+    # ragged query count; uniform + clustered + exact nodes + box corners + outside
+    xq = np.concatenate([synth.mixed_queries(301, lo, hi, seed=3), og.x[:17],
+                         np.array([lo, hi, 0.5 * (lo + hi)])])
+    u = sg.eval_feedback(S, cuda(xq)).cpu().numpy()
+    ref = ointerp.eval_surplus(og, w, xq)
+    assert rel(u, ref) <= 1e-10
+    # interpolation is exact at the nodes
+    assert np.max(np.abs(u[301:318] - f[:17])) <= 1e-12 * np.max(np.abs(f))
+
+
+def test_eval_slightly_outside_box():
+    """Outside the box the same polynomial is evaluated; at low degree this is
+    well conditioned, so the two forms still agree."""
+    g = sg.Grid(6, 2, LO, HI)
+    og = ogrid.Grid(6, 2, LO, HI)
+    f = np.random.default_rng(8).standard_normal((og.M, 3))
+    S = sg.Surplus(g, cuda(f))
+    xq = np.array([1.05 * HI, 1.05 * LO, [0.9, -0.9, 0.0, 0.2, -0.85, 0.81]])
+    u = sg.eval_feedback(S, cuda(xq)).cpu().numpy()
+    ref = ointerp.eval_surplus(og, ointerp.surpluses(og, f), xq)
+    assert rel(u, ref) <= 1e-10
+
+
+def test_eval_empty_and_single():
+    g = sg.Grid(6, 2, LO, HI)
+    S = sg.Surplus(g, cuda(np.ones((g.M, 3))))
+    assert sg.eval_feedback(S, torch.empty((0, 6), dtype=torch.float64, device="cuda")).shape == (0, 3)
+    u = sg.eval_feedback(S, cuda(np.zeros((1, 6)))).cpu().numpy()
+    assert np.allclose(u, 1.0, atol=1e-14)   # the constant is reproduced
+
+
+def test_eval_full_size_sampled():
+    """Level-4 grid (1457 nodes) at 1e6 mixed queries, in the launch the benchmark
+    times; 256 sampled queries are recomputed by the oracle."""
+    g = sg.Grid(6, 4, LO, HI)
+    og = ogrid.Grid(6, 4, LO, HI)
+    f = np.random.default_rng(4).standard_normal((og.M, 3))
+    S = sg.Surplus(g, cuda(f))
+    xq = synth.mixed_queries(1_000_000, LO, HI, seed=1)
+    u = sg.eval_feedback(S, cuda(xq)).cpu().numpy()
+    idx = np.random.default_rng(5).choice(xq.shape[0], 256, replace=False)
+    w = ointerp.surpluses(og, f)
+    ref = ointerp.eval_surplus(og, w, xq[idx])
+    assert rel(u[idx], ref) <= 1e-10
+    assert np.all(np.isfinite(u))
+
+
+# ------------------------------------------------------------------ BVP: LQ closed form
+@pytest.mark.parametrize("prec", [sg.PREC_FP64, sg.PREC_MIXED])
+def test_lq_matches_discrete_riccati(prec):
+    params = synth.lq_params(0)
+    pr = oprob.make(params)
+    X0 = synth.uniform_queries(40, LO, HI, seed=21)
+    for T, N in ((1.0, 4), (2.0, 16), (10.0, 128)):
+        res = sg.solve_bvps(sg.problem_from(params), cuda(X0), T, N, tol=1e-12, precision=prec)
+        st = res["status"].cpu().numpy()
+        assert np.all(st == sg.CONVERGED)
+        P0 = riccati.riccati_p0(pr, T, N, discrete=True)
+        ref = X0 @ P0.T
+        assert rel(res["lambda0"].cpu().numpy(), ref) <= 1e-10
+        if prec == sg.PREC_FP64:
+            assert np.all(res["iters"].cpu().numpy() <= 2)
+
+
+def test_lq_continuous_value_fine_mesh():
+    params = synth.lq_params(0)
+    pr = oprob.make(params)
+    X0 = synth.uniform_queries(8, LO, HI, seed=22)
+    res = sg.solve_bvps(sg.problem_from(params), cuda(X0), 10.0, 1024, tol=1e-12)
+    V = np.array([riccati.lq_value(pr, x, 10.0) for x in X0])
+    assert rel(res["V"].cpu().numpy(), V) <= 1e-8
+
+
+# ------------------------------------------------------------------ BVP: attitude vs oracle
+def _oracle(params, X0, T, N):
+    pr = oprob.make(params)
+    T = np.broadcast_to(T, (X0.shape[0],))
+    N = np.broadcast_to(N, (X0.shape[0],))
+    sols = [obvp.solve(pr, X0[i], float(T[i]), int(N[i])) for i in range(X0.shape[0])]
+    assert all(s.status == obvp.CONVERGED for s in sols)
+    return (np.array([s.lambda0 for s in sols]), np.array([s.u0 for s in sols]),
+            np.array([s.V for s in sols]), sols)
+
+
+@pytest.fixture(scope="module")
+def att_case():
+    params = synth.attitude_params(0)
+    X0 = np.concatenate([synth.uniform_queries(10, LO, HI, seed=31), np.zeros((1, 6))])
+    T = np.array([5.0, 10.0, 20.0, 3.0, 7.5, 20.0, 10.0, 5.0, 12.0, 20.0, 20.0])
+    N = np.array([8, 17, 64, 1, 33, 128, 40, 16, 3, 100, 64])   # ragged, incl. N = 1
+    return params, X0, T, N, _oracle(params, X0, T, N)
+
+
+@pytest.mark.parametrize("prec", [sg.PREC_FP64, sg.PREC_MIXED])
+def test_attitude_matches_oracle(att_case, prec):
+    params, X0, T, N, (lam, u, V, _) = att_case
+    res = sg.solve_bvps(sg.problem_from(params), cuda(X0), cuda(T), cuda(N, torch.int32),
+                        tol=1e-12, precision=prec)
+    assert np.all(res["status"].cpu().numpy() == sg.CONVERGED)
+    assert rel(res["lambda0"].cpu().numpy(), lam) <= 1e-8
+    assert rel(res["u0"].cpu().numpy(), u) <= 1e-8
+    assert rel(res["V"].cpu().numpy(), V) <= 1e-8
+    # the origin is an equilibrium: 0 iterations, exact zeros
+    assert res["iters"][-1].item() == 0 and res["V"][-1].item() == 0.0
+
+
+def test_attitude_residual_at_default_tolerance(att_case):
+    """At the default 1e-8 residual tolerance the oracle, recomputing the
+    residual of the collocation system on the GPU's solution, agrees."""
+    params, X0, T, N, _ = att_case
+    res = sg.solve_bvps(sg.problem_from(params), cuda(X0), cuda(T), cuda(N, torch.int32), return_Y=True)
+    Y = res["Y"].cpu().numpy()
+    pr = oprob.make(params)
+    for i in range(X0.shape[0]):
+        F = obvp.residual(pr, Y[i, :3 * N[i] + 1], X0[i], T[i], N[i])
+        assert np.max(np.abs(F)) <= 1e-8
+
+
+def test_attitude_oracle_solution_trajectory(att_case):
+    params, X0, T, N, (_, _, _, sols) = att_case
+    res = sg.solve_bvps(sg.problem_from(params), cuda(X0), cuda(T), cuda(N, torch.int32), tol=1e-12,
+                        return_Y=True)
+    Y = res["Y"].cpu().numpy()
+    for i in (0, 2, 5):
+        ref = sols[i].Y
+        assert rel(Y[i, :3 * N[i] + 1], ref) <= 1e-8
+
+
+def test_batch_independence_bitwise(att_case):
+    """Each node's result is the same alone and inside a batch (Section 3: no
+    communication between nodes)."""
+    params, X0, T, N, _ = att_case
+    prob = sg.problem_from(params)
+    full = sg.solve_bvps(prob, cuda(X0), cuda(T), cuda(N, torch.int32), n_max=128)
+    perm = np.random.default_rng(0).permutation(X0.shape[0])
+    shuf = sg.solve_bvps(prob, cuda(X0[perm]), cuda(T[perm]), cuda(N[perm], torch.int32), n_max=128)
+    for key in ("lambda0", "u0", "V", "iters"):
+        assert torch.equal(full[key][perm], shuf[key])
+    alone = sg.solve_bvps(prob, cuda(X0[2:3]), cuda(T[2:3]), cuda(N[2:3], torch.int32), n_max=128)
+    assert torch.equal(alone["lambda0"][0], full["lambda0"][2])
+
+
+def test_edge_cases_and_bad_input():
+    params = synth.attitude_params(0)
+    prob = sg.problem_from(params)
+    empty = sg.solve_bvps(prob, torch.empty((0, 6), dtype=torch.float64, device="cuda"), 1.0, 4, n_max=4)
+    assert empty["V"].numel() == 0
+    X0 = np.array([[0.1] * 6, [np.nan] + [0.0] * 5, [0.1] * 6, [0.1] * 6])
+    T = np.array([1.0, 1.0, -1.0, 1.0])
+    N = np.array([4, 4, 4, 9])          # last one exceeds n_max
+    res = sg.solve_bvps(prob, cuda(X0), cuda(T), cuda(N, torch.int32), n_max=8)
+    st = res["status"].cpu().numpy()
+    assert st[0] == sg.CONVERGED
+    assert list(st[1:]) == [sg.BADINPUT] * 3
+    with pytest.raises(sg.SGError):
+        sg.solve_bvps(prob, cuda(X0[:1]), 1.0, 4, n_max=4,
+                      workspace=torch.empty(16, dtype=torch.uint8, device="cuda"))
+
+
+def test_max_iter_reported():
+    params = synth.attitude_params(0)
+    X0 = synth.uniform_queries(4, LO, HI, seed=41)
+    res = sg.solve_bvps(sg.problem_from(params), cuda(X0), 20.0, 64, max_iter=1)
+    assert np.all(res["status"].cpu().numpy() == sg.MAXITER)
+    assert np.all(res["iters"].cpu().numpy() == 1)
+
+
+def test_full_size_batched_solve_sampled():
+    """Level-4 grid, 1457 nodes, horizons {10, 20, 40} with N = 64/128/256, in
+    the launch the benchmark times; 6 sampled nodes are re-solved by the oracle."""
+    params = synth.attitude_params(0)
+    g = sg.Grid(6, 4, LO, HI)
+    og = ogrid.Grid(6, 4, LO, HI)
+    T, N = synth.mixed_horizons(g.M, seed=2)
+    for prec in (sg.PREC_FP64, sg.PREC_MIXED):
+        res = sg.solve_bvps(sg.problem_from(params), g.coords, cuda(T), cuda(N, torch.int32), tol=1e-12,
+                            precision=prec)
+        st = res["status"].cpu().numpy()
+        assert np.all(st == sg.CONVERGED), np.bincount(st)
+        idx = np.random.default_rng(7).choice(g.M, 6, replace=False)
+        lam, u, V, _ = _oracle(params, og.x[idx], T[idx], N[idx])
+        assert rel(res["lambda0"].cpu().numpy()[idx], lam) <= 1e-8
+        assert rel(res["u0"].cpu().numpy()[idx], u) <= 1e-8
+        assert rel(res["V"].cpu().numpy()[idx], V) <= 1e-8
