@@ -155,6 +155,37 @@ int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t n,
                   double* d_lambda0, double* d_u0, double* d_V,
                   int32_t* d_status, int32_t* d_iters, double* d_Y, void* stream);
 
+/* sg_solve_bvps_static - the same solve as sg_solve_bvps, for callers that
+ * cannot allocate device memory when they solve: an on-board or real-time
+ * control loop that must not stall or fail on an allocation mid-run, a plugin
+ * whose host process owns the whole device memory pool (so cudaMalloc would
+ * fail or fragment it), or code with a fixed memory budget set at start-up.
+ * The paper has no counterpart; this is an interface convenience only.
+ *
+ * The workspace is a fixed array of SG_STATIC_SCRATCH_BYTES (32 MiB) compiled
+ * into this library: every GPU that loads the library holds it until the
+ * process exits.  This call allocates nothing (no cudaMalloc, no cudaFree, no
+ * allocating library routine); inputs and outputs are caller-owned device
+ * buffers exactly as for sg_solve_bvps, and there is no d_work argument.
+ *   - Batches whose workspace (sg_solve_workspace_bytes(n, n_max_intervals,
+ *     precision)) exceeds SG_STATIC_SCRATCH_BYTES are rejected with SG_EINVAL
+ *     and a message giving both sizes.  That allows 28 nodes at N = 64 in FP64
+ *     (53 mixed), 14 at N = 128 (26), 7 at N = 256 (13) per call.
+ *   - The first call on each device looks up the array's device address with
+ *     cudaGetSymbolAddress (with that device current) and caches it; make that
+ *     first call before any stream capture begins on the device.
+ *   - All calls on a device share the one array, which keeps the last call's
+ *     contents.  The solver writes every region before reading it, so no
+ *     clearing is needed, but calls that overlap on the GPU (concurrent streams
+ *     or host threads) race on the array: serialise them.
+ * Errors: SG_EINVAL, SG_EUNSUPPORTED (device ordinal above 63), SG_ECUDA. */
+#define SG_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, int64_t n,
+                         const double* d_T, const int32_t* d_N, int n_max_intervals,
+                         const sg_solve_opts* opts, double* d_lambda0, double* d_u0,
+                         double* d_V, int32_t* d_status, int32_t* d_iters, double* d_Y,
+                         void* stream);
+
 /* ---------------------------------------------------------------- Step III
  * sg_build_surpluses - hierarchical surpluses of values at the grid nodes,
  * Eq. interpo: level by level, w_n = f(x_n) - I^{|i_n|-1}(f)(x_n).

@@ -752,3 +752,84 @@ extern "C" int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t
   Workspace w = carve(d_work, n, n_max_intervals, sizeof(double));
   return run_solve<double>(a, w, st, d_lambda0, d_u0, d_V, d_status, d_iters, d_Y);
 }
+
+// ---------------------------------------------------------------- no-allocation variant
+// sg_solve_bvps_static: the same solve with its workspace in a fixed array
+// compiled into this library, for callers that cannot allocate device memory
+// when they solve (see include/sg.h).  Nothing here calls cudaMalloc/cudaFree.
+namespace sg {
+
+static __device__ __align__(256) unsigned char g_static_scratch[SG_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxStaticDevices = 64;
+static std::mutex g_static_mu;
+static void* g_static_ptr[kMaxStaticDevices] = {nullptr};
+
+// Device address of g_static_scratch on the current device.  In host code the
+// symbol is only a host-side stand-in, so the address is looked up once per
+// device (with that device current) and cached.
+static int static_scratch_address(void** out) {
+  int dev = -1;
+  SG_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxStaticDevices)
+    return fail(SG_EUNSUPPORTED, "sg_solve_bvps_static: device ordinal above 63");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "sg_solve_bvps_static: cudaGetSymbolAddress");
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return SG_OK;
+}
+
+}  // namespace sg
+
+extern "C" int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, int64_t n, const double* d_T,
+                                    const int32_t* d_N, int n_max_intervals, const sg_solve_opts* opts,
+                                    double* d_lambda0, double* d_u0, double* d_V, int32_t* d_status,
+                                    int32_t* d_iters, double* d_Y, void* stream) {
+  clear_error();
+  if (!prob) return fail(SG_EINVAL, "sg_solve_bvps_static: null problem");
+  if (n < 0) return fail(SG_EINVAL, "sg_solve_bvps_static: n < 0");
+  if (n == 0) return SG_OK;
+  if (n_max_intervals < 1 || n_max_intervals > (1 << 16))
+    return fail(SG_EINVAL, "sg_solve_bvps_static: n_max_intervals must be 1..65536");
+  if (!d_x0 || !d_T || !d_N || !d_lambda0 || !d_u0 || !d_V || !d_status || !d_iters)
+    return fail(SG_EINVAL, "sg_solve_bvps_static: null device pointer");
+  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0};
+  if (opts) o = *opts;
+  if (!(o.tol > 0.0) || o.max_iter < 0) return fail(SG_EINVAL, "sg_solve_bvps_static: bad tol or max_iter");
+  if (o.precision != SG_PREC_FP64 && o.precision != SG_PREC_MIXED)
+    return fail(SG_EINVAL, "sg_solve_bvps_static: unknown precision");
+  const size_t need = ws_bytes(n, n_max_intervals, o.precision);
+  if (need > SG_STATIC_SCRATCH_BYTES)
+    return fail(SG_EINVAL, "sg_solve_bvps_static: this batch needs " + std::to_string(need) +
+                               " bytes of scratch but the static array holds " +
+                               std::to_string(size_t(SG_STATIC_SCRATCH_BYTES)) +
+                               "; solve fewer nodes per call, or use sg_solve_bvps with a caller workspace");
+  SolveArgs a{};
+  if (!make_dev_problem(*prob, &a.P)) return fail(SG_EINVAL, "sg_solve_bvps_static: invalid problem parameters");
+  void* scratch = nullptr;
+  int rc = static_scratch_address(&scratch);
+  if (rc != SG_OK) return rc;
+  a.x0 = d_x0;
+  a.T = d_T;
+  a.N = d_N;
+  a.n = n;
+  a.Nmax = n_max_intervals;
+  a.tol = o.tol;
+  a.max_iter = o.max_iter;
+  a.damping = o.damping;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Every region the solver reads is written first in this call (k_init sets the
+  // iterate, the corrections and the per-node state; the counters are zeroed
+  // before each use), so the previous call's contents need no clearing here.
+  if (o.precision == SG_PREC_MIXED) {
+    Workspace w = carve(scratch, n, n_max_intervals, sizeof(float));
+    return run_solve<float>(a, w, st, d_lambda0, d_u0, d_V, d_status, d_iters, d_Y);
+  }
+  Workspace w = carve(scratch, n, n_max_intervals, sizeof(double));
+  return run_solve<double>(a, w, st, d_lambda0, d_u0, d_V, d_status, d_iters, d_Y);
+}

@@ -56,6 +56,9 @@ def _load():
     lib.sg_solve_workspace_bytes.restype = C.c_size_t
     lib.sg_solve_bvps.argtypes = [C.POINTER(Problem), P, I64, P, P, I32, C.POINTER(SolveOpts),
                                   P, C.c_size_t, P, P, P, P, P, P, P]
+    lib.sg_solve_bvps_static.argtypes = [C.POINTER(Problem), P, I64, P, P, I32, C.POINTER(SolveOpts),
+                                         P, P, P, P, P, P, P]
+    lib.sg_solve_bvps_static.restype = C.c_int
     lib.sg_build_surpluses.argtypes = [P, P, I32, C.POINTER(P), P]
     lib.sg_surplus_info.argtypes = [P, C.POINTER(I64), C.POINTER(I32), C.POINTER(P)]
     lib.sg_surplus_free.argtypes = [P]
