@@ -427,7 +427,9 @@ def roofline(kt, iters, N_h, M, prec):
     steps_timed = None
     models = {
         "k_condense" + suffix: ("alu", flops_condense_interval() * int_units, peak_lin, "TFLOP/s"),
+        "k_condense_reg_fp32": ("alu", flops_condense_interval() * int_units, PEAK_FP32_TFLOPS, "TFLOP/s"),
         "k_abd" + suffix: ("alu", flops_abd_interval() * int_units, peak_lin, "TFLOP/s"),
+        "k_abd_reg" + suffix: ("alu", flops_abd_interval() * int_units, peak_lin, "TFLOP/s"),
         "k_recover" + suffix: ("alu", flops_recover_interval() * int_units, peak_lin, "TFLOP/s"),
         "k_point" + suffix: ("hbm", bytes_point(tsize) * pt_units, None, "GB/s"),
         "k_eval_fp64": ("alu", flops_eval_query(M, 3) * N_QUERIES, PEAK_FP64_TFLOPS, "TFLOP/s"),

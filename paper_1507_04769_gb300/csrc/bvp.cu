@@ -329,6 +329,117 @@ __global__ void __launch_bounds__(32 * kCondWarps) k_condense(SolveArgs a, Works
   }
 }
 
+// Stage condensation, register-resident FP32 form: warp per interval.  Lane
+// r < 24 holds interior equation row r (stage 2 or 3); lanes 24..31 hold the
+// stage-4 rows 24..31 and lanes 0..3 also hold stage-4 rows 32..35.  Partial
+// pivoting over the 24 interior rows: the pivot is the largest |a_rk| among
+// the rows not yet pivoted, found by one warp max-reduction of
+// (|a_rk| bits with the 5 low bits replaced by 31 - lane), so ties go to the
+// lower row.  Rows never move: the pivot row is broadcast by shuffles and
+// every other row updates itself in registers.  At the end the pivot rows
+// (in pivot order) are the stored interior rows and the stage-4 rows hold the
+// condensed block row in columns 24..48.
+__global__ void __launch_bounds__(128) k_condense_reg(SolveArgs a, Workspace w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = blockIdx.x * int64_t(4) + (threadIdx.x >> 5);
+  if (wid >= a.n * a.Nmax) return;
+  const int64_t node = wid / a.Nmax;
+  const int i = static_cast<int>(wid % a.Nmax);
+  if (!w.ns[node].active) return;
+  const int N = a.N[node];
+  if (i >= N) return;
+  const double h = a.T[node] / N;
+  const int64_t pbase = node * npts(a.Nmax) + 3 * int64_t(i);
+  const float* J = static_cast<const float*>(w.Jm) + pbase * 144;
+  const double* Y = w.Y + pbase * 12;
+  const double* F = w.Fv + pbase * 12;
+
+  // row r = 12 (k - 1) + comp, k = stage 2, 3, 4 (1-based 2..4 -> k = 1..3)
+  auto build = [&](int r, float* row) {
+    const int k = r / 12 + 1, comp = r % 12;
+    float cf[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cf[j] = static_cast<float>(-h * kLobA[k][j]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4* src = reinterpret_cast<const float4*>(J + j * 144 + comp * 12);
+      const int c0 = j == 0 ? 24 : (j == 3 ? 36 : 12 * (j - 1));
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float4 v = src[q];
+        row[c0 + 4 * q + 0] = cf[j] * v.x;
+        row[c0 + 4 * q + 1] = cf[j] * v.y;
+        row[c0 + 4 * q + 2] = cf[j] * v.z;
+        row[c0 + 4 * q + 3] = cf[j] * v.w;
+      }
+    }
+    // identity terms: +I on the stage's own point, -I on y_i (static
+    // register indices: compare against every column)
+    const int plus = k < 3 ? 12 * (k - 1) + comp : 36 + comp;
+    const int minus = 24 + comp;
+#pragma unroll
+    for (int c = 0; c < 48; ++c) {
+      if (c == plus) row[c] += 1.0f;
+      if (c == minus) row[c] -= 1.0f;
+    }
+    const double res = Y[12 * k + comp] - Y[comp] -
+                       h * (kLobA[k][0] * F[comp] + kLobA[k][1] * F[12 + comp] + kLobA[k][2] * F[24 + comp] +
+                            kLobA[k][3] * F[36 + comp]);
+    row[48] = static_cast<float>(-res);
+  };
+
+  float ra[kCondLd], rb[kCondLd];
+  build(lane, ra);
+  const bool has_b = lane < 4;
+  if (has_b) build(32 + lane, rb);
+  const bool interior = lane < 24;
+  bool done = false;
+  int my_step = -1;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 24; ++k) {
+    const bool cand = interior && !done;
+    const unsigned key = cand ? ((__float_as_uint(fabsf(ra[k])) & ~31u) | unsigned(31 - lane)) : 0u;
+    const unsigned best = __reduce_max_sync(0xffffffffu, key);
+    const int p = 31 - int(best & 31u);
+    const float piv = __shfl_sync(0xffffffffu, ra[k], p);
+    const bool good = piv != 0.0f && isfinite(piv);
+    ok = ok && good;
+    const float inv = good ? 1.0f / piv : 0.0f;
+    if (lane == p) {
+      done = true;
+      my_step = k;
+    }
+    const bool upd = !(interior && done);
+    const float la = upd ? ra[k] * inv : 0.0f;
+    const float lb = has_b ? rb[k] * inv : 0.0f;
+#pragma unroll
+    for (int c = k + 1; c < kCondLd; ++c) {
+      const float pc = __shfl_sync(0xffffffffu, ra[c], p);
+      if (upd) ra[c] = fmaf(-la, pc, ra[c]);
+      rb[c] = fmaf(-lb, pc, rb[c]);
+    }
+  }
+  if (!ok && lane == 0) w.ns[node].singular = 1;
+  const int64_t blk = node * a.Nmax + i;
+  float* rec = static_cast<float*>(w.Rec) + blk * kRec;
+  float* cond = static_cast<float*>(w.Cond) + blk * kBlk;
+  if (interior) {
+    float* dst = rec + my_step * kCondLd;
+#pragma unroll
+    for (int c = 0; c < kCondLd; ++c) dst[c] = ra[c];
+  } else {
+    float* dst = cond + (lane - 24) * 25;
+#pragma unroll
+    for (int c = 0; c < 25; ++c) dst[c] = ra[24 + c];
+  }
+  if (has_b) {
+    float* dst = cond + (8 + lane) * 25;
+#pragma unroll
+    for (int c = 0; c < 25; ++c) dst[c] = rb[24 + c];
+  }
+}
+
 // Staircase elimination over the block rows of one node, then back substitution.
 template <typename T>
 __global__ void k_abd(SolveArgs a, Workspace w) {
@@ -412,6 +523,206 @@ __global__ void k_abd(SolveArgs a, Workspace w) {
     }
     dy = warp_backsolve<T, 12>(pan, 25, acc, lane);
     if (lane < 12) D[3 * int64_t(i) * 12 + lane] = double(dy);
+  }
+  if (!ok && lane == 0) w.ns[node].singular = 1;
+}
+
+// Pivot search shared by the register-resident kernels: the largest |v| over
+// the candidate lanes, ties to the lower lane (magnitude bits with the 5 low
+// bits replaced by 31 - lane, reduced by one warp max).
+template <typename T>
+__device__ __forceinline__ int warp_pivot_lane(T v, bool cand, int lane) {
+  const float m = fabsf(static_cast<float>(v));
+  const unsigned key = cand ? ((__float_as_uint(m) & ~31u) | unsigned(31 - lane)) : 0u;
+  const unsigned best = __reduce_max_sync(0xffffffffu, key);
+  return 31 - int(best & 31u);
+}
+
+// Staircase elimination, register-resident: warp per node, lanes 0..17 hold
+// the 18 rows of the current panel [carry (6) ; block row i (12)] over the
+// 25 columns [y_i (12) | y_{i+1} (12) | rhs].  Twelve pivot steps with partial
+// pivoting leave 12 pivot rows (stored in pivot order, with the reciprocal of
+// the pivot in place of the pivot) and 6 rows that carry y_{i+1} into the next
+// panel.  The next block row is prefetched into lanes 0..11 while the current
+// panel is eliminated.  After the lambda(T) rows close the system, back
+// substitution runs from the last mesh point to the first.
+template <typename T>
+__global__ void __launch_bounds__(128) k_abd_reg(SolveArgs a, Workspace w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t node = blockIdx.x * int64_t(4) + (threadIdx.x >> 5);
+  if (node >= a.n) return;
+  if (!w.ns[node].active) return;
+  const int N = a.N[node];
+  const int64_t pb = node * npts(a.Nmax);
+  const double* Y = w.Y + pb * 12;
+  const double* x0 = a.x0 + node * 6;
+  const T* cond = static_cast<const T*>(w.Cond) + node * a.Nmax * int64_t(kBlk);
+  T* abd = static_cast<T*>(w.Abd) + node * a.Nmax * int64_t(kBlk);
+  double* D = w.D + pb * 12;
+  const bool rowlane = lane < 18;
+  T r[25], nx[25];
+  // carry rows: [I 0] dy_0 = -(x(0) - x0); lanes 6..17: block row 0
+#pragma unroll
+  for (int c = 0; c < 25; ++c) r[c] = T(0);
+  if (lane < 6) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      if (c == lane) r[c] = T(1);
+    r[24] = T(-(Y[lane] - x0[lane]));
+  } else if (rowlane) {
+#pragma unroll
+    for (int c = 0; c < 25; ++c) r[c] = cond[(lane - 6) * 25 + c];
+  }
+  bool ok = true;
+  for (int i = 0; i < N; ++i) {
+    // prefetch block row i+1 into lanes 0..11
+    if (i + 1 < N && lane < 12) {
+      const T* src = cond + int64_t(i + 1) * kBlk + lane * 25;
+#pragma unroll
+      for (int c = 0; c < 25; ++c) nx[c] = src[c];
+    }
+    bool done = false;
+    int my_step = -1;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const int p = warp_pivot_lane<T>(r[k], rowlane && !done, lane);
+      const T piv = __shfl_sync(0xffffffffu, r[k], p);
+      const bool good = piv != T(0) && isfinite(piv);
+      ok = ok && good;
+      const T inv = good ? T(1) / piv : T(0);
+      if (lane == p) {
+        done = true;
+        my_step = k;
+        r[k] = inv;   // stored pivot row keeps 1/pivot on the diagonal
+      }
+      const bool upd = rowlane && !done;
+      const T l = upd ? r[k] * inv : T(0);
+#pragma unroll
+      for (int c = k + 1; c < 25; ++c) {
+        const T pc = __shfl_sync(0xffffffffu, r[c], p);
+        if (upd) r[c] -= l * pc;
+      }
+    }
+    if (done) {
+      T* dst = abd + int64_t(i) * kBlk + my_step * 25;
+#pragma unroll
+      for (int c = 0; c < 25; ++c) dst[c] = r[c];
+    }
+    // next panel: carry rows shift y_{i+1} into the first block; pivot lanes
+    // take the prefetched block row i+1 (in lane order)
+    const unsigned dmask = __ballot_sync(0xffffffffu, done);
+    const int rank = __popc(dmask & ((1u << lane) - 1u));
+    const bool last = i + 1 == N;
+#pragma unroll
+    for (int c = 0; c < 25; ++c) {
+      const T v = __shfl_sync(0xffffffffu, nx[c], rank & 15);
+      if (rowlane && !done) {
+        if (c < 12) r[c] = r[c + 12];
+        else if (c < 24) r[c] = T(0);
+      } else if (done && !last) {
+        r[c] = v;
+      }
+    }
+    if (last && done) {
+      // closing rows: lambda(T) - grad h(x(T)) = 0 for ranks 0..5, empty rows above
+      const double* yN = Y + 3 * int64_t(N) * 12;
+#pragma unroll
+      for (int c = 0; c < 25; ++c) r[c] = T(0);
+      if (rank < 6) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) r[c] = T(-terminal_hess(a.P, rank, c));
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+          if (c == rank) r[6 + c] = T(1);
+        r[24] = T(-(yN[6 + rank] - terminal_grad(a.P, yN, rank)));
+      }
+    }
+    if (last) {
+      // the closing 12 x 12 system: carry lanes and the 6 terminal rows
+      const bool active_row = rowlane && (!done || rank < 6);
+      bool done2 = false;
+      int my2 = -1;
+      int plane[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const int p = warp_pivot_lane<T>(r[k], active_row && !done2, lane);
+        plane[k] = p;
+        const T piv = __shfl_sync(0xffffffffu, r[k], p);
+        const bool good = piv != T(0) && isfinite(piv);
+        ok = ok && good;
+        const T inv = good ? T(1) / piv : T(0);
+        if (lane == p) {
+          done2 = true;
+          my2 = k;
+          r[k] = inv;
+        }
+        const bool upd = active_row && !done2;
+        const T l = upd ? r[k] * inv : T(0);
+#pragma unroll
+        for (int c = k + 1; c < 12; ++c) {
+          const T pc = __shfl_sync(0xffffffffu, r[c], p);
+          if (upd) r[c] -= l * pc;
+        }
+        const T pr = __shfl_sync(0xffffffffu, r[24], p);
+        if (upd) r[24] -= l * pr;
+      }
+      (void)my2;
+      // back substitution of the closing system: dy_N
+      T dy[12];
+      T t = r[24];
+#pragma unroll
+      for (int k = 11; k >= 0; --k) {
+        const int p = plane[k];
+        const T dk = __shfl_sync(0xffffffffu, t * r[k], p);
+        dy[k] = dk;
+        // every row pivoted before step k subtracts its column-k term
+        t -= r[k] * dk;
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) D[3 * int64_t(N) * 12 + c] = double(dy[c]);
+      }
+      // backward sweep over the stored pivot rows
+      T row[25];
+      if (lane < 12) {
+        const T* src = abd + int64_t(N - 1) * kBlk + lane * 25;
+#pragma unroll
+        for (int c = 0; c < 25; ++c) row[c] = src[c];
+      }
+      for (int ii = N - 1; ii >= 0; --ii) {
+        T pre[25];
+        if (ii > 0 && lane < 12) {
+          const T* src = abd + int64_t(ii - 1) * kBlk + lane * 25;
+#pragma unroll
+          for (int c = 0; c < 25; ++c) pre[c] = src[c];
+        }
+        // lane k holds the pivot row of step k: U (cols k..11, 1/pivot at k),
+        // V (cols 12..23), rhs (24)
+        T tt = row[24];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) tt -= row[12 + c] * dy[c];
+        T nd[12];
+#pragma unroll
+        for (int k = 11; k >= 0; --k) {
+          const T dk = __shfl_sync(0xffffffffu, tt * row[k], k);
+          nd[k] = dk;
+          if (lane < k) tt -= row[k] * dk;
+        }
+#pragma unroll
+        for (int c = 0; c < 12; ++c) dy[c] = nd[c];
+        if (lane < 12) {
+          T mine = T(0);
+#pragma unroll
+          for (int c = 0; c < 12; ++c)
+            if (c == lane) mine = dy[c];
+          D[3 * int64_t(ii) * 12 + lane] = double(mine);
+        }
+        if (ii > 0) {
+#pragma unroll
+          for (int c = 0; c < 25; ++c) row[c] = pre[c];
+        }
+      }
+    }
   }
   if (!ok && lane == 0) w.ns[node].singular = 1;
 }
@@ -675,8 +986,12 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
   for (int it = 0; it < a.max_iter && active > 0; ++it) {
     SG_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), st));
     SG_TIMED(kname<T>("k_point"), st, (k_point<T><<<gp, 128, 0, st>>>(a, w)));
-    SG_TIMED(kname<T>("k_condense"), st, (k_condense<T><<<gcond, 32 * kCondWarps, cond_smem, st>>>(a, w)));
-    SG_TIMED(kname<T>("k_abd"), st, (k_abd<T><<<gabd, 128, 0, st>>>(a, w)));
+    if constexpr (sizeof(T) == sizeof(float)) {
+      SG_TIMED("k_condense_reg_fp32", st, (k_condense_reg<<<grec, 128, 0, st>>>(a, w)));
+    } else {
+      SG_TIMED(kname<T>("k_condense"), st, (k_condense<T><<<gcond, 32 * kCondWarps, cond_smem, st>>>(a, w)));
+    }
+    SG_TIMED(kname<T>("k_abd_reg"), st, (k_abd_reg<T><<<gabd, 128, 0, st>>>(a, w)));
     SG_TIMED(kname<T>("k_recover"), st, (k_recover<T><<<grec, 128, 0, st>>>(a, w)));
     SG_TIMED("k_ls_begin", st, (k_ls_begin<<<gnode_thr, 128, 0, st>>>(a, w)));
     SG_LAUNCH_CHECK("newton kernels");

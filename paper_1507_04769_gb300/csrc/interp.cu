@@ -140,10 +140,38 @@ __global__ void k_gather_rows(int64_t M, int k, const int32_t* __restrict__ orde
 
 // FP64 evaluation: thread per query.  The d x nf basis table of each query
 // lives in shared memory (query index fastest, so a warp's accesses are
-// consecutive); the node loop is uniform across the block, and nodes in
-// lexicographic id order reuse the prefix products of their predecessor
-// from dimension start[m] on.
-template <int D>
+// consecutive).  The node loop is uniform across the block.  Each node
+// carries the table offsets of its active dimensions only (level >= 2; the
+// level-1 factor is the constant 1), so its basis product costs
+// (active - 1) multiplications, taken by a warp-uniform branch, and the
+// contraction costs K fused multiply-adds.
+template <int K>
+__device__ __forceinline__ void eval_accumulate(const EvalArgs& e, const double* __restrict__ tab,
+                                                int tid, double* acc) {
+  for (int64_t m = 0; m < e.M; ++m) {
+    const int na = e.nact[m];
+    const uint16_t* o = e.ops + m * kMaxDim;
+    double phi;
+    switch (na) {
+      case 0: phi = 1.0; break;
+      case 1: phi = tab[o[0] * kEvalThreads + tid]; break;
+      case 2: phi = tab[o[0] * kEvalThreads + tid] * tab[o[1] * kEvalThreads + tid]; break;
+      case 3:
+        phi = tab[o[0] * kEvalThreads + tid] * tab[o[1] * kEvalThreads + tid] * tab[o[2] * kEvalThreads + tid];
+        break;
+      default: {
+        phi = tab[o[0] * kEvalThreads + tid] * tab[o[1] * kEvalThreads + tid] *
+              tab[o[2] * kEvalThreads + tid] * tab[o[3] * kEvalThreads + tid];
+        for (int j = 4; j < na; ++j) phi *= tab[o[j] * kEvalThreads + tid];
+      }
+    }
+    const double* w = e.W + m * K;
+#pragma unroll
+    for (int c = 0; c < K; ++c) acc[c] = fma(phi, w[c], acc[c]);
+  }
+}
+
+template <int D, int K>
 __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(EvalArgs e) {
   extern __shared__ double tabs_s[];
   const int tid = threadIdx.x;
@@ -151,46 +179,75 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(EvalArgs e) {
   const bool live = q < e.Q;
   const int nf = e.nf;
   // tab[(dim * nf + id) * kEvalThreads + tid]
-  if (live) {
-    for (int dim = 0; dim < D; ++dim) {
-      const double u = (e.xq[q * D + dim] - e.lo[dim]) * e.inv_width[dim];
-      basis_row(u, e.level, e.xf, tabs_s + (dim * nf) * kEvalThreads + tid, kEvalThreads);
-    }
+  for (int dim = 0; dim < D; ++dim) {
+    const double u = live ? (e.xq[q * D + dim] - e.lo[dim]) * e.inv_width[dim] : 0.5;
+    basis_row(u, e.level, e.xf, tabs_s + (dim * nf) * kEvalThreads + tid, kEvalThreads);
   }
   __syncthreads();
-  double acc[kMaxOut];
+  double acc[K];
 #pragma unroll
-  for (int c = 0; c < kMaxOut; ++c) acc[c] = 0.0;
-  double pp[D + 1];
-  pp[0] = 1.0;
+  for (int c = 0; c < K; ++c) acc[c] = 0.0;
+  eval_accumulate<K>(e, tabs_s, tid, acc);
+  if (live) {
 #pragma unroll
-  for (int j = 1; j <= D; ++j) pp[j] = 1.0;
-  const int k = e.k;
-  for (int64_t m = 0; m < e.M; ++m) {
-    const int start = e.start[m];
-    const uint8_t* ids = e.fid + m * D;
-#pragma unroll
-    for (int dim = 0; dim < D; ++dim) {
-      if (dim >= start) pp[dim + 1] = pp[dim] * tabs_s[(dim * nf + ids[dim]) * kEvalThreads + tid];
-    }
-    const double phi = pp[D];
-    const double* w = e.W + m * k;
-#pragma unroll
-    for (int c = 0; c < kMaxOut; ++c)
-      if (c < k) acc[c] = fma(phi, w[c], acc[c]);
+    for (int c = 0; c < K; ++c) e.out[q * K + c] = acc[c];
   }
-  if (live)
-    for (int c = 0; c < k; ++c) e.out[q * k + c] = acc[c];
+}
+
+// Any output count: the same loop with a runtime count (rarely used shapes).
+template <int D>
+__global__ void __launch_bounds__(kEvalThreads) k_eval_fp64_anyk(EvalArgs e) {
+  extern __shared__ double tabs_s[];
+  const int tid = threadIdx.x;
+  const int64_t q = blockIdx.x * int64_t(kEvalThreads) + tid;
+  const bool live = q < e.Q;
+  const int nf = e.nf;
+  for (int dim = 0; dim < D; ++dim) {
+    const double u = live ? (e.xq[q * D + dim] - e.lo[dim]) * e.inv_width[dim] : 0.5;
+    basis_row(u, e.level, e.xf, tabs_s + (dim * nf) * kEvalThreads + tid, kEvalThreads);
+  }
+  __syncthreads();
+  const int k = e.k;
+  for (int c0 = 0; c0 < k; c0 += 4) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t m = 0; m < e.M; ++m) {
+      const int na = e.nact[m];
+      const uint16_t* o = e.ops + m * kMaxDim;
+      double phi = 1.0;
+      for (int j = 0; j < na; ++j) phi *= tabs_s[o[j] * kEvalThreads + tid];
+      const double* w = e.W + m * k;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c0 + c < k) acc[c] = fma(phi, w[c0 + c], acc[c]);
+    }
+    if (live)
+      for (int c = 0; c < 4 && c0 + c < k; ++c) e.out[q * k + c0 + c] = acc[c];
+  }
 }
 
 template <int D>
 static int launch_eval_fp64(const EvalArgs& e, cudaStream_t st) {
   const size_t smem = sizeof(double) * D * e.nf * kEvalThreads;
   if (smem > 200 * 1024) return fail(SG_EUNSUPPORTED, "sg_eval_feedback: grid level too high for the FP64 kernel");
-  SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_fp64<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   static_cast<int>(smem)));
   const unsigned blocks = static_cast<unsigned>(ceil_div(e.Q, kEvalThreads));
-  SG_TIMED("k_eval_fp64", st, (k_eval_fp64<D><<<blocks, kEvalThreads, smem, st>>>(e)));
+#define SG_EVAL_K(KK)                                                                              \
+  case KK:                                                                                         \
+    SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_fp64<D, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     static_cast<int>(smem)));                                     \
+    SG_TIMED("k_eval_fp64", st, (k_eval_fp64<D, KK><<<blocks, kEvalThreads, smem, st>>>(e)));      \
+    break;
+  switch (e.k) {
+    SG_EVAL_K(1)
+    SG_EVAL_K(2)
+    SG_EVAL_K(3)
+    SG_EVAL_K(4)
+    SG_EVAL_K(6)
+    default:
+      SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_fp64_anyk<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem)));
+      SG_TIMED("k_eval_fp64", st, (k_eval_fp64_anyk<D><<<blocks, kEvalThreads, smem, st>>>(e)));
+  }
+#undef SG_EVAL_K
   SG_LAUNCH_CHECK("k_eval_fp64");
   return SG_OK;
 }
@@ -256,7 +313,8 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
     }
     return false;
   });
-  std::vector<uint8_t> fid_sorted(M * d), start(M);
+  std::vector<uint8_t> fid_sorted(M * d), start(M), nact(M, 0);
+  std::vector<uint16_t> ops(M * kMaxDim, 0);
   for (int64_t r = 0; r < M; ++r) {
     const int32_t n = order[r];
     for (int dim = 0; dim < d; ++dim) fid_sorted[r * d + dim] = fid[int64_t(n) * d + dim];
@@ -266,6 +324,12 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
       if (st0 == d) st0 = d - 1;
     }
     start[r] = static_cast<uint8_t>(st0);
+    int na = 0;
+    for (int dim = 0; dim < d; ++dim) {
+      const int id = fid_sorted[r * d + dim];
+      if (id != 0) ops[r * kMaxDim + na++] = static_cast<uint16_t>(dim * s->nf + id);
+    }
+    nact[r] = static_cast<uint8_t>(na);
   }
 
   uint8_t* d_fid = nullptr;
@@ -287,6 +351,8 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   SG_TRY_CLEAN(cudaMalloc(&s->Ws, M * k * sizeof(double)));
   SG_TRY_CLEAN(cudaMalloc(&s->fid_sorted, M * d));
   SG_TRY_CLEAN(cudaMalloc(&s->start, M));
+  SG_TRY_CLEAN(cudaMalloc(&s->nact, M));
+  SG_TRY_CLEAN(cudaMalloc(&s->ops, M * kMaxDim * sizeof(uint16_t)));
   SG_TRY_CLEAN(cudaMalloc(&s->box, 2 * d * sizeof(double)));
   SG_TRY_CLEAN(cudaMalloc(&s->xf, (fine_n + 1) * sizeof(double)));
   SG_TRY_CLEAN(cudaMalloc(&d_fid, M * d));
@@ -303,6 +369,8 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   SG_TRY_CLEAN(cudaMemcpyAsync(d_fpt, fpt.data(), M * d * sizeof(int16_t), cudaMemcpyHostToDevice, st));
   SG_TRY_CLEAN(cudaMemcpyAsync(s->fid_sorted, fid_sorted.data(), M * d, cudaMemcpyHostToDevice, st));
   SG_TRY_CLEAN(cudaMemcpyAsync(s->start, start.data(), M, cudaMemcpyHostToDevice, st));
+  SG_TRY_CLEAN(cudaMemcpyAsync(s->nact, nact.data(), M, cudaMemcpyHostToDevice, st));
+  SG_TRY_CLEAN(cudaMemcpyAsync(s->ops, ops.data(), M * kMaxDim * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
   SG_TRY_CLEAN(cudaMemcpyAsync(d_order, order.data(), M * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   SG_TIMED("k_fine_coords", st, (k_fine_coords<<<static_cast<unsigned>(ceil_div(fine_n + 1, 64)), 64, 0, st>>>(L, s->xf)));
   SG_TIMED("k_fine_table", st, (k_fine_table<<<static_cast<unsigned>(ceil_div(fine_n + 1, 64)), 64, 0, st>>>(L, s->xf, d_tab1)));
@@ -340,6 +408,8 @@ extern "C" void sg_surplus_free(sg_surplus* s) {
   if (s->Ws) cudaFree(s->Ws);
   if (s->fid_sorted) cudaFree(s->fid_sorted);
   if (s->start) cudaFree(s->start);
+  if (s->nact) cudaFree(s->nact);
+  if (s->ops) cudaFree(s->ops);
   if (s->box) cudaFree(s->box);
   if (s->xf) cudaFree(s->xf);
   delete s;
@@ -362,6 +432,8 @@ extern "C" int sg_eval_feedback(const sg_surplus* s, const double* d_xq, int64_t
   e.level = s->level;
   e.fid = s->fid_sorted;
   e.start = s->start;
+  e.nact = s->nact;
+  e.ops = s->ops;
   e.W = s->Ws;
   e.lo = s->box;
   e.inv_width = s->box + s->d;

@@ -18,6 +18,8 @@ struct EvalArgs {
   int level;
   const uint8_t* fid;     // M x d, evaluation order
   const uint8_t* start;   // M
+  const uint8_t* nact;    // M: number of active (level >= 2) dimensions
+  const uint16_t* ops;    // M x kMaxDim: table offsets dim * nf + id of the active dimensions
   const double* W;        // M x k, evaluation order
   const double* lo;       // d
   const double* inv_width;// d
@@ -40,6 +42,8 @@ struct sg_surplus {
   double* Ws = nullptr;           // M x k, evaluation order
   uint8_t* fid_sorted = nullptr;  // M x d
   uint8_t* start = nullptr;       // M
+  uint8_t* nact = nullptr;        // M
+  uint16_t* ops = nullptr;        // M x kMaxDim
   double* box = nullptr;          // lo[d], 1/(hi-lo)[d]
   double* xf = nullptr;           // finest 1-D set, 2^L + 1 points
 };
