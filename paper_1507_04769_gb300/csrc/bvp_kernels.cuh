@@ -1,0 +1,754 @@
+// Kernels of the characteristic BVP solver (Section 3.1, Eq. hamchar):
+// four-stage Lobatto IIIA collocation on N equal intervals, damped Newton.
+//
+// One Newton iteration:
+//   k_point     Jacobian dF/dy (precision T) at every collocation point
+//   k_condense  the 36 linearised stage equations of one interval; Gaussian
+//               elimination of the two interior stages (24 columns, partial
+//               pivoting over the 24 interior rows) leaves the 12 x 25 block
+//               row [S | T | rhs] that couples y_i and y_{i+1}
+//   k_abd_reg   staircase elimination with partial pivoting over
+//               [x(0) rows; block rows; lambda(T) rows] and back substitution
+//               for the mesh-point corrections (serial over the intervals of a
+//               node, parallel over nodes)
+//   k_recover   interior-stage corrections from the stored pivot rows
+//   k_trial     FP64 residual at Y + alpha D, per interval; it also stores the
+//               stage residual rows (the right-hand side of the next
+//               condensation); k_ls_reduce takes the Armijo decision per node
+//               in a fixed reduction order
+// T = double gives the FP64 form, T = float the mixed form (FP32 Jacobian,
+// elimination and direction; FP64 residual, line search and update).
+#pragma once
+
+#include <cmath>
+
+#include "common.cuh"
+#include "linalg.cuh"
+#include "problems.cuh"
+
+namespace sg {
+
+// ---------------------------------------------------------------- tableau
+// Four-stage Lobatto IIIA (Hairer & Wanner, Solving ODEs II, Sec. IV.5):
+// c = 0, (5 - sqrt5)/10, (5 + sqrt5)/10, 1; b = (1, 5, 5, 1)/12.
+#define SG_S5 2.2360679774997896964091736687312762
+#define SG_LOB_A                                                                                    \
+  {{0.0, 0.0, 0.0, 0.0},                                                                            \
+   {(11.0 + SG_S5) / 120.0, (25.0 - SG_S5) / 120.0, (25.0 - 13.0 * SG_S5) / 120.0,                  \
+    (-1.0 + SG_S5) / 120.0},                                                                        \
+   {(11.0 - SG_S5) / 120.0, (25.0 + 13.0 * SG_S5) / 120.0, (25.0 + SG_S5) / 120.0,                  \
+    (-1.0 - SG_S5) / 120.0},                                                                        \
+   {1.0 / 12.0, 5.0 / 12.0, 5.0 / 12.0, 1.0 / 12.0}}
+__constant__ double kLobA[4][4] = SG_LOB_A;
+__constant__ float kLobAf[4][4] = SG_LOB_A;
+__constant__ double kLobB[4] = {1.0 / 12.0, 5.0 / 12.0, 5.0 / 12.0, 1.0 / 12.0};
+
+struct NodeState {
+  double fnorm2;   // |F|_2^2 at the current iterate
+  double fmax;     // |F|_inf at the current iterate
+  double alpha;    // current step length
+  int active;      // still iterating
+  int searching;   // in the line search
+  int singular;    // a zero pivot was met this iteration
+  int iters;
+  int status;
+  int _pad;
+};
+
+constexpr int kCols = 49;        // 24 interior + 12 (y_i) + 12 (y_{i+1}) + rhs
+constexpr int kRecLd = 52;       // row stride of a stored interior pivot row (16-byte multiple)
+constexpr int kRec = 24 * kRecLd;
+constexpr int kBlkLd = 28;       // row stride of a 12-row block of 25 columns
+constexpr int kBlk = 12 * kBlkLd;
+constexpr int kResRows = 36;     // stage residual rows per interval
+
+struct Workspace {
+  double* Y;       // n x P x 12, current iterate
+  double* D;       // n x P x 12, Newton direction
+  void* Jm;        // n x P x 144 (T), Jacobians
+  void* Res;       // n x Nmax x 36 (T), stage residuals at the iterate
+  void* Cond;      // n x Nmax x kBlk (T), condensed block rows
+  void* Rec;       // n x Nmax x kRec (T), interior pivot rows
+  void* Abd;       // n x Nmax x kBlk (T), staircase pivot rows
+  double* part;    // n x Nmax x 2, partial |F|^2 and |F|_inf
+  NodeState* ns;   // n
+  int* counters;   // 2
+  size_t bytes;
+};
+
+struct SolveArgs {
+  DevProblem P;
+  const double* x0;
+  const double* T;
+  const int32_t* N;
+  int64_t n;
+  int Nmax;
+  double tol;
+  int max_iter;
+  int damping;
+};
+
+__host__ __device__ __forceinline__ int64_t npts(int Nmax) { return 3 * int64_t(Nmax) + 1; }
+
+// ---------------------------------------------------------------- setup
+__global__ void k_init(SolveArgs a, Workspace w) {
+  const int64_t P = npts(a.Nmax);
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= a.n * P) return;
+  const int64_t node = t / P;
+  const int64_t p = t % P;
+  const double* x0 = a.x0 + node * 6;
+  double* y = w.Y + t * 12;
+  double* d = w.D + t * 12;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    y[c] = x0[c];   // x held at x0, lambda = 0 (zero control)
+    y[6 + c] = 0.0;
+    d[c] = 0.0;
+    d[6 + c] = 0.0;
+  }
+  if (p == 0) {
+    NodeState s{};
+    const int N = a.N[node];
+    const double T = a.T[node];
+    bool ok = N >= 1 && N <= a.Nmax && T > 0.0 && T < INFINITY;
+    for (int c = 0; c < 6; ++c) ok = ok && isfinite(x0[c]);
+    s.alpha = 0.0;   // the first residual evaluation is at Y itself
+    s.active = ok ? 1 : 0;
+    s.searching = ok ? 1 : 0;
+    s.status = ok ? SG_MAXITER : SG_BADINPUT;
+    w.ns[node] = s;
+  }
+}
+
+// ---------------------------------------------------------------- residual
+// FP64 residual at Y + alpha D for one interval: stage rows 2..4 (the first
+// interval adds the x(0) rows, the last the lambda(T) rows).  Writes the
+// partial |.|_2^2 and |.|_inf, and the 36 stage rows (precision T) for the
+// next condensation.
+template <typename T>
+__global__ void k_trial(SolveArgs a, Workspace w) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= a.n * a.Nmax) return;
+  const int64_t node = t / a.Nmax;
+  const int i = static_cast<int>(t % a.Nmax);
+  const NodeState& s = w.ns[node];
+  if (!s.searching) return;
+  const int N = a.N[node];
+  if (i >= N) return;
+  const double h = a.T[node] / N;
+  const double alpha = s.alpha;
+  const int64_t base = (node * npts(a.Nmax) + 3 * int64_t(i)) * 12;
+  double y[4][12], F[4][12];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) y[j][c] = __fma_rn(alpha, w.D[base + 12 * j + c], w.Y[base + 12 * j + c]);
+    char_rhs(a.P, y[j], F[j]);
+  }
+  T* res = static_cast<T*>(w.Res) + t * kResRows;
+  double ss = 0.0, mx = 0.0;
+  bool bad = false;
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      const double r = y[k][c] - y[0][c] -
+                       h * (kLobA[k][0] * F[0][c] + kLobA[k][1] * F[1][c] + kLobA[k][2] * F[2][c] +
+                            kLobA[k][3] * F[3][c]);
+      res[12 * (k - 1) + c] = static_cast<T>(r);
+      bad = bad || !isfinite(r);
+      ss += r * r;
+      mx = fmax(mx, fabs(r));
+    }
+  }
+  if (i == 0) {
+    const double* x0 = a.x0 + node * 6;
+    for (int c = 0; c < 6; ++c) {
+      const double r = y[0][c] - x0[c];
+      bad = bad || !isfinite(r);
+      ss += r * r;
+      mx = fmax(mx, fabs(r));
+    }
+  }
+  if (i == N - 1) {
+    for (int c = 0; c < 6; ++c) {
+      const double r = y[3][6 + c] - terminal_grad(a.P, y[3], c);
+      bad = bad || !isfinite(r);
+      ss += r * r;
+      mx = fmax(mx, fabs(r));
+    }
+  }
+  if (bad) {
+    ss = INFINITY;
+    mx = INFINITY;
+  }
+  w.part[2 * t] = ss;
+  w.part[2 * t + 1] = mx;
+}
+
+// Warp per node: reduce the partial norms in a fixed order and decide.
+// mode 0: initial residual (convergence test at iteration 0);
+// mode 1: Armijo test for the current alpha.
+__global__ void k_ls_reduce(SolveArgs a, Workspace w, int mode) {
+  const int lane = threadIdx.x & 31;
+  const int64_t node = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  if (node >= a.n) return;
+  NodeState s = w.ns[node];
+  if (!s.searching) return;
+  const int N = a.N[node];
+  double ss = 0.0, mx = 0.0;
+  for (int i = lane; i < N; i += 32) {
+    ss += w.part[2 * (node * a.Nmax + i)];
+    mx = fmax(mx, w.part[2 * (node * a.Nmax + i) + 1]);
+  }
+  ss = warp_sum(ss);
+  mx = warp_max(mx);
+  if (lane != 0) return;
+  if (mode == 0) {
+    s.fnorm2 = ss;
+    s.fmax = mx;
+    s.searching = 0;
+    if (!(mx < INFINITY)) {
+      s.status = SG_NONFINITE;
+      s.active = 0;
+    } else if (mx <= a.tol) {
+      s.status = SG_CONVERGED;
+      s.active = 0;
+    } else {
+      atomicAdd(&w.counters[1], 1);
+    }
+  } else {
+    const bool finite = ss < INFINITY;
+    const bool accept = !a.damping || (finite && ss <= (1.0 - 2e-4 * s.alpha) * s.fnorm2) ||
+                        s.alpha <= 0x1p-10;
+    if (accept) {
+      s.fnorm2 = ss;
+      s.fmax = mx;
+      s.searching = 0;
+    } else {
+      s.alpha *= 0.5;
+      atomicAdd(&w.counters[0], 1);
+    }
+  }
+  w.ns[node] = s;
+}
+
+// ---------------------------------------------------------------- Jacobian
+template <typename T>
+__global__ void k_point(SolveArgs a, Workspace w) {
+  const int64_t P = npts(a.Nmax);
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= a.n * P) return;
+  const int64_t node = t / P;
+  const int64_t p = t % P;
+  if (!w.ns[node].active) return;
+  if (p > 3 * int64_t(a.N[node])) return;
+  double y[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) y[c] = w.Y[t * 12 + c];
+  char_jacobian<T>(a.P, y, static_cast<T*>(w.Jm) + t * 144, nullptr);
+}
+
+
+// ---------------------------------------------------------------- helpers
+// Pivot search of the register-resident kernels: the largest |v| over the
+// candidate lanes, ties to the lower lane (magnitude bits with the 5 low bits
+// replaced by 31 - lane, reduced by one warp max).
+template <typename T>
+__device__ __forceinline__ int warp_pivot_lane(T v, bool cand, int lane) {
+  const float m = fabsf(static_cast<float>(v));
+  const unsigned key = cand ? ((__float_as_uint(m) & ~31u) | unsigned(31 - lane)) : 0u;
+  const unsigned best = __reduce_max_sync(0xffffffffu, key);
+  return 31 - int(best & 31u);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_row25(const T* __restrict__ src, T (&r)[25]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const float4 v = s4[q];
+      r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+    }
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const double2 v = s2[q];
+      r[2 * q] = v.x; r[2 * q + 1] = v.y;
+    }
+  }
+  r[24] = src[24];
+}
+
+template <typename T>
+__device__ __forceinline__ void store_row25(T* __restrict__ dst, const T (&r)[25]) {
+  if constexpr (sizeof(T) == 4) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) d4[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+  } else {
+    double2* d2 = reinterpret_cast<double2*>(dst);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) d2[q] = make_double2(r[2 * q], r[2 * q + 1]);
+  }
+  dst[24] = r[24];
+}
+
+// Twelve pivot steps with partial pivoting on 25-column rows held one per
+// lane.  cand: this lane's row takes part.  The pivot row of step k keeps
+// 1/pivot at column k; plane[k] is the lane that held it.
+template <typename T>
+__device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& done, int& my_step,
+                                                  int (&plane)[12], bool& ok, int lane) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int p = warp_pivot_lane<T>(r[k], cand && !done, lane);
+    plane[k] = p;
+    const T piv = __shfl_sync(0xffffffffu, r[k], p);
+    const bool good = piv != T(0) && isfinite(piv);
+    ok = ok && good;
+    const T inv = good ? T(1) / piv : T(0);
+    const bool is_p = lane == p;
+    const T l = (cand && !done && !is_p) ? r[k] * inv : T(0);
+#pragma unroll
+    for (int c = k + 1; c < 25; ++c) {
+      const T pc = __shfl_sync(0xffffffffu, r[c], p);
+      r[c] = fma(-l, pc, r[c]);
+    }
+    if (is_p) {
+      done = true;
+      my_step = k;
+      r[k] = inv;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- condensation
+// Register-resident FP32 form: warp per interval.  Lane r < 24 holds interior
+// equation row r (stages 2 and 3); lanes 24..31 hold stage-4 rows 24..31 and
+// lanes 0..3 also hold stage-4 rows 32..35.  Pivoting is over the 24 interior
+// rows; rows never move: the pivot row is broadcast by shuffles and every
+// other row updates itself in registers.  The pivot rows (in pivot order) are
+// stored for the stage recovery; the stage-4 rows end up holding the
+// condensed block row in columns 24..48.
+__global__ void __launch_bounds__(128) k_condense_reg(SolveArgs a, Workspace w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = blockIdx.x * int64_t(4) + (threadIdx.x >> 5);
+  if (wid >= a.n * a.Nmax) return;
+  const int64_t node = wid / a.Nmax;
+  const int i = static_cast<int>(wid % a.Nmax);
+  if (!w.ns[node].active) return;
+  const int N = a.N[node];
+  if (i >= N) return;
+  const float hf = static_cast<float>(a.T[node]) / static_cast<float>(N);
+  const int64_t pbase = node * npts(a.Nmax) + 3 * int64_t(i);
+  const float* J = static_cast<const float*>(w.Jm) + pbase * 144;
+  const float* res = static_cast<const float*>(w.Res) + wid * kResRows;
+
+  // row r = 12 (k - 1) + comp for stage k = 1, 2, 3 (Lobatto stages 2, 3, 4)
+  auto build = [&](int r, float* row) {
+    const int k = r / 12 + 1, comp = r % 12;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float cf = -hf * kLobAf[k][j];
+      const float4* src = reinterpret_cast<const float4*>(J + j * 144 + comp * 12);
+      const int c0 = j == 0 ? 24 : (j == 3 ? 36 : 12 * (j - 1));
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float4 v = src[q];
+        row[c0 + 4 * q + 0] = cf * v.x;
+        row[c0 + 4 * q + 1] = cf * v.y;
+        row[c0 + 4 * q + 2] = cf * v.z;
+        row[c0 + 4 * q + 3] = cf * v.w;
+      }
+    }
+    // +I on the stage's own point, -I on y_i (compare against every column
+    // so that register indices stay static)
+    const int plus = k < 3 ? 12 * (k - 1) + comp : 36 + comp;
+    const int minus = 24 + comp;
+#pragma unroll
+    for (int c = 0; c < 48; ++c) {
+      if (c == plus) row[c] += 1.0f;
+      if (c == minus) row[c] -= 1.0f;
+    }
+    row[48] = -res[r];
+  };
+
+  float ra[kCols], rb[kCols];
+  build(lane, ra);
+  const bool has_b = lane < 4;
+  if (has_b) build(32 + lane, rb);
+  const bool interior = lane < 24;
+  bool done = false;
+  int my_step = -1;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 24; ++k) {
+    const int p = warp_pivot_lane<float>(ra[k], interior && !done, lane);
+    const float piv = __shfl_sync(0xffffffffu, ra[k], p);
+    const bool good = piv != 0.0f && isfinite(piv);
+    ok = ok && good;
+    const float inv = good ? 1.0f / piv : 0.0f;
+    const bool is_p = lane == p;
+    const float la = (interior && done) || is_p ? 0.0f : ra[k] * inv;
+    const float lb = has_b ? rb[k] * inv : 0.0f;
+#pragma unroll
+    for (int c = k + 1; c < kCols; ++c) {
+      const float pc = __shfl_sync(0xffffffffu, ra[c], p);
+      ra[c] = fmaf(-la, pc, ra[c]);
+      rb[c] = fmaf(-lb, pc, rb[c]);
+    }
+    if (is_p) {
+      done = true;
+      my_step = k;
+    }
+  }
+  if (!ok && lane == 0) w.ns[node].singular = 1;
+  const int64_t blk = node * a.Nmax + i;
+  float* rec = static_cast<float*>(w.Rec) + blk * kRec;
+  float* cond = static_cast<float*>(w.Cond) + blk * kBlk;
+  if (interior) {
+    float4* dst = reinterpret_cast<float4*>(rec + my_step * kRecLd);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) dst[q] = make_float4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
+    rec[my_step * kRecLd + 48] = ra[48];
+  } else {
+    float tmp[25];
+#pragma unroll
+    for (int c = 0; c < 25; ++c) tmp[c] = ra[24 + c];
+    store_row25<float>(cond + (lane - 24) * kBlkLd, tmp);
+  }
+  if (has_b) {
+    float tmp[25];
+#pragma unroll
+    for (int c = 0; c < 25; ++c) tmp[c] = rb[24 + c];
+    store_row25<float>(cond + (8 + lane) * kBlkLd, tmp);
+  }
+}
+
+// Shared-memory FP64 form (used by the FP64 solve): the 36 x 49 system of one
+// interval in shared memory, one warp per interval, elimination of the first
+// 24 columns with partial pivoting over all 36 rows (warp_eliminate).
+constexpr int kCondWarps = 4;
+__global__ void __launch_bounds__(32 * kCondWarps) k_condense_smem(SolveArgs a, Workspace w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t wid = blockIdx.x * int64_t(kCondWarps) + warp;
+  if (wid >= a.n * a.Nmax) return;
+  const int64_t node = wid / a.Nmax;
+  const int i = static_cast<int>(wid % a.Nmax);
+  if (!w.ns[node].active) return;
+  const int N = a.N[node];
+  if (i >= N) return;
+  const double h = a.T[node] / N;
+  double* M = reinterpret_cast<double*>(smem_raw) + warp * (36 * kCols);
+  const int64_t pbase = node * npts(a.Nmax) + 3 * int64_t(i);
+  const double* J = static_cast<const double*>(w.Jm) + pbase * 144;
+  const double* res = static_cast<const double*>(w.Res) + wid * kResRows;
+  double cf[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cf[k][j] = -h * kLobA[k][j];
+  for (int e = lane; e < 36 * 48; e += 32) {
+    const int r = e / 48, c = e % 48;
+    const int k = r / 12 + 1, comp = r % 12;
+    int j, cc;
+    if (c < 24) {
+      j = c / 12 + 1;
+      cc = c % 12;
+    } else if (c < 36) {
+      j = 0;
+      cc = c - 24;
+    } else {
+      j = 3;
+      cc = c - 36;
+    }
+    double v = cf[k][j] * J[j * 144 + comp * 12 + cc];
+    if (comp == cc) {
+      if (j == k) v += 1.0;
+      if (j == 0) v -= 1.0;
+    }
+    M[r * kCols + c] = v;
+  }
+  for (int r = lane; r < 36; r += 32) M[r * kCols + 48] = -res[r];
+  __syncwarp();
+  const bool ok = warp_eliminate<double, 36, kCols, 24>(M, lane);
+  if (!ok && lane == 0) w.ns[node].singular = 1;
+  const int64_t blk = node * a.Nmax + i;
+  double* rec = static_cast<double*>(w.Rec) + blk * kRec;
+  for (int e = lane; e < 24 * kCols; e += 32) rec[(e / kCols) * kRecLd + e % kCols] = M[e];
+  double* cond = static_cast<double*>(w.Cond) + blk * kBlk;
+  for (int e = lane; e < 12 * 25; e += 32) {
+    const int r = e / 25, c = e % 25;
+    cond[r * kBlkLd + c] = M[(24 + r) * kCols + 24 + c];
+  }
+}
+
+// ---------------------------------------------------------------- staircase
+// Register-resident staircase elimination: warp per node, lanes 0..17 hold the
+// 18 rows of the current panel [carry (6) ; block row i (12)] over the 25
+// columns [y_i (12) | y_{i+1} (12) | rhs].  Twelve pivot steps leave 12 pivot
+// rows (stored in pivot order, 1/pivot on the diagonal) and 6 rows that carry
+// y_{i+1} into the next panel.  The next block row is prefetched into lanes
+// 0..11 while the current panel is eliminated.  The lambda(T) rows close the
+// system; back substitution then runs from the last mesh point to the first.
+template <typename T>
+__global__ void __launch_bounds__(128) k_abd_reg(SolveArgs a, Workspace w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t node = blockIdx.x * int64_t(4) + (threadIdx.x >> 5);
+  if (node >= a.n) return;
+  if (!w.ns[node].active) return;
+  const int N = a.N[node];
+  const int64_t pb = node * npts(a.Nmax);
+  const double* Y = w.Y + pb * 12;
+  const double* x0 = a.x0 + node * 6;
+  const T* cond = static_cast<const T*>(w.Cond) + node * a.Nmax * int64_t(kBlk);
+  T* abd = static_cast<T*>(w.Abd) + node * a.Nmax * int64_t(kBlk);
+  double* D = w.D + pb * 12;
+  const bool rowlane = lane < 18;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  T r[25], nx[25];
+#pragma unroll
+  for (int c = 0; c < 25; ++c) {
+    r[c] = T(0);
+    nx[c] = T(0);
+  }
+  if (lane < 6) {
+    // x(0) - x0 = 0 linearised: [I 0] dy_0 = -(x(0) - x0)
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      if (c == lane) r[c] = T(1);
+    r[24] = T(-(Y[lane] - x0[lane]));
+  } else if (rowlane) {
+    load_row25<T>(cond + (lane - 6) * kBlkLd, r);
+  }
+  bool ok = true;
+  bool done = false;
+  int rank = 0;
+  int plane[12];
+  for (int i = 0; i < N; ++i) {
+    if (i + 1 < N && lane < 12) load_row25<T>(cond + int64_t(i + 1) * kBlk + lane * kBlkLd, nx);
+    done = false;
+    int my_step = -1;
+    panel_eliminate12<T>(r, rowlane, done, my_step, plane, ok, lane);
+    if (done) store_row25<T>(abd + int64_t(i) * kBlk + my_step * kBlkLd, r);
+    rank = __popc(__ballot_sync(0xffffffffu, done) & lt_mask);
+    // next panel: carry rows shift y_{i+1} into the first block; the pivot
+    // lanes take the prefetched block row i+1, in lane order
+#pragma unroll
+    for (int c = 0; c < 25; ++c) {
+      const T v = __shfl_sync(0xffffffffu, nx[c], rank & 15);
+      if (done) {
+        r[c] = v;
+      } else if (c < 12) {
+        r[c] = r[c < 12 ? c + 12 : c];
+      } else if (c < 24) {
+        r[c] = T(0);
+      }
+    }
+  }
+  // closing rows: lambda(T) - grad h(x(T)) = 0, taken by pivot lanes of rank
+  // 0..5 (the other pivot lanes sit out); the carry lanes hold the rest
+  const double* yN = Y + 3 * int64_t(N) * 12;
+  if (done) {
+#pragma unroll
+    for (int c = 0; c < 25; ++c) r[c] = T(0);
+    if (rank < 6) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) r[c] = T(-terminal_hess(a.P, rank, c));
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+        if (c == rank) r[6 + c] = T(1);
+      r[24] = T(-(yN[6 + rank] - terminal_grad(a.P, yN, rank)));
+    }
+  }
+  {
+    const bool cand = rowlane && (!done || rank < 6);
+    bool done2 = false;
+    int my2 = -1;
+    panel_eliminate12<T>(r, cand, done2, my2, plane, ok, lane);
+  }
+  // back substitution of the closing system: dy_N (uniform across lanes)
+  T dy[12];
+  {
+    T t = r[24];
+#pragma unroll
+    for (int k = 11; k >= 0; --k) {
+      const T dk = __shfl_sync(0xffffffffu, t * r[k], plane[k]);
+      dy[k] = dk;
+      t = fma(-r[k], dk, t);
+    }
+  }
+  if (lane < 12) {
+    T mine = T(0);
+#pragma unroll
+    for (int c = 0; c < 12; ++c)
+      if (c == lane) mine = dy[c];
+    D[3 * int64_t(N) * 12 + lane] = double(mine);
+  }
+  // backward sweep: lane k holds the stored pivot row of step k of interval ii:
+  // U (cols k..11, 1/pivot at k), V (cols 12..23), rhs (24)
+  T row[25], pre[25];
+#pragma unroll
+  for (int c = 0; c < 25; ++c) {
+    row[c] = T(0);
+    pre[c] = T(0);
+  }
+  if (lane < 12) load_row25<T>(abd + int64_t(N - 1) * kBlk + lane * kBlkLd, row);
+  for (int ii = N - 1; ii >= 0; --ii) {
+    if (ii > 0 && lane < 12) load_row25<T>(abd + int64_t(ii - 1) * kBlk + lane * kBlkLd, pre);
+    T tt = row[24];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) tt = fma(-row[12 + c], dy[c], tt);
+#pragma unroll
+    for (int k = 11; k >= 0; --k) {
+      const T dk = __shfl_sync(0xffffffffu, tt * row[k], k);
+      dy[k] = dk;
+      tt = (lane < k) ? fma(-row[k], dk, tt) : tt;
+    }
+    if (lane < 12) {
+      T mine = T(0);
+#pragma unroll
+      for (int c = 0; c < 12; ++c)
+        if (c == lane) mine = dy[c];
+      D[3 * int64_t(ii) * 12 + lane] = double(mine);
+    }
+#pragma unroll
+    for (int c = 0; c < 25; ++c) row[c] = pre[c];
+  }
+  if (!ok && lane == 0) w.ns[node].singular = 1;
+}
+
+// Interior-stage corrections from the stored condensation pivot rows.
+template <typename T>
+__global__ void k_recover(SolveArgs a, Workspace w) {
+  __shared__ __align__(16) T rows_s[4][kRec];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t wid = blockIdx.x * int64_t(4) + warp;
+  if (wid >= a.n * a.Nmax) return;
+  const int64_t node = wid / a.Nmax;
+  const int i = static_cast<int>(wid % a.Nmax);
+  if (!w.ns[node].active) return;
+  if (i >= a.N[node]) return;
+  T* U = rows_s[warp];
+  const T* rec = static_cast<const T*>(w.Rec) + wid * kRec;
+  for (int e = lane; e < kRec; e += 32) U[e] = rec[e];
+  double* D = w.D + (node * npts(a.Nmax) + 3 * int64_t(i)) * 12;
+  const T dyl = lane < 12 ? T(D[lane]) : T(0);
+  const T dyr = lane < 12 ? T(D[36 + lane]) : T(0);
+  __syncwarp();
+  T acc = lane < 24 ? U[lane * kRecLd + 48] : T(0);
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    const T l = __shfl_sync(0xffffffffu, dyl, c);
+    const T r = __shfl_sync(0xffffffffu, dyr, c);
+    if (lane < 24) acc -= U[lane * kRecLd + 24 + c] * l + U[lane * kRecLd + 36 + c] * r;
+  }
+  const T x = warp_backsolve<T, 24>(U, kRecLd, acc, lane);
+  if (lane < 24) D[12 + lane] = double(x);   // points 3i+1 and 3i+2 are contiguous
+}
+
+// ---------------------------------------------------------------- update
+__global__ void k_ls_begin(SolveArgs a, Workspace w) {
+  const int64_t node = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (node >= a.n) return;
+  NodeState s = w.ns[node];
+  if (!s.active) return;
+  if (s.singular) {
+    s.status = SG_SINGULAR;
+    s.active = 0;
+  } else {
+    s.searching = 1;
+    s.alpha = 1.0;
+  }
+  w.ns[node] = s;
+}
+
+__global__ void k_update(SolveArgs a, Workspace w) {
+  const int64_t P = npts(a.Nmax);
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= a.n * P) return;
+  const int64_t node = t / P;
+  if (!w.ns[node].active) return;
+  if (t % P > 3 * int64_t(a.N[node])) return;
+  const double alpha = w.ns[node].alpha;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) w.Y[t * 12 + c] = __fma_rn(alpha, w.D[t * 12 + c], w.Y[t * 12 + c]);
+}
+
+__global__ void k_after_update(SolveArgs a, Workspace w) {
+  const int64_t node = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (node >= a.n) return;
+  NodeState s = w.ns[node];
+  if (!s.active) return;
+  s.iters += 1;
+  if (!(s.fmax < INFINITY)) {
+    s.status = SG_NONFINITE;
+    s.active = 0;
+  } else if (s.fmax <= a.tol) {
+    s.status = SG_CONVERGED;
+    s.active = 0;
+  } else if (s.iters >= a.max_iter) {
+    s.status = SG_MAXITER;
+    s.active = 0;
+  } else {
+    atomicAdd(&w.counters[1], 1);
+  }
+  w.ns[node] = s;
+}
+
+// Outputs (Eq. optuv): lambda(0), u*(x0, lambda(0)), V = z(T) + h(x(T)) with
+// z(T) = h sum_i sum_j b_j L(Y_ij) (the Lobatto IIIA step of z' = L).
+__global__ void k_outputs(SolveArgs a, Workspace w, double* lambda0, double* u0, double* V,
+                          int32_t* status, int32_t* iters) {
+  const int lane = threadIdx.x & 31;
+  const int64_t node = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  if (node >= a.n) return;
+  const NodeState s = w.ns[node];
+  const double* Y = w.Y + node * npts(a.Nmax) * 12;
+  if (s.status == SG_BADINPUT) {
+    if (lane == 0) {
+      for (int c = 0; c < 6; ++c) lambda0[node * 6 + c] = NAN;
+      for (int c = 0; c < 3; ++c) u0[node * 3 + c] = NAN;
+      V[node] = NAN;
+      status[node] = s.status;
+      iters[node] = 0;
+    }
+    return;
+  }
+  const int N = a.N[node];
+  const double h = a.T[node] / N;
+  double z = 0.0;
+  for (int i = lane; i < N; i += 32) {
+    const double* yi = Y + 3 * int64_t(i) * 12;
+    z += h * (kLobB[0] * running_cost(a.P, yi) + kLobB[1] * running_cost(a.P, yi + 12) +
+              kLobB[2] * running_cost(a.P, yi + 24) + kLobB[3] * running_cost(a.P, yi + 36));
+  }
+  z = warp_sum(z);
+  if (lane == 0) {
+    const double* yN = Y + 3 * int64_t(N) * 12;
+    V[node] = z + terminal_cost(a.P, yN);
+    double u[3];
+    optimal_control(a.P, Y + 6, u);
+    for (int c = 0; c < 6; ++c) lambda0[node * 6 + c] = Y[6 + c];
+    for (int c = 0; c < 3; ++c) u0[node * 3 + c] = u[c];
+    status[node] = s.status;
+    iters[node] = s.iters;
+  }
+}
+
+__global__ void k_copy_Y(SolveArgs a, Workspace w, double* out) {
+  const int64_t P = npts(a.Nmax);
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= a.n * P) return;
+  const int64_t node = t / P;
+  if (t % P > 3 * int64_t(a.N[node])) return;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) out[t * 12 + c] = w.Y[t * 12 + c];
+}
+
+}  // namespace sg
