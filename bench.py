@@ -41,7 +41,7 @@ LEVEL, D = 4, 6
 N_QUERIES = 1_000_000
 TOL = 1e-8
 WORKLOAD = ("attitude6d_L4_1457nodes_T{10,20,40}_N{64,128,256}_mixedprec"
-            "+surplus+1e6queries_fp64eval")
+            "+surplus+1e6queries")
 
 # Derived ALU peaks (unit counts x maximum SM clock, 2070 MHz, 152 SMs):
 #   FP32: 128 FMA lanes/SM x 2 flops = 80.6 TFLOP/s
@@ -79,6 +79,13 @@ def bytes_point(tsize: int) -> float:
 def flops_eval_query(M: int, k: int) -> float:
     """Per query: the contraction (2 k flops per node) and one product per node."""
     return M * (2 * k + 1)
+
+
+def flops_eval_query_df32(M: int, k: int) -> float:
+    """Per query on the FP32 pipe (pair-of-floats arithmetic, FMA = 2 flops):
+    per node and output 15 (exact product 3, cross terms 4, exact sum 6, tail
+    2) and about 17 for the basis product (1.7 pair multiplications of 10)."""
+    return M * (15 * k + 17)
 
 
 # ------------------------------------------------------------------ helpers
@@ -217,6 +224,7 @@ def gpu_arm(args):
     from paper_1507_04769_gb300 import sg
 
     prec = sg.PREC_MIXED if args.precision == "mixed" else sg.PREC_FP64
+    eval_mode = {"fp64": sg.EVAL_FP64, "df32": sg.EVAL_DF32, "tf32x3": sg.EVAL_TF32X3}[args.eval]
     lo, hi = synth.box(D)
     params = synth.attitude_params(0)
     prob = sg.problem_from(params)
@@ -245,7 +253,7 @@ def gpu_arm(args):
         S = sg.Surplus(g, res["u0"])
         if events:
             events[3].record(stream)
-        sg.eval_feedback(S, xq_d, out=u_out)
+        sg.eval_feedback(S, xq_d, mode=eval_mode, out=u_out)
         if events:
             events[4].record(stream)
         return res
@@ -373,7 +381,8 @@ def gpu_arm(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "nodes": M, "grid_level": LEVEL, "d": D,
                    "horizons": "T in {10,20,40}, N = 6.4 T", "queries": N_QUERIES, "tol": TOL,
-                   "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
+                   "precision": args.precision, "eval": args.eval,
+                   "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"{world} independent instance(s), no collective"},
         "feedback_evals_per_s": N_QUERIES / (phase_ms["eval"] / 1e3),
         "breakdown_ms": phase_ms,
@@ -433,6 +442,7 @@ def roofline(kt, iters, N_h, M, prec):
         "k_recover" + suffix: ("alu", flops_recover_interval() * int_units, peak_lin, "TFLOP/s"),
         "k_point" + suffix: ("hbm", bytes_point(tsize) * pt_units, None, "GB/s"),
         "k_eval_fp64": ("alu", flops_eval_query(M, 3) * N_QUERIES, PEAK_FP64_TFLOPS, "TFLOP/s"),
+        "k_eval_df32": ("alu", flops_eval_query_df32(M, 3) * N_QUERIES, PEAK_FP32_TFLOPS, "TFLOP/s"),
     }
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = 6785.9
@@ -448,7 +458,7 @@ def roofline(kt, iters, N_h, M, prec):
         if name in models and n > 0:
             bound, work_per_solve, peak, unit = models[name]
             # every timed step repeats the same solve (work per step = work_per_solve)
-            if name == "k_eval_fp64":
+            if name.startswith("k_eval"):
                 work_total = work_per_solve * n
             else:
                 steps_timed = steps_timed or max(1, round(kt.get("k_outputs", (0, 1))[1]))
@@ -483,7 +493,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--cpu-nodes", type=int, default=40)
+    ap.add_argument("--eval", choices=["df32", "fp64", "tf32x3"], default="df32")
+    ap.add_argument("--cpu-nodes", type=int, default=100)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--cpu-worker", nargs=2, type=int, default=None, help=argparse.SUPPRESS)

@@ -58,8 +58,15 @@ enum { SG_PREC_FP64 = 0, SG_PREC_MIXED = 1 };
  * is skipped and its outputs are NaN). */
 enum { SG_CONVERGED = 0, SG_MAXITER = 1, SG_NONFINITE = 2, SG_SINGULAR = 3, SG_BADINPUT = 4 };
 
-/* Interpolant evaluation mode. */
-enum { SG_EVAL_FP64 = 0, SG_EVAL_TF32X3 = 1 };
+/* Interpolant evaluation mode.
+ * FP64:   FP64 arithmetic throughout.
+ * TF32X3: contraction on tensor cores with split-TF32 operands (about 1e-6
+ *         relative; the bound is stated with sg_eval_feedback).
+ * DF32:   FP64-accurate on the FP32 pipe: every quantity is a pair of floats
+ *         (about 48 significant bits), the contraction is a compensated dot
+ *         product folded into FP64 every 64 nodes; agrees with FP64 to about
+ *         1e-13 relative (k = 1, 2, 3, 4 or 6). */
+enum { SG_EVAL_FP64 = 0, SG_EVAL_TF32X3 = 1, SG_EVAL_DF32 = 2 };
 
 /* ---------------------------------------------------------------- problem
  * The optimal control problem of Section 2 for the two families built in:

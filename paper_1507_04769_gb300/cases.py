@@ -21,7 +21,7 @@ import torch  # noqa: E402
 import synth  # noqa: E402
 from paper_1507_04769_gb300 import sg  # noqa: E402
 
-MODES = {"fp64": sg.EVAL_FP64, "tf32x3": sg.EVAL_TF32X3}
+MODES = {"fp64": sg.EVAL_FP64, "tf32x3": sg.EVAL_TF32X3, "df32": sg.EVAL_DF32}
 
 
 def main(argv=None):

@@ -330,6 +330,7 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
       if (id != 0) ops[r * kMaxDim + na++] = static_cast<uint16_t>(dim * s->nf + id);
     }
     nact[r] = static_cast<uint8_t>(na);
+    if (na > s->amax) s->amax = na;
   }
 
   uint8_t* d_fid = nullptr;
@@ -355,6 +356,8 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   SG_TRY_CLEAN(cudaMalloc(&s->ops, M * kMaxDim * sizeof(uint16_t)));
   SG_TRY_CLEAN(cudaMalloc(&s->box, 2 * d * sizeof(double)));
   SG_TRY_CLEAN(cudaMalloc(&s->xf, (fine_n + 1) * sizeof(double)));
+  SG_TRY_CLEAN(cudaMalloc(&s->xfdf, (fine_n + 1) * sizeof(float2)));
+  SG_TRY_CLEAN(cudaMalloc(&s->Wdf, M * k * sizeof(float2)));
   SG_TRY_CLEAN(cudaMalloc(&d_fid, M * d));
   SG_TRY_CLEAN(cudaMalloc(&d_fpt, M * d * sizeof(int16_t)));
   SG_TRY_CLEAN(cudaMalloc(&d_tab1, size_t(s->nf) * (fine_n + 1) * sizeof(double)));
@@ -383,6 +386,8 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   }
   SG_TIMED("k_gather_rows", st, (k_gather_rows<<<static_cast<unsigned>(ceil_div(M * k, 256)), 256, 0, st>>>(M, k, d_order, s->W, s->Ws)));
   SG_TRY_CLEAN(cudaGetLastError());
+  if (split_df(fine_n + 1, s->xf, s->xfdf, st) != SG_OK || split_df(M * k, s->Ws, s->Wdf, st) != SG_OK)
+    return cleanup(cudaGetLastError(), "split_df");
   SG_TRY_CLEAN(cudaStreamSynchronize(st));
 #undef SG_TRY_CLEAN
   cudaFree(d_fid);
@@ -412,6 +417,8 @@ extern "C" void sg_surplus_free(sg_surplus* s) {
   if (s->ops) cudaFree(s->ops);
   if (s->box) cudaFree(s->box);
   if (s->xf) cudaFree(s->xf);
+  if (s->xfdf) cudaFree(s->xfdf);
+  if (s->Wdf) cudaFree(s->Wdf);
   delete s;
 }
 
@@ -430,6 +437,7 @@ extern "C" int sg_eval_feedback(const sg_surplus* s, const double* d_xq, int64_t
   e.k = s->k;
   e.nf = s->nf;
   e.level = s->level;
+  e.amax = s->amax;
   e.fid = s->fid_sorted;
   e.start = s->start;
   e.nact = s->nact;
@@ -438,8 +446,11 @@ extern "C" int sg_eval_feedback(const sg_surplus* s, const double* d_xq, int64_t
   e.lo = s->box;
   e.inv_width = s->box + s->d;
   e.xf = s->xf;
+  e.xfdf = s->xfdf;
+  e.Wdf = s->Wdf;
   e.out = d_out;
   if (mode == SG_EVAL_FP64) return eval_fp64(e, s->d, st);
   if (mode == SG_EVAL_TF32X3) return eval_tf32x3(e, s, st);
+  if (mode == SG_EVAL_DF32) return eval_df32(e, s->d, st);
   return fail(SG_EINVAL, "sg_eval_feedback: unknown mode");
 }

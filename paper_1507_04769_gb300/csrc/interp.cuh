@@ -16,6 +16,7 @@ struct EvalArgs {
   int k;
   int nf;
   int level;
+  int amax;               // largest number of active dimensions over the nodes
   const uint8_t* fid;     // M x d, evaluation order
   const uint8_t* start;   // M
   const uint8_t* nact;    // M: number of active (level >= 2) dimensions
@@ -24,6 +25,8 @@ struct EvalArgs {
   const double* lo;       // d
   const double* inv_width;// d
   const double* xf;       // 2^L + 1 points of the finest 1-D set
+  const float2* xfdf;     // the same points as (hi, lo) float pairs
+  const float2* Wdf;      // M x k surpluses as (hi, lo) pairs, evaluation order
   double* out;            // Q x k
 };
 
@@ -37,6 +40,7 @@ struct sg_surplus {
   int level = 0;
   int k = 0;
   int nf = 0;
+  int amax = 0;
   int64_t M = 0;
   double* W = nullptr;            // M x k, grid order
   double* Ws = nullptr;           // M x k, evaluation order
@@ -46,8 +50,12 @@ struct sg_surplus {
   uint16_t* ops = nullptr;        // M x kMaxDim
   double* box = nullptr;          // lo[d], 1/(hi-lo)[d]
   double* xf = nullptr;           // finest 1-D set, 2^L + 1 points
+  float2* xfdf = nullptr;         // finest 1-D set as (hi, lo) pairs
+  float2* Wdf = nullptr;          // Ws as (hi, lo) pairs
 };
 
 namespace sg {
 int eval_tf32x3(const EvalArgs& e, const sg_surplus* s, cudaStream_t st);
+int eval_df32(const EvalArgs& e, int d, cudaStream_t st);
+int split_df(int64_t n, const double* src, float2* dst, cudaStream_t st);
 }

@@ -19,7 +19,7 @@ SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_EUNSUPPORTED = 0, 1, 2, 3, 4
 PROBLEM_ATTITUDE, PROBLEM_LQ = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 CONVERGED, MAXITER, NONFINITE, SINGULAR, BADINPUT = 0, 1, 2, 3, 4
-EVAL_FP64, EVAL_TF32X3 = 0, 1
+EVAL_FP64, EVAL_TF32X3, EVAL_DF32 = 0, 1, 2
 
 
 class Problem(C.Structure):

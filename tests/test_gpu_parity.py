@@ -58,8 +58,12 @@ def test_surpluses_match_oracle(d, L, k):
     assert rel(S.W.cpu().numpy(), w) <= 1e-11
 
 
+EVAL_MODES = [sg.EVAL_FP64, sg.EVAL_DF32]
+
+
+@pytest.mark.parametrize("mode", EVAL_MODES, ids=["fp64", "df32"])
 @pytest.mark.parametrize("d,L", [(6, 2), (6, 3), (3, 5), (2, 6)])
-def test_eval_matches_oracle(d, L):
+def test_eval_matches_oracle(d, L, mode):
     lo, hi = synth.box(d)
     g = sg.Grid(d, L, lo, hi)
     og = ogrid.Grid(d, L, lo, hi)
@@ -69,14 +73,15 @@ def test_eval_matches_oracle(d, L):
     # ragged query count; uniform + clustered + exact nodes + box corners + outside
     xq = np.concatenate([synth.mixed_queries(301, lo, hi, seed=3), og.x[:17],
                          np.array([lo, hi, 0.5 * (lo + hi)])])
-    u = sg.eval_feedback(S, cuda(xq)).cpu().numpy()
+    u = sg.eval_feedback(S, cuda(xq), mode=mode).cpu().numpy()
     ref = ointerp.eval_surplus(og, w, xq)
     assert rel(u, ref) <= 1e-10
     # interpolation is exact at the nodes
     assert np.max(np.abs(u[301:318] - f[:17])) <= 1e-12 * np.max(np.abs(f))
 
 
-def test_eval_slightly_outside_box():
+@pytest.mark.parametrize("mode", EVAL_MODES, ids=["fp64", "df32"])
+def test_eval_slightly_outside_box(mode):
     """Outside the box the same polynomial is evaluated; at low degree this is
     well conditioned, so the two forms still agree."""
     g = sg.Grid(6, 2, LO, HI)
@@ -84,9 +89,21 @@ def test_eval_slightly_outside_box():
     f = np.random.default_rng(8).standard_normal((og.M, 3))
     S = sg.Surplus(g, cuda(f))
     xq = np.array([1.05 * HI, 1.05 * LO, [0.9, -0.9, 0.0, 0.2, -0.85, 0.81]])
-    u = sg.eval_feedback(S, cuda(xq)).cpu().numpy()
+    u = sg.eval_feedback(S, cuda(xq), mode=mode).cpu().numpy()
     ref = ointerp.eval_surplus(og, ointerp.surpluses(og, f), xq)
     assert rel(u, ref) <= 1e-10
+
+
+def test_eval_df32_agrees_with_fp64_everywhere():
+    """Pair-of-floats evaluation against the FP64 kernel on every query of a
+    level-4 batch (mixed distribution), 1e-12 relative to the largest value."""
+    g = sg.Grid(6, 4, LO, HI)
+    f = np.random.default_rng(12).standard_normal((g.M, 3))
+    S = sg.Surplus(g, cuda(f))
+    xq = cuda(synth.mixed_queries(200_000, LO, HI, seed=13))
+    a = sg.eval_feedback(S, xq, mode=sg.EVAL_DF32)
+    b = sg.eval_feedback(S, xq, mode=sg.EVAL_FP64)
+    assert ((a - b).abs().max() / b.abs().max()).item() <= 1e-12
 
 
 def test_eval_empty_and_single():
@@ -97,7 +114,8 @@ def test_eval_empty_and_single():
     assert np.allclose(u, 1.0, atol=1e-14)   # the constant is reproduced
 
 
-def test_eval_full_size_sampled():
+@pytest.mark.parametrize("mode", EVAL_MODES, ids=["fp64", "df32"])
+def test_eval_full_size_sampled(mode):
     """Level-4 grid (1457 nodes) at 1e6 mixed queries, in the launch the benchmark
     times; 256 sampled queries are recomputed by the oracle."""
     g = sg.Grid(6, 4, LO, HI)
@@ -105,7 +123,7 @@ def test_eval_full_size_sampled():
     f = np.random.default_rng(4).standard_normal((og.M, 3))
     S = sg.Surplus(g, cuda(f))
     xq = synth.mixed_queries(1_000_000, LO, HI, seed=1)
-    u = sg.eval_feedback(S, cuda(xq)).cpu().numpy()
+    u = sg.eval_feedback(S, cuda(xq), mode=mode).cpu().numpy()
     idx = np.random.default_rng(5).choice(xq.shape[0], 256, replace=False)
     w = ointerp.surpluses(og, f)
     ref = ointerp.eval_surplus(og, w, xq[idx])
