@@ -247,7 +247,8 @@ def gpu_arm(args):
         g = sg.Grid(D, LEVEL, lo, hi)
         if events:
             events[1].record(stream)
-        res = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=prec, workspace=ws, n_max=n_max)
+        res = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=prec, workspace=ws, n_max=n_max,
+                            persistent=args.persistent)
         if events:
             events[2].record(stream)
         S = sg.Surplus(g, res["u0"])
@@ -382,6 +383,7 @@ def gpu_arm(args):
         "config": {"workload": WORKLOAD, "nodes": M, "grid_level": LEVEL, "d": D,
                    "horizons": "T in {10,20,40}, N = 6.4 T", "queries": N_QUERIES, "tol": TOL,
                    "precision": args.precision, "eval": args.eval,
+                   "solve_form": "persistent" if args.persistent else "launch-per-phase",
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"{world} independent instance(s), no collective"},
         "feedback_evals_per_s": N_QUERIES / (phase_ms["eval"] / 1e3),
@@ -440,6 +442,8 @@ def roofline(kt, iters, N_h, M, prec):
         "k_abd" + suffix: ("alu", flops_abd_interval() * int_units, peak_lin, "TFLOP/s"),
         "k_abd_reg" + suffix: ("alu", flops_abd_interval() * int_units, peak_lin, "TFLOP/s"),
         "k_recover" + suffix: ("alu", flops_recover_interval() * int_units, peak_lin, "TFLOP/s"),
+        "k_newton_persistent" + suffix: ("alu", (flops_condense_interval() + flops_abd_interval()
+                                                  + flops_recover_interval()) * int_units, peak_lin, "TFLOP/s"),
         "k_point" + suffix: ("hbm", bytes_point(tsize) * pt_units, None, "GB/s"),
         "k_eval_fp64": ("alu", flops_eval_query(M, 3) * N_QUERIES, PEAK_FP64_TFLOPS, "TFLOP/s"),
         "k_eval_df32": ("alu", flops_eval_query_df32(M, 3) * N_QUERIES, PEAK_FP32_TFLOPS, "TFLOP/s"),
@@ -494,6 +498,7 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--eval", choices=["df32", "fp64", "tf32x3"], default="df32")
+    ap.add_argument("--persistent", type=int, default=1, help="1: persistent batched solve form")
     ap.add_argument("--cpu-nodes", type=int, default=100)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")

@@ -102,6 +102,16 @@ typedef struct sg_solve_opts {
   int32_t precision;   /* SG_PREC_FP64 or SG_PREC_MIXED                          */
   int32_t damping;     /* 1: Armijo backtracking alpha = 1, 1/2, ..., 2^-10;
                           0: full Newton steps                                  */
+  int32_t persistent;  /* 0: one launch per Newton phase, the host reads a counter
+                          per iteration and line-search trial (the call returns
+                          when all nodes are done);
+                          1: batched persistent form: one warp per node runs the
+                          whole Newton iteration, nodes taken from a device queue
+                          (converged nodes retire and the warp takes the next);
+                          no host round trip, but the call still synchronises
+                          `stream` before returning                              */
+  int32_t blocks_per_sm; /* persistent form: cap on resident 128-thread blocks per
+                          SM (0 = as many as fit); picked by sg_autotune_solve    */
   int32_t _pad;
 } sg_solve_opts;
 

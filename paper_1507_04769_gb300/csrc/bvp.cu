@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "bvp_kernels.cuh"
+#include "bvp_persistent.cuh"
 #include "common.cuh"
 #include "diag.cuh"
 
@@ -148,6 +149,27 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
     SG_CUDA_TRY(cudaFuncSetAttribute(k_condense_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(cond_smem)));
   }
+  if (a.persistent) {
+    // one warp per node, nodes from a device queue, no host round trip
+    const int smem = 4 * persist_smem_per_warp<T>();
+    SG_CUDA_TRY(cudaFuncSetAttribute(k_newton_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    SG_CUDA_TRY(cudaGetDevice(&dev));
+    SG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton_persistent<T>, 128, smem));
+    if (per_sm < 1) per_sm = 1;
+    if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
+    const int64_t want = ceil_div(a.n, 4);
+    const unsigned grid = static_cast<unsigned>(want < int64_t(sms) * per_sm ? want : int64_t(sms) * per_sm);
+    SG_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), st));
+    SG_TIMED("k_init", st, (k_init<<<gp, 128, 0, st>>>(a, w)));
+    SG_TIMED(kname<T>("k_newton_persistent"), st, (k_newton_persistent<T><<<grid, 128, smem, st>>>(a, w)));
+    SG_TIMED("k_outputs", st, (k_outputs<<<gnode_warp, 128, 0, st>>>(a, w, lambda0, u0, V, status, iters)));
+    if (Yout) SG_TIMED("k_copy_Y", st, (k_copy_Y<<<gp, 128, 0, st>>>(a, w, Yout)));
+    SG_LAUNCH_CHECK("persistent solve");
+    if (a.sync_at_end) SG_CUDA_TRY(cudaStreamSynchronize(st));
+    return SG_OK;
+  }
   int h_cnt[2] = {0, 0};
   auto read_counters = [&]() -> int {
     cudaError_t e = cudaMemcpyAsync(h_cnt, w.counters, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -222,7 +244,7 @@ extern "C" int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t
     return fail(SG_EINVAL, "sg_solve_bvps: n_max_intervals must be 1..65536");
   if (!d_x0 || !d_T || !d_N || !d_work || !d_lambda0 || !d_u0 || !d_V || !d_status || !d_iters)
     return fail(SG_EINVAL, "sg_solve_bvps: null device pointer");
-  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0};
+  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0};
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iter < 0) return fail(SG_EINVAL, "sg_solve_bvps: bad tol or max_iter");
   if (o.precision != SG_PREC_FP64 && o.precision != SG_PREC_MIXED)
@@ -242,6 +264,9 @@ extern "C" int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t
   a.tol = o.tol;
   a.max_iter = o.max_iter;
   a.damping = o.damping;
+  a.persistent = o.persistent;
+  a.blocks_per_sm = o.blocks_per_sm;
+  a.sync_at_end = 1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (o.precision == SG_PREC_MIXED) {
     Workspace w = carve(d_work, n, n_max_intervals, sizeof(float));
@@ -296,7 +321,7 @@ extern "C" int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, 
     return fail(SG_EINVAL, "sg_solve_bvps_static: n_max_intervals must be 1..65536");
   if (!d_x0 || !d_T || !d_N || !d_lambda0 || !d_u0 || !d_V || !d_status || !d_iters)
     return fail(SG_EINVAL, "sg_solve_bvps_static: null device pointer");
-  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0};
+  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0};
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iter < 0) return fail(SG_EINVAL, "sg_solve_bvps_static: bad tol or max_iter");
   if (o.precision != SG_PREC_FP64 && o.precision != SG_PREC_MIXED)
@@ -320,6 +345,9 @@ extern "C" int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, 
   a.tol = o.tol;
   a.max_iter = o.max_iter;
   a.damping = o.damping;
+  a.persistent = o.persistent;
+  a.blocks_per_sm = o.blocks_per_sm;
+  a.sync_at_end = 1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // Every region the solver reads is written first in this call (k_init sets the
   // iterate, the corrections and the per-node state; the counters are zeroed

@@ -86,6 +86,9 @@ struct SolveArgs {
   double tol;
   int max_iter;
   int damping;
+  int persistent;      // one warp per node from a device queue (bvp_persistent.cuh)
+  int blocks_per_sm;   // cap on resident 4-warp blocks per SM for the persistent form (0 = occupancy)
+  int sync_at_end;
 };
 
 __host__ __device__ __forceinline__ int64_t npts(int Nmax) { return 3 * int64_t(Nmax) + 1; }
@@ -334,15 +337,9 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
 // other row updates itself in registers.  The pivot rows (in pivot order) are
 // stored for the stage recovery; the stage-4 rows end up holding the
 // condensed block row in columns 24..48.
-__global__ void __launch_bounds__(128) k_condense_reg(SolveArgs a, Workspace w) {
-  const int lane = threadIdx.x & 31;
-  const int64_t wid = blockIdx.x * int64_t(4) + (threadIdx.x >> 5);
-  if (wid >= a.n * a.Nmax) return;
-  const int64_t node = wid / a.Nmax;
-  const int i = static_cast<int>(wid % a.Nmax);
-  if (!w.ns[node].active) return;
-  const int N = a.N[node];
-  if (i >= N) return;
+__device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const Workspace& w, int64_t node,
+                                                      int i, int N, int lane) {
+  const int64_t wid = node * a.Nmax + i;
   const float hf = static_cast<float>(a.T[node]) / static_cast<float>(N);
   const int64_t pbase = node * npts(a.Nmax) + 3 * int64_t(i);
   const float* J = static_cast<const float*>(w.Jm) + pbase * 144;
@@ -429,22 +426,26 @@ __global__ void __launch_bounds__(128) k_condense_reg(SolveArgs a, Workspace w) 
   }
 }
 
-// Shared-memory FP64 form (used by the FP64 solve): the 36 x 49 system of one
-// interval in shared memory, one warp per interval, elimination of the first
-// 24 columns with partial pivoting over all 36 rows (warp_eliminate).
-constexpr int kCondWarps = 4;
-__global__ void __launch_bounds__(32 * kCondWarps) k_condense_smem(SolveArgs a, Workspace w) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t wid = blockIdx.x * int64_t(kCondWarps) + warp;
+__global__ void __launch_bounds__(128) k_condense_reg(SolveArgs a, Workspace w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = blockIdx.x * int64_t(4) + (threadIdx.x >> 5);
   if (wid >= a.n * a.Nmax) return;
   const int64_t node = wid / a.Nmax;
   const int i = static_cast<int>(wid % a.Nmax);
   if (!w.ns[node].active) return;
   const int N = a.N[node];
   if (i >= N) return;
+  condense_interval_reg(a, w, node, i, N, lane);
+}
+
+// Shared-memory FP64 form (used by the FP64 solve): the 36 x 49 system of one
+// interval in shared memory, one warp per interval, elimination of the first
+// 24 columns with partial pivoting over all 36 rows (warp_eliminate).
+constexpr int kCondWarps = 4;
+__device__ __forceinline__ void condense_interval_smem(const SolveArgs& a, const Workspace& w, int64_t node,
+                                                       int i, int N, int lane, double* M) {
+  const int64_t wid = node * a.Nmax + i;
   const double h = a.T[node] / N;
-  double* M = reinterpret_cast<double*>(smem_raw) + warp * (36 * kCols);
   const int64_t pbase = node * npts(a.Nmax) + 3 * int64_t(i);
   const double* J = static_cast<const double*>(w.Jm) + pbase * 144;
   const double* res = static_cast<const double*>(w.Res) + wid * kResRows;
@@ -486,6 +487,20 @@ __global__ void __launch_bounds__(32 * kCondWarps) k_condense_smem(SolveArgs a, 
     const int r = e / 25, c = e % 25;
     cond[r * kBlkLd + c] = M[(24 + r) * kCols + 24 + c];
   }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(32 * kCondWarps) k_condense_smem(SolveArgs a, Workspace w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t wid = blockIdx.x * int64_t(kCondWarps) + warp;
+  if (wid >= a.n * a.Nmax) return;
+  const int64_t node = wid / a.Nmax;
+  const int i = static_cast<int>(wid % a.Nmax);
+  if (!w.ns[node].active) return;
+  const int N = a.N[node];
+  if (i >= N) return;
+  condense_interval_smem(a, w, node, i, N, lane, reinterpret_cast<double*>(smem_raw) + warp * (36 * kCols));
 }
 
 // ---------------------------------------------------------------- staircase
@@ -497,12 +512,8 @@ __global__ void __launch_bounds__(32 * kCondWarps) k_condense_smem(SolveArgs a, 
 // 0..11 while the current panel is eliminated.  The lambda(T) rows close the
 // system; back substitution then runs from the last mesh point to the first.
 template <typename T>
-__global__ void __launch_bounds__(128) k_abd_reg(SolveArgs a, Workspace w) {
-  const int lane = threadIdx.x & 31;
-  const int64_t node = blockIdx.x * int64_t(4) + (threadIdx.x >> 5);
-  if (node >= a.n) return;
-  if (!w.ns[node].active) return;
-  const int N = a.N[node];
+__device__ __forceinline__ bool abd_node_reg(const SolveArgs& a, const Workspace& w, int64_t node, int N,
+                                             int lane) {
   const int64_t pb = node * npts(a.Nmax);
   const double* Y = w.Y + pb * 12;
   const double* x0 = a.x0 + node * 6;
@@ -620,21 +631,24 @@ __global__ void __launch_bounds__(128) k_abd_reg(SolveArgs a, Workspace w) {
 #pragma unroll
     for (int c = 0; c < 25; ++c) row[c] = pre[c];
   }
+  return ok;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_abd_reg(SolveArgs a, Workspace w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t node = blockIdx.x * int64_t(4) + (threadIdx.x >> 5);
+  if (node >= a.n) return;
+  if (!w.ns[node].active) return;
+  const bool ok = abd_node_reg<T>(a, w, node, a.N[node], lane);
   if (!ok && lane == 0) w.ns[node].singular = 1;
 }
 
 // Interior-stage corrections from the stored condensation pivot rows.
 template <typename T>
-__global__ void k_recover(SolveArgs a, Workspace w) {
-  __shared__ __align__(16) T rows_s[4][kRec];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t wid = blockIdx.x * int64_t(4) + warp;
-  if (wid >= a.n * a.Nmax) return;
-  const int64_t node = wid / a.Nmax;
-  const int i = static_cast<int>(wid % a.Nmax);
-  if (!w.ns[node].active) return;
-  if (i >= a.N[node]) return;
-  T* U = rows_s[warp];
+__device__ __forceinline__ void recover_interval(const SolveArgs& a, const Workspace& w, int64_t node, int i,
+                                                 int lane, T* U) {
+  const int64_t wid = node * a.Nmax + i;
   const T* rec = static_cast<const T*>(w.Rec) + wid * kRec;
   for (int e = lane; e < kRec; e += 32) U[e] = rec[e];
   double* D = w.D + (node * npts(a.Nmax) + 3 * int64_t(i)) * 12;
@@ -650,6 +664,20 @@ __global__ void k_recover(SolveArgs a, Workspace w) {
   }
   const T x = warp_backsolve<T, 24>(U, kRecLd, acc, lane);
   if (lane < 24) D[12 + lane] = double(x);   // points 3i+1 and 3i+2 are contiguous
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void k_recover(SolveArgs a, Workspace w) {
+  __shared__ __align__(16) T rows_s[4][kRec];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t wid = blockIdx.x * int64_t(4) + warp;
+  if (wid >= a.n * a.Nmax) return;
+  const int64_t node = wid / a.Nmax;
+  const int i = static_cast<int>(wid % a.Nmax);
+  if (!w.ns[node].active) return;
+  if (i >= a.N[node]) return;
+  recover_interval<T>(a, w, node, i, lane, rows_s[warp]);
 }
 
 // ---------------------------------------------------------------- update

@@ -33,7 +33,8 @@ class Problem(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
-                ("damping", C.c_int32), ("_pad", C.c_int32)]
+                ("damping", C.c_int32), ("persistent", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("_pad", C.c_int32)]
 
 
 class SGError(RuntimeError):
@@ -160,7 +161,8 @@ def workspace_bytes(n: int, n_max: int, precision: int = PREC_FP64) -> int:
 
 def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=50,
                precision=PREC_FP64, damping=True, n_max=None, return_Y=False,
-               workspace: torch.Tensor | None = None, stream=None):
+               workspace: torch.Tensor | None = None, persistent=False, blocks_per_sm=0,
+               stream=None):
     """sg_solve_bvps on device tensors.  x0 (n, 6) f64; T (n,) f64; N (n,) int32."""
     x0 = _dev(x0, torch.float64).reshape(-1, 6)
     n = x0.shape[0]
@@ -180,7 +182,8 @@ def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=5
         "iters": torch.empty((n,), dtype=torch.int32, device=dev),
     }
     Y = torch.zeros((n, 3 * n_max + 1, 12), dtype=torch.float64, device=dev) if return_Y else None
-    opts = SolveOpts(tol=tol, max_iter=max_iter, precision=precision, damping=int(bool(damping)))
+    opts = SolveOpts(tol=tol, max_iter=max_iter, precision=precision, damping=int(bool(damping)),
+                     persistent=int(bool(persistent)), blocks_per_sm=int(blocks_per_sm))
     _check(LIB.sg_solve_bvps(C.byref(problem), _ptr(x0), n, _ptr(T), _ptr(N), n_max, C.byref(opts),
                              _ptr(workspace), workspace.numel(), _ptr(out["lambda0"]), _ptr(out["u0"]),
                              _ptr(out["V"]), _ptr(out["status"]), _ptr(out["iters"]),

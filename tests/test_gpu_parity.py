@@ -177,11 +177,15 @@ def att_case():
     return params, X0, T, N, _oracle(params, X0, T, N)
 
 
-@pytest.mark.parametrize("prec", [sg.PREC_FP64, sg.PREC_MIXED])
-def test_attitude_matches_oracle(att_case, prec):
+FORMS = [(sg.PREC_FP64, False), (sg.PREC_MIXED, False), (sg.PREC_FP64, True), (sg.PREC_MIXED, True)]
+FORM_IDS = ["fp64", "mixed", "fp64-persistent", "mixed-persistent"]
+
+
+@pytest.mark.parametrize("prec,persistent", FORMS, ids=FORM_IDS)
+def test_attitude_matches_oracle(att_case, prec, persistent):
     params, X0, T, N, (lam, u, V, _) = att_case
     res = sg.solve_bvps(sg.problem_from(params), cuda(X0), cuda(T), cuda(N, torch.int32),
-                        tol=1e-12, precision=prec)
+                        tol=1e-12, precision=prec, persistent=persistent)
     assert np.all(res["status"].cpu().numpy() == sg.CONVERGED)
     assert rel(res["lambda0"].cpu().numpy(), lam) <= 1e-8
     assert rel(res["u0"].cpu().numpy(), u) <= 1e-8
@@ -212,18 +216,32 @@ def test_attitude_oracle_solution_trajectory(att_case):
         assert rel(Y[i, :3 * N[i] + 1], ref) <= 1e-8
 
 
-def test_batch_independence_bitwise(att_case):
+@pytest.mark.parametrize("prec,persistent", FORMS, ids=FORM_IDS)
+def test_batch_independence_bitwise(att_case, prec, persistent):
     """Each node's result is the same alone and inside a batch (Section 3: no
     communication between nodes)."""
     params, X0, T, N, _ = att_case
     prob = sg.problem_from(params)
-    full = sg.solve_bvps(prob, cuda(X0), cuda(T), cuda(N, torch.int32), n_max=128)
+    kw = dict(n_max=128, precision=prec, persistent=persistent)
+    full = sg.solve_bvps(prob, cuda(X0), cuda(T), cuda(N, torch.int32), **kw)
     perm = np.random.default_rng(0).permutation(X0.shape[0])
-    shuf = sg.solve_bvps(prob, cuda(X0[perm]), cuda(T[perm]), cuda(N[perm], torch.int32), n_max=128)
+    shuf = sg.solve_bvps(prob, cuda(X0[perm]), cuda(T[perm]), cuda(N[perm], torch.int32), **kw)
     for key in ("lambda0", "u0", "V", "iters"):
         assert torch.equal(full[key][perm], shuf[key])
-    alone = sg.solve_bvps(prob, cuda(X0[2:3]), cuda(T[2:3]), cuda(N[2:3], torch.int32), n_max=128)
+    alone = sg.solve_bvps(prob, cuda(X0[2:3]), cuda(T[2:3]), cuda(N[2:3], torch.int32), **kw)
     assert torch.equal(alone["lambda0"][0], full["lambda0"][2])
+
+
+def test_persistent_and_phase_forms_agree(att_case):
+    """Both forms take the same Newton steps (same residual, elimination and
+    line search), so they agree to rounding at every tolerance."""
+    params, X0, T, N, _ = att_case
+    prob = sg.problem_from(params)
+    for prec in (sg.PREC_FP64, sg.PREC_MIXED):
+        a = sg.solve_bvps(prob, cuda(X0), cuda(T), cuda(N, torch.int32), precision=prec)
+        b = sg.solve_bvps(prob, cuda(X0), cuda(T), cuda(N, torch.int32), precision=prec, persistent=True)
+        assert torch.equal(a["status"], b["status"])
+        assert rel(b["lambda0"].cpu().numpy(), a["lambda0"].cpu().numpy()) <= 1e-8
 
 
 def test_edge_cases_and_bad_input():
@@ -258,9 +276,9 @@ def test_full_size_batched_solve_sampled():
     g = sg.Grid(6, 4, LO, HI)
     og = ogrid.Grid(6, 4, LO, HI)
     T, N = synth.mixed_horizons(g.M, seed=2)
-    for prec in (sg.PREC_FP64, sg.PREC_MIXED):
+    for prec, persistent in FORMS:
         res = sg.solve_bvps(sg.problem_from(params), g.coords, cuda(T), cuda(N, torch.int32), tol=1e-12,
-                            precision=prec)
+                            precision=prec, persistent=persistent)
         st = res["status"].cpu().numpy()
         assert np.all(st == sg.CONVERGED), np.bincount(st)
         idx = np.random.default_rng(7).choice(g.M, 6, replace=False)

@@ -38,7 +38,7 @@ def _static_solve(problem, x0, T, N, n_max, precision):
            "V": torch.empty((n,), dtype=torch.float64, device=dev),
            "status": torch.empty((n,), dtype=torch.int32, device=dev),
            "iters": torch.empty((n,), dtype=torch.int32, device=dev)}
-    opts = sg.SolveOpts(tol=1e-12, max_iter=50, precision=precision, damping=1)
+    opts = sg.SolveOpts(tol=1e-12, max_iter=50, precision=precision, damping=1, persistent=0)
     p = lambda t: C.c_void_p(t.data_ptr())
     rc = sg.LIB.sg_solve_bvps_static(C.byref(problem), p(x0), n, p(T), p(N), n_max, C.byref(opts),
                                      p(out["lambda0"]), p(out["u0"]), p(out["V"]), p(out["status"]),
