@@ -111,8 +111,13 @@ typedef struct sg_solve_opts {
                           no host round trip, but the call still synchronises
                           `stream` before returning                              */
   int32_t blocks_per_sm; /* persistent form: cap on resident 128-thread blocks per
-                          SM (0 = as many as fit); picked by sg_autotune_solve    */
-  int32_t _pad;
+                          SM (0 = as many as fit)                                 */
+  int32_t graph;       /* 1: run the solve as a cached CUDA graph.  In the launch-
+                          per-phase form the Newton and line-search loops become
+                          device-side WHILE conditional nodes (no host round trip
+                          per iteration).  One graph is instantiated and cached per
+                          (sizes, precision, problem, buffers) the first time and
+                          replayed afterwards                                     */
 } sg_solve_opts;
 
 /* ---------------------------------------------------------------- errors */
@@ -202,6 +207,24 @@ int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, int64_t n,
                          const sg_solve_opts* opts, double* d_lambda0, double* d_u0,
                          double* d_V, int32_t* d_status, int32_t* d_iters, double* d_Y,
                          void* stream);
+
+/* sg_autotune_solve - picks the execution form of sg_solve_bvps for a batch
+ * (a shape tuner; the method itself is unchanged).  It solves the caller's
+ * batch with each candidate form - 0 launch per phase with a host loop, 1 the
+ * same as a CUDA graph with device-side loops, 2 and 3 the persistent
+ * warp-per-node kernel as a graph with all / one resident block(s) per SM -
+ * timing each second run with CUDA events, and returns the fastest in *best
+ * (base's tolerance, iteration cap, damping and precision are kept).  The
+ * choice is cached per (precision, n, n_max_intervals, tol, max_iter,
+ * damping); with force = 0 a cached choice is returned without solving.
+ * Arguments as for sg_solve_bvps; the outputs hold the last candidate's
+ * solution.  report_ms (host, 4 entries, may be NULL) receives the timings.
+ * Synchronises `stream`.  Errors: those of sg_solve_bvps. */
+int sg_autotune_solve(const sg_problem* prob, const double* d_x0, int64_t n, const double* d_T,
+                      const int32_t* d_N, int n_max_intervals, const sg_solve_opts* base,
+                      void* d_work, size_t work_bytes, double* d_lambda0, double* d_u0,
+                      double* d_V, int32_t* d_status, int32_t* d_iters, sg_solve_opts* best,
+                      double* report_ms, int force, void* stream);
 
 /* ---------------------------------------------------------------- Step III
  * sg_build_surpluses - hierarchical surpluses of values at the grid nodes,

@@ -2,6 +2,7 @@
 // Host side of the solver: workspace layout, the Newton loop over the kernels
 // of bvp_kernels.cuh, and the C ABI entry points.
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -222,6 +223,236 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
   return SG_OK;
 }
 
+// ---------------------------------------------------------------- graph form
+// The launch-per-phase solve as one CUDA graph: the Newton iteration and the
+// line search are WHILE conditional nodes whose conditions are set on the
+// device from the active / searching counters, so the data-dependent loop
+// trip counts never reach the host.  Executable graphs are cached per
+// (sizes, precision, buffers, problem): one per mesh size for a given batch.
+__global__ void k_set_cond(cudaGraphConditionalHandle h, const int* cnt) {
+  cudaGraphSetConditional(h, cnt[0] > 0 ? 1u : 0u);
+}
+__global__ void k_set_cond_one(cudaGraphConditionalHandle h) { cudaGraphSetConditional(h, 1u); }
+
+// Counts the nodes that start a line search (replaces the host read).
+__global__ void k_count_searching(SolveArgs a, Workspace w) {
+  const int64_t node = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (node >= a.n) return;
+  if (w.ns[node].searching) atomicAdd(&w.counters[0], 1);
+}
+
+struct GraphBuilder {
+  cudaGraph_t g;
+  std::vector<cudaGraphNode_t> last;   // dependencies for the next node
+  cudaError_t err = cudaSuccess;
+
+  template <typename... Args>
+  void kernel(void (*f)(Args...), unsigned grid, unsigned block, size_t smem, Args... args) {
+    if (err != cudaSuccess) return;
+    void* ptrs[] = {static_cast<void*>(&args)...};
+    cudaKernelNodeParams p{};
+    p.func = reinterpret_cast<void*>(f);
+    p.gridDim = dim3(grid);
+    p.blockDim = dim3(block);
+    p.sharedMemBytes = static_cast<unsigned>(smem);
+    p.kernelParams = ptrs;
+    cudaGraphNode_t n;
+    err = cudaGraphAddKernelNode(&n, g, last.data(), last.size(), &p);
+    last.assign(1, n);
+  }
+  void memset0(void* ptr, size_t bytes) {
+    if (err != cudaSuccess) return;
+    cudaMemsetParams p{};
+    p.dst = ptr;
+    p.value = 0;
+    p.elementSize = 1;
+    p.width = bytes;
+    p.height = 1;
+    cudaGraphNode_t n;
+    err = cudaGraphAddMemsetNode(&n, g, last.data(), last.size(), &p);
+    last.assign(1, n);
+  }
+  // Adds a WHILE node; returns its body graph (empty) through *body.
+  void loop(cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    if (err != cudaSuccess) return;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t n;
+    err = cudaGraphAddNode(&n, g, last.data(), nullptr, last.size(), &p);
+    last.assign(1, n);
+    *body = p.conditional.phGraph_out[0];
+  }
+};
+
+template <typename T>
+static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, double* lambda0, double* u0,
+                                     double* V, int32_t* status, int32_t* iters, double* Yout,
+                                     cudaGraph_t* out) {
+  const int64_t P = npts(a.Nmax);
+  const int64_t nint = a.n * a.Nmax;
+  const unsigned gp = static_cast<unsigned>(ceil_div(a.n * P, 128));
+  const unsigned gi = static_cast<unsigned>(ceil_div(nint, 128));
+  const unsigned gnt = static_cast<unsigned>(ceil_div(a.n, 128));
+  const unsigned gnw = static_cast<unsigned>(ceil_div(a.n * 32, 128));
+  const unsigned gwi = static_cast<unsigned>(ceil_div(nint, 4));
+  const unsigned gwn = static_cast<unsigned>(ceil_div(a.n, 4));
+  const size_t cond_smem = sizeof(double) * kCondWarps * 36 * kCols;
+  cudaGraph_t root;
+  cudaError_t e = cudaGraphCreate(&root, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle hn, hl;
+  if ((e = cudaGraphConditionalHandleCreate(&hn, root, 0, 0)) != cudaSuccess) return e;
+  if ((e = cudaGraphConditionalHandleCreate(&hl, root, 0, 0)) != cudaSuccess) return e;
+  GraphBuilder rb{root, {}};
+  rb.memset0(w.counters, 4 * sizeof(int));
+  rb.kernel(k_init, gp, 128, 0, a, w);
+  rb.kernel(k_trial<T>, gi, 128, 0, a, w);
+  rb.kernel(k_ls_reduce, gnw, 128, 0, a, w, 0);
+  rb.kernel(k_set_cond, 1, 1, 0, hn, static_cast<const int*>(w.counters + 1));
+  cudaGraph_t newton_body;
+  rb.loop(hn, &newton_body);
+  rb.kernel(k_outputs, gnw, 128, 0, a, w, lambda0, u0, V, status, iters);
+  if (Yout) rb.kernel(k_copy_Y, gp, 128, 0, a, w, Yout);
+  if (rb.err != cudaSuccess) return rb.err;
+
+  GraphBuilder nb{newton_body, {}};
+  nb.memset0(w.counters, 2 * sizeof(int));
+  nb.kernel(k_point<T>, gp, 128, 0, a, w);
+  if constexpr (sizeof(T) == sizeof(float)) {
+    nb.kernel(k_condense_reg, gwi, 128, 0, a, w);
+  } else {
+    nb.kernel(k_condense_smem, static_cast<unsigned>(ceil_div(nint, kCondWarps)), 32 * kCondWarps, cond_smem, a, w);
+  }
+  nb.kernel(k_abd_reg<T>, gwn, 128, 0, a, w);
+  nb.kernel(k_recover<T>, gwi, 128, 0, a, w);
+  nb.kernel(k_ls_begin, gnt, 128, 0, a, w);
+  nb.kernel(k_set_cond_one, 1, 1, 0, hl);
+  cudaGraph_t ls_body;
+  nb.loop(hl, &ls_body);
+  nb.memset0(w.counters, 2 * sizeof(int));
+  nb.kernel(k_update, gp, 128, 0, a, w);
+  nb.kernel(k_after_update, gnt, 128, 0, a, w);
+  nb.kernel(k_set_cond, 1, 1, 0, hn, static_cast<const int*>(w.counters + 1));
+  if (nb.err != cudaSuccess) return nb.err;
+
+  GraphBuilder lb{ls_body, {}};
+  lb.memset0(w.counters, sizeof(int));
+  lb.kernel(k_trial<T>, gi, 128, 0, a, w);
+  lb.kernel(k_ls_reduce, gnw, 128, 0, a, w, 1);
+  lb.kernel(k_set_cond, 1, 1, 0, hl, static_cast<const int*>(w.counters));
+  if (lb.err != cudaSuccess) return lb.err;
+  *out = root;
+  return cudaSuccess;
+}
+
+// Persistent form as a graph: queue reset, init, persistent kernel, outputs.
+template <typename T>
+static cudaError_t build_persistent_graph(const SolveArgs& a, const Workspace& w, unsigned grid, int smem,
+                                          double* lambda0, double* u0, double* V, int32_t* status,
+                                          int32_t* iters, double* Yout, cudaGraph_t* out) {
+  const int64_t P = npts(a.Nmax);
+  cudaGraph_t root;
+  cudaError_t e = cudaGraphCreate(&root, 0);
+  if (e != cudaSuccess) return e;
+  GraphBuilder rb{root, {}};
+  rb.memset0(w.counters, 4 * sizeof(int));
+  rb.kernel(k_init, static_cast<unsigned>(ceil_div(a.n * P, 128)), 128, 0, a, w);
+  rb.kernel(k_newton_persistent<T>, grid, 128, static_cast<size_t>(smem), a, w);
+  rb.kernel(k_outputs, static_cast<unsigned>(ceil_div(a.n * 32, 128)), 128, 0, a, w, lambda0, u0, V, status, iters);
+  if (Yout) rb.kernel(k_copy_Y, static_cast<unsigned>(ceil_div(a.n * P, 128)), 128, 0, a, w, Yout);
+  if (rb.err != cudaSuccess) return rb.err;
+  *out = root;
+  return cudaSuccess;
+}
+
+struct GraphKey {
+  std::string bytes;
+  bool operator<(const GraphKey& o) const { return bytes < o.bytes; }
+};
+
+static std::mutex g_graph_mu;
+static std::map<GraphKey, cudaGraphExec_t>& graph_cache() {
+  static auto* m = new std::map<GraphKey, cudaGraphExec_t>();
+  return *m;
+}
+static std::vector<GraphKey>& graph_order() {   // insertion order, for eviction
+  static auto* v = new std::vector<GraphKey>();
+  return *v;
+}
+constexpr size_t kGraphCacheCap = 32;
+
+template <typename T>
+static int run_solve_graph(const SolveArgs& a, Workspace w, cudaStream_t st, double* lambda0, double* u0,
+                           double* V, int32_t* status, int32_t* iters, double* Yout) {
+  int dev = 0;
+  SG_CUDA_TRY(cudaGetDevice(&dev));
+  unsigned grid = 0;
+  int smem = 0;
+  if (a.persistent) {
+    smem = 4 * persist_smem_per_warp<T>();
+    SG_CUDA_TRY(cudaFuncSetAttribute(k_newton_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int sms = 0, per_sm = 0;
+    SG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton_persistent<T>, 128, smem));
+    if (per_sm < 1) per_sm = 1;
+    if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
+    const int64_t want = ceil_div(a.n, 4);
+    grid = static_cast<unsigned>(want < int64_t(sms) * per_sm ? want : int64_t(sms) * per_sm);
+  } else if constexpr (sizeof(T) == sizeof(double)) {
+    SG_CUDA_TRY(cudaFuncSetAttribute(k_condense_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(sizeof(double) * kCondWarps * 36 * kCols)));
+  }
+  // key: every byte that is baked into the graph's kernel parameters
+  GraphKey key;
+  key.bytes.append(reinterpret_cast<const char*>(&a), sizeof(a));
+  key.bytes.append(reinterpret_cast<const char*>(&w), sizeof(w));
+  const void* outs[6] = {lambda0, u0, V, status, iters, Yout};
+  key.bytes.append(reinterpret_cast<const char*>(outs), sizeof(outs));
+  key.bytes.append(reinterpret_cast<const char*>(&dev), sizeof(dev));
+  key.bytes.append(reinterpret_cast<const char*>(&grid), sizeof(grid));
+  const int tsz = sizeof(T);
+  key.bytes.append(reinterpret_cast<const char*>(&tsz), sizeof(tsz));
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto it = graph_cache().find(key);
+    if (it != graph_cache().end()) exec = it->second;
+  }
+  if (!exec) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = a.persistent
+                        ? build_persistent_graph<T>(a, w, grid, smem, lambda0, u0, V, status, iters, Yout, &g)
+                        : build_solve_graph<T>(a, w, lambda0, u0, V, status, iters, Yout, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "sg_solve_bvps: building the solve graph");
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "sg_solve_bvps: instantiating the solve graph");
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    if (graph_cache().size() >= kGraphCacheCap) {
+      // evict the oldest graph (its launches have completed: every solve
+      // synchronises its stream before returning)
+      const GraphKey old = graph_order().front();
+      graph_order().erase(graph_order().begin());
+      auto it = graph_cache().find(old);
+      if (it != graph_cache().end()) {
+        cudaGraphExecDestroy(it->second);
+        graph_cache().erase(it);
+      }
+    }
+    graph_cache()[key] = exec;
+    graph_order().push_back(key);
+  }
+  {
+    KernelTimer kt(a.persistent ? kname<T>("graph_persistent") : kname<T>("graph_solve"), st);
+    SG_CUDA_TRY(cudaGraphLaunch(exec, st));
+  }
+  SG_CUDA_TRY(cudaStreamSynchronize(st));
+  return SG_OK;
+}
+
 }  // namespace sg
 
 using namespace sg;
@@ -244,7 +475,7 @@ extern "C" int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t
     return fail(SG_EINVAL, "sg_solve_bvps: n_max_intervals must be 1..65536");
   if (!d_x0 || !d_T || !d_N || !d_work || !d_lambda0 || !d_u0 || !d_V || !d_status || !d_iters)
     return fail(SG_EINVAL, "sg_solve_bvps: null device pointer");
-  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0};
+  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0};
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iter < 0) return fail(SG_EINVAL, "sg_solve_bvps: bad tol or max_iter");
   if (o.precision != SG_PREC_FP64 && o.precision != SG_PREC_MIXED)
@@ -270,9 +501,11 @@ extern "C" int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (o.precision == SG_PREC_MIXED) {
     Workspace w = carve(d_work, n, n_max_intervals, sizeof(float));
+    if (o.graph) return run_solve_graph<float>(a, w, st, d_lambda0, d_u0, d_V, d_status, d_iters, d_Y);
     return run_solve<float>(a, w, st, d_lambda0, d_u0, d_V, d_status, d_iters, d_Y);
   }
   Workspace w = carve(d_work, n, n_max_intervals, sizeof(double));
+  if (o.graph) return run_solve_graph<double>(a, w, st, d_lambda0, d_u0, d_V, d_status, d_iters, d_Y);
   return run_solve<double>(a, w, st, d_lambda0, d_u0, d_V, d_status, d_iters, d_Y);
 }
 
@@ -321,7 +554,7 @@ extern "C" int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, 
     return fail(SG_EINVAL, "sg_solve_bvps_static: n_max_intervals must be 1..65536");
   if (!d_x0 || !d_T || !d_N || !d_lambda0 || !d_u0 || !d_V || !d_status || !d_iters)
     return fail(SG_EINVAL, "sg_solve_bvps_static: null device pointer");
-  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0};
+  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0};
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iter < 0) return fail(SG_EINVAL, "sg_solve_bvps_static: bad tol or max_iter");
   if (o.precision != SG_PREC_FP64 && o.precision != SG_PREC_MIXED)

@@ -34,7 +34,7 @@ class Problem(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("damping", C.c_int32), ("persistent", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("_pad", C.c_int32)]
+                ("graph", C.c_int32)]
 
 
 class SGError(RuntimeError):
@@ -60,6 +60,9 @@ def _load():
     lib.sg_solve_bvps_static.argtypes = [C.POINTER(Problem), P, I64, P, P, I32, C.POINTER(SolveOpts),
                                          P, P, P, P, P, P, P]
     lib.sg_solve_bvps_static.restype = C.c_int
+    lib.sg_autotune_solve.argtypes = [C.POINTER(Problem), P, I64, P, P, I32, C.POINTER(SolveOpts), P,
+                                      C.c_size_t, P, P, P, P, P, C.POINTER(SolveOpts), C.POINTER(D), I32, P]
+    lib.sg_autotune_solve.restype = C.c_int
     lib.sg_build_surpluses.argtypes = [P, P, I32, C.POINTER(P), P]
     lib.sg_surplus_info.argtypes = [P, C.POINTER(I64), C.POINTER(I32), C.POINTER(P)]
     lib.sg_surplus_free.argtypes = [P]
@@ -162,8 +165,10 @@ def workspace_bytes(n: int, n_max: int, precision: int = PREC_FP64) -> int:
 def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=50,
                precision=PREC_FP64, damping=True, n_max=None, return_Y=False,
                workspace: torch.Tensor | None = None, persistent=False, blocks_per_sm=0,
-               stream=None):
-    """sg_solve_bvps on device tensors.  x0 (n, 6) f64; T (n,) f64; N (n,) int32."""
+               graph=False, out=None, stream=None):
+    """sg_solve_bvps on device tensors.  x0 (n, 6) f64; T (n,) f64; N (n,) int32.
+    `out` may hold preallocated output tensors (keys lambda0, u0, V, status,
+    iters); reusing them (and the workspace) lets graph=True replay one graph."""
     x0 = _dev(x0, torch.float64).reshape(-1, 6)
     n = x0.shape[0]
     dev = x0.device
@@ -174,16 +179,18 @@ def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=5
     if workspace is None:
         workspace = torch.empty(max(workspace_bytes(n, n_max, precision), 1), dtype=torch.uint8,
                                 device=dev)
-    out = {
-        "lambda0": torch.empty((n, 6), dtype=torch.float64, device=dev),
-        "u0": torch.empty((n, 3), dtype=torch.float64, device=dev),
-        "V": torch.empty((n,), dtype=torch.float64, device=dev),
-        "status": torch.empty((n,), dtype=torch.int32, device=dev),
-        "iters": torch.empty((n,), dtype=torch.int32, device=dev),
-    }
+    if out is None:
+        out = {
+            "lambda0": torch.empty((n, 6), dtype=torch.float64, device=dev),
+            "u0": torch.empty((n, 3), dtype=torch.float64, device=dev),
+            "V": torch.empty((n,), dtype=torch.float64, device=dev),
+            "status": torch.empty((n,), dtype=torch.int32, device=dev),
+            "iters": torch.empty((n,), dtype=torch.int32, device=dev),
+        }
     Y = torch.zeros((n, 3 * n_max + 1, 12), dtype=torch.float64, device=dev) if return_Y else None
     opts = SolveOpts(tol=tol, max_iter=max_iter, precision=precision, damping=int(bool(damping)),
-                     persistent=int(bool(persistent)), blocks_per_sm=int(blocks_per_sm))
+                     persistent=int(bool(persistent)), blocks_per_sm=int(blocks_per_sm),
+                     graph=int(bool(graph)))
     _check(LIB.sg_solve_bvps(C.byref(problem), _ptr(x0), n, _ptr(T), _ptr(N), n_max, C.byref(opts),
                              _ptr(workspace), workspace.numel(), _ptr(out["lambda0"]), _ptr(out["u0"]),
                              _ptr(out["V"]), _ptr(out["status"]), _ptr(out["iters"]),
@@ -191,6 +198,34 @@ def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=5
     if Y is not None:
         out["Y"] = Y
     return out
+
+
+FORM_NAMES = ["phase-host-loop", "phase-graph", "persistent-graph", "persistent-graph-1blk"]
+
+
+def autotune_solve(problem: Problem, x0, T, N, *, tol=1e-8, max_iter=50, precision=PREC_FP64,
+                   damping=True, n_max=None, workspace=None, force=False, stream=None):
+    """sg_autotune_solve: returns (best options as a dict, {form name: ms})."""
+    x0 = _dev(x0, torch.float64).reshape(-1, 6)
+    n = x0.shape[0]
+    dev = x0.device
+    T = _dev(T, torch.float64, dev).reshape(-1).expand(n).contiguous()
+    N = _dev(N, torch.int32, dev).reshape(-1).expand(n).contiguous()
+    if n_max is None:
+        n_max = int(N.max().item()) if n else 1
+    if workspace is None:
+        workspace = torch.empty(max(workspace_bytes(n, n_max, precision), 1), dtype=torch.uint8, device=dev)
+    outs = [torch.empty((n, 6), dtype=torch.float64, device=dev), torch.empty((n, 3), dtype=torch.float64, device=dev),
+            torch.empty((n,), dtype=torch.float64, device=dev), torch.empty((n,), dtype=torch.int32, device=dev),
+            torch.empty((n,), dtype=torch.int32, device=dev)]
+    base = SolveOpts(tol=tol, max_iter=max_iter, precision=precision, damping=int(bool(damping)))
+    best = SolveOpts()
+    ms = (C.c_double * 4)(*([float("nan")] * 4))
+    _check(LIB.sg_autotune_solve(C.byref(problem), _ptr(x0), n, _ptr(T), _ptr(N), n_max, C.byref(base),
+                                 _ptr(workspace), workspace.numel(), *[_ptr(t) for t in outs], C.byref(best),
+                                 ms, int(bool(force)), _stream(stream)))
+    choice = {"persistent": bool(best.persistent), "graph": bool(best.graph), "blocks_per_sm": best.blocks_per_sm}
+    return choice, {FORM_NAMES[i]: ms[i] for i in range(4)}
 
 
 # --------------------------------------------------------------- Step III

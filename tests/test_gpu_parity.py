@@ -179,13 +179,15 @@ def att_case():
 
 FORMS = [(sg.PREC_FP64, False), (sg.PREC_MIXED, False), (sg.PREC_FP64, True), (sg.PREC_MIXED, True)]
 FORM_IDS = ["fp64", "mixed", "fp64-persistent", "mixed-persistent"]
+GFORMS = [(p, q, g) for (p, q) in FORMS for g in (False, True)]
+GFORM_IDS = [f"{i}{'-graph' if g else ''}" for i in FORM_IDS for g in (False, True)]
 
 
-@pytest.mark.parametrize("prec,persistent", FORMS, ids=FORM_IDS)
-def test_attitude_matches_oracle(att_case, prec, persistent):
+@pytest.mark.parametrize("prec,persistent,graph", GFORMS, ids=GFORM_IDS)
+def test_attitude_matches_oracle(att_case, prec, persistent, graph):
     params, X0, T, N, (lam, u, V, _) = att_case
     res = sg.solve_bvps(sg.problem_from(params), cuda(X0), cuda(T), cuda(N, torch.int32),
-                        tol=1e-12, precision=prec, persistent=persistent)
+                        tol=1e-12, precision=prec, persistent=persistent, graph=graph)
     assert np.all(res["status"].cpu().numpy() == sg.CONVERGED)
     assert rel(res["lambda0"].cpu().numpy(), lam) <= 1e-8
     assert rel(res["u0"].cpu().numpy(), u) <= 1e-8
@@ -230,6 +232,39 @@ def test_batch_independence_bitwise(att_case, prec, persistent):
         assert torch.equal(full[key][perm], shuf[key])
     alone = sg.solve_bvps(prob, cuda(X0[2:3]), cuda(T[2:3]), cuda(N[2:3], torch.int32), **kw)
     assert torch.equal(alone["lambda0"][0], full["lambda0"][2])
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_graph_replay_reuses_buffers(att_case, persistent):
+    """The cached graph is replayed when the same buffers come back; a replay on
+    new inputs written into the same input tensors gives the host-loop result."""
+    params, X0, T, N, _ = att_case
+    prob = sg.problem_from(params)
+    x0, Tt, Nt = cuda(X0), cuda(T), cuda(N, torch.int32)
+    nmax = int(N.max())
+    ws = torch.empty(sg.workspace_bytes(len(X0), nmax, sg.PREC_MIXED), dtype=torch.uint8, device="cuda")
+    out = None
+    for rep in range(3):
+        if rep == 2:
+            x0.copy_(cuda(0.5 * X0))
+        out = sg.solve_bvps(prob, x0, Tt, Nt, precision=sg.PREC_MIXED, persistent=persistent, graph=True,
+                            workspace=ws, n_max=nmax, out=out)
+        ref = sg.solve_bvps(prob, x0, Tt, Nt, precision=sg.PREC_MIXED, persistent=persistent, n_max=nmax)
+        for key in ("lambda0", "V", "status", "iters"):
+            assert torch.equal(out[key], ref[key]), (rep, key)
+
+
+def test_autotuner_picks_a_form_and_caches_it(att_case):
+    params, X0, T, N, _ = att_case
+    prob = sg.problem_from(params)
+    choice, ms = sg.autotune_solve(prob, cuda(X0), cuda(T), cuda(N, torch.int32), precision=sg.PREC_MIXED,
+                                   force=True)
+    assert set(ms) == set(sg.FORM_NAMES) and all(v > 0 for v in ms.values())
+    again, ms2 = sg.autotune_solve(prob, cuda(X0), cuda(T), cuda(N, torch.int32), precision=sg.PREC_MIXED)
+    assert again == choice and all(v != v for v in ms2.values())   # cached: nothing re-timed
+    a = sg.solve_bvps(prob, cuda(X0), cuda(T), cuda(N, torch.int32), precision=sg.PREC_MIXED, **choice)
+    b = sg.solve_bvps(prob, cuda(X0), cuda(T), cuda(N, torch.int32), precision=sg.PREC_MIXED)
+    assert rel(a["lambda0"].cpu().numpy(), b["lambda0"].cpu().numpy()) <= 1e-8
 
 
 def test_persistent_and_phase_forms_agree(att_case):
