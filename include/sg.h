@@ -280,6 +280,23 @@ int sg_timing_collect(int max_kernels, char* names, int name_len, double* total_
 int sg_fma_probe(int precision, void* d_scratch, size_t scratch_bytes, int blocks, int threads,
                  int iters, double* flops_per_launch, void* stream);
 
+/* ---------------------------------------------------------------- closed loop
+ * sg_simulate_closed_loop - the on-line phase of Section 3.3 run against the
+ * plant: zero-order hold as in the model predictive control of Section 5.  At
+ * t_k = k dt the control u_k = I^q(u*)(x_k) is interpolated from `s` (which
+ * must hold u* at the nodes: d = 6 states, k = 3 controls) and held while one
+ * classical RK4 step advances x' = f(x, u_k) and z' = L(x, u_k), z(0) = 0.
+ *   d_x0    ntraj x 6 initial states;  nsteps >= 0 steps of width dt > 0
+ *   mode    SG_EVAL_FP64 or SG_EVAL_DF32 (the interpolation arithmetic;
+ *           the plant and the cost are always FP64)
+ *   d_xT    ntraj x 6 final states;  d_cost ntraj accumulated costs z(T)
+ *   d_traj  NULL or ntraj x (nsteps+1) x 6 states;  d_ctrl NULL or
+ *           ntraj x nsteps x 3 held controls
+ * One warp per trajectory.  Asynchronous on `stream`.  Errors: SG_EINVAL, SG_ECUDA. */
+int sg_simulate_closed_loop(const sg_problem* prob, const sg_surplus* s, const double* d_x0,
+                            int64_t ntraj, int nsteps, double dt, int mode, double* d_xT,
+                            double* d_cost, double* d_traj, double* d_ctrl, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

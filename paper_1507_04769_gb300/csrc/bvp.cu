@@ -75,6 +75,9 @@ bool make_dev_problem(const sg_problem& in, DevProblem* out) {
         p.Kw[3 * i + j] = s / in.r;
         p.Gw[3 * i + j] = in.B[3 * j + i] * p.Jinv[j] / in.r;
       }
+    // plant input matrix J^-1 B in rows 3..5 of a 6 x 3 (rows 0..2 zero)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) p.Bu[3 * (3 + i) + j] = JB[3 * i + j];
     p.wv = in.wv;
     p.ww = in.ww;
     p.r = in.r;
@@ -89,6 +92,7 @@ bool make_dev_problem(const sg_problem& in, DevProblem* out) {
       p.QT[e] = in.QT[e];
     }
     for (int e = 0; e < 9; ++e) p.R[e] = in.R[e];
+    for (int e = 0; e < 18; ++e) p.Bu[e] = in.Blq[e];
     // G = R^-1 B' (3 x 6); K = B G (6 x 6)
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 6; ++j) {

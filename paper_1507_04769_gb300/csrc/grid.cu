@@ -66,9 +66,14 @@ void enumerate_nodes(int d, int level, std::vector<int8_t>& lev, std::vector<int
   }
 }
 
-// x^i_k = (1 - cos(k pi / 2^(i-1))) / 2 = sin^2(k pi / 2^i), exact at 0, 1/2, 1.
+// x^i_k = (1 - cos(k pi / 2^(i-1))) / 2 = sin^2(k pi / 2^i); the two ends and
+// the middle are set exactly (0, 1, 1/2), so nested points coincide exactly.
 __device__ __forceinline__ double cgl_coord(int i, int k) {
   if (i == 1) return 0.5;
+  const int n = 1 << (i - 1);
+  if (k == 0) return 0.0;
+  if (k == n) return 1.0;
+  if (2 * k == n) return 0.5;
   double s = sinpi(static_cast<double>(k) / static_cast<double>(1 << i));
   return s * s;
 }

@@ -19,6 +19,7 @@
 #include "common.cuh"
 #include "diag.cuh"
 #include "grid.cuh"
+#include "basis.cuh"
 #include "interp.cuh"
 
 namespace sg {
@@ -37,53 +38,6 @@ int function_id(int l, int kidx) {
   return off + j;
 }
 
-// All 1-D basis values at one coordinate u in [0, 1] for levels 1..L+1,
-// written to tab[id * stride].  xf holds the fine_n + 1 = 2^L + 1 points of
-// the finest set X^{L+1}.  Exact Kronecker values when u coincides with a
-// point of the level's set.
-__device__ void basis_row(double u, int level, const double* __restrict__ xf, double* tab, int stride) {
-  tab[0] = 1.0;   // a^1 = 1
-  if (level == 0) return;
-  const int fine_n = 1 << level;
-  double rinv[kMaxFine + 1];
-  int hit = -1;
-  for (int p = 0; p <= fine_n; ++p) {
-    const double diff = u - xf[p];
-    if (diff == 0.0) hit = p;
-    rinv[p] = diff == 0.0 ? 0.0 : 1.0 / diff;
-  }
-  int id = 1;
-  for (int l = 2; l <= level + 1; ++l) {
-    const int n = 1 << (l - 1);            // X^l has n + 1 points
-    const int sf = fine_n / n;             // point m of X^l is fine point m * sf
-    const bool exact = hit >= 0 && (hit % sf) == 0;
-    double denom = 0.0;
-    if (!exact) {
-      for (int m = 0; m <= n; ++m) {
-        double wm = (m & 1) ? -1.0 : 1.0;
-        if (m == 0 || m == n) wm *= 0.5;
-        denom += wm * rinv[m * sf];
-      }
-    }
-    const double inv_denom = exact ? 0.0 : 1.0 / denom;
-    // increment points of X^l: level 2 -> m = 0, n; level >= 3 -> odd m
-    const int cnt = l == 2 ? 2 : (n >> 1);
-    for (int j = 0; j < cnt; ++j) {
-      const int m = l == 2 ? j * n : 2 * j + 1;
-      double v;
-      if (exact) {
-        v = (m * sf == hit) ? 1.0 : 0.0;
-      } else {
-        double wm = (m & 1) ? -1.0 : 1.0;
-        if (m == 0 || m == n) wm *= 0.5;
-        v = wm * rinv[m * sf] * inv_denom;
-      }
-      tab[(id + j) * stride] = v;
-    }
-    id += cnt;
-  }
-}
-
 // Points of the finest set X^{L+1} on [0, 1]: x_p = (1 - cos(p pi / 2^L)) / 2
 // = sin^2(p pi / 2^(L+1)) (Eq. CGL).
 __global__ void k_fine_coords(int level, double* xf) {
@@ -92,6 +46,10 @@ __global__ void k_fine_coords(int level, double* xf) {
   if (p > fine_n) return;
   if (level == 0) {
     xf[p] = 0.5;
+    return;
+  }
+  if (p == 0 || p == fine_n || 2 * p == fine_n) {
+    xf[p] = p == 0 ? 0.0 : (p == fine_n ? 1.0 : 0.5);   // exact ends and middle
     return;
   }
   const double s = sinpi(static_cast<double>(p) / static_cast<double>(2 * fine_n));
@@ -180,7 +138,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64(EvalArgs e) {
   const int nf = e.nf;
   // tab[(dim * nf + id) * kEvalThreads + tid]
   for (int dim = 0; dim < D; ++dim) {
-    const double u = live ? (e.xq[q * D + dim] - e.lo[dim]) * e.inv_width[dim] : 0.5;
+    const double u = live ? (e.xq[q * D + dim] - e.lo[dim]) / e.width[dim] : 0.5;
     basis_row(u, e.level, e.xf, tabs_s + (dim * nf) * kEvalThreads + tid, kEvalThreads);
   }
   __syncthreads();
@@ -203,7 +161,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_fp64_anyk(EvalArgs e) {
   const bool live = q < e.Q;
   const int nf = e.nf;
   for (int dim = 0; dim < D; ++dim) {
-    const double u = live ? (e.xq[q * D + dim] - e.lo[dim]) * e.inv_width[dim] : 0.5;
+    const double u = live ? (e.xq[q * D + dim] - e.lo[dim]) / e.width[dim] : 0.5;
     basis_row(u, e.level, e.xf, tabs_s + (dim * nf) * kEvalThreads + tid, kEvalThreads);
   }
   __syncthreads();
@@ -365,7 +323,7 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   std::vector<double> box(2 * d);
   for (int dim = 0; dim < d; ++dim) {
     box[dim] = g->h_lo[dim];
-    box[d + dim] = 1.0 / (g->h_hi[dim] - g->h_lo[dim]);
+    box[d + dim] = g->h_hi[dim] - g->h_lo[dim];
   }
   SG_TRY_CLEAN(cudaMemcpyAsync(s->box, box.data(), 2 * d * sizeof(double), cudaMemcpyHostToDevice, st));
   SG_TRY_CLEAN(cudaMemcpyAsync(d_fid, fid.data(), M * d, cudaMemcpyHostToDevice, st));
@@ -444,7 +402,7 @@ extern "C" int sg_eval_feedback(const sg_surplus* s, const double* d_xq, int64_t
   e.ops = s->ops;
   e.W = s->Ws;
   e.lo = s->box;
-  e.inv_width = s->box + s->d;
+  e.width = s->box + s->d;
   e.xf = s->xf;
   e.xfdf = s->xfdf;
   e.Wdf = s->Wdf;

@@ -23,7 +23,7 @@ struct EvalArgs {
   const uint16_t* ops;    // M x kMaxDim: table offsets dim * nf + id of the active dimensions
   const double* W;        // M x k, evaluation order
   const double* lo;       // d
-  const double* inv_width;// d
+  const double* width;    // d: hi - lo (divided, so that nodes map exactly)
   const double* xf;       // 2^L + 1 points of the finest 1-D set
   const float2* xfdf;     // the same points as (hi, lo) float pairs
   const float2* Wdf;      // M x k surpluses as (hi, lo) pairs, evaluation order
@@ -32,7 +32,6 @@ struct EvalArgs {
 
 int n_functions(int level);
 int function_id(int l, int kidx);
-__device__ void basis_row(double u, int level, const double* xf, double* tab, int stride);
 }  // namespace sg
 
 struct sg_surplus {
@@ -48,7 +47,7 @@ struct sg_surplus {
   uint8_t* start = nullptr;       // M
   uint8_t* nact = nullptr;        // M
   uint16_t* ops = nullptr;        // M x kMaxDim
-  double* box = nullptr;          // lo[d], 1/(hi-lo)[d]
+  double* box = nullptr;          // lo[d], (hi-lo)[d]
   double* xf = nullptr;           // finest 1-D set, 2^L + 1 points
   float2* xfdf = nullptr;         // finest 1-D set as (hi, lo) pairs
   float2* Wdf = nullptr;          // Ws as (hi, lo) pairs

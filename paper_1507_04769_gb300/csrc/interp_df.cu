@@ -14,103 +14,10 @@
 // accumulator, so the error grows with the block length, not with M.
 #include "common.cuh"
 #include "diag.cuh"
+#include "basis.cuh"
 #include "interp.cuh"
 
 namespace sg {
-
-struct df {
-  float hi, lo;
-};
-
-__device__ __forceinline__ df df_from(double x) {
-  const float hi = __double2float_rn(x);
-  return {hi, __double2float_rn(x - static_cast<double>(hi))};
-}
-
-__device__ __forceinline__ df df_norm(float s, float e) {
-  const float hi = __fadd_rn(s, e);
-  return {hi, __fsub_rn(e, __fsub_rn(hi, s))};
-}
-
-__device__ __forceinline__ df df_add(df a, df b) {
-  const float s = __fadd_rn(a.hi, b.hi);
-  const float bb = __fsub_rn(s, a.hi);
-  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
-  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-  return df_norm(s, e);
-}
-
-__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, {-b.hi, -b.lo}); }
-
-__device__ __forceinline__ df df_mul(df a, df b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  return df_norm(p, e);
-}
-
-__device__ __forceinline__ df df_scale(df a, float s) {   // s exact power-of-two multiple of +-1
-  return {__fmul_rn(a.hi, s), __fmul_rn(a.lo, s)};
-}
-
-__device__ __forceinline__ df df_recip(df a) {
-  const float q = __frcp_rn(a.hi);
-  // residual 1 - a q, with a = hi + lo
-  float r = __fmaf_rn(-a.hi, q, 1.0f);
-  r = __fmaf_rn(-a.lo, q, r);
-  return df_norm(q, __fmul_rn(q, r));
-}
-
-// All 1-D basis values at u (FP64 in [0,1]) for levels 1..L+1, as pairs, in
-// barycentric form on the finest set (see basis_row in interp.cu).
-__device__ void basis_row_df(double u, int level, const float2* __restrict__ xf, float2* tab, int stride) {
-  tab[0] = make_float2(1.0f, 0.0f);
-  if (level == 0) return;
-  const int fine_n = 1 << level;
-  const df uu = df_from(u);
-  df rinv[kMaxFine + 1];
-  int hit = -1;
-  for (int p = 0; p <= fine_n; ++p) {
-    const df d = df_sub(uu, {xf[p].x, xf[p].y});
-    if (d.hi == 0.0f && d.lo == 0.0f) {
-      hit = p;
-      rinv[p] = {0.0f, 0.0f};
-    } else {
-      rinv[p] = df_recip(d);
-    }
-  }
-  int id = 1;
-  for (int l = 2; l <= level + 1; ++l) {
-    const int n = 1 << (l - 1);
-    const int sf = fine_n / n;
-    const bool exact = hit >= 0 && (hit % sf) == 0;
-    df inv_denom = {0.0f, 0.0f};
-    if (!exact) {
-      df den = {0.0f, 0.0f};
-      for (int m = 0; m <= n; ++m) {
-        float wm = (m & 1) ? -1.0f : 1.0f;
-        if (m == 0 || m == n) wm *= 0.5f;
-        den = df_add(den, df_scale(rinv[m * sf], wm));
-      }
-      inv_denom = df_recip(den);
-    }
-    const int cnt = l == 2 ? 2 : (n >> 1);
-    for (int j = 0; j < cnt; ++j) {
-      const int m = l == 2 ? j * n : 2 * j + 1;
-      df v;
-      if (exact) {
-        v = {(m * sf == hit) ? 1.0f : 0.0f, 0.0f};
-      } else {
-        float wm = (m & 1) ? -1.0f : 1.0f;
-        if (m == 0 || m == n) wm *= 0.5f;
-        v = df_mul(df_scale(rinv[m * sf], wm), inv_denom);
-      }
-      tab[(id + j) * stride] = make_float2(v.hi, v.lo);
-    }
-    id += cnt;
-  }
-}
 
 constexpr int kFoldBlock = 64;     // nodes per FP64 fold of the compensated sums
 constexpr int kChunk = 128;        // nodes staged in shared memory at a time
@@ -130,7 +37,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_df32(EvalArgs e, int d) {
   const int64_t q = blockIdx.x * int64_t(kEvalThreads) + tid;
   const bool live = q < e.Q;
   for (int dim = 0; dim < d; ++dim) {
-    const double u = live ? (e.xq[q * d + dim] - e.lo[dim]) * e.inv_width[dim] : 0.5;
+    const double u = live ? (e.xq[q * d + dim] - e.lo[dim]) / e.width[dim] : 0.5;
     basis_row_df(u, e.level, e.xfdf, tab + (dim * nf) * kEvalThreads + tid, kEvalThreads);
   }
   double total[K];

@@ -33,6 +33,7 @@ struct DevProblem {
   double QT[36];
   double G[18];   // R^-1 B' (3 x 6)
   double R[9];
+  double Bu[18];  // plant input matrix: attitude J^-1 B (rows 3..5 of a 6 x 3), LQ B (6 x 3)
 };
 
 // ------------------------------------------------------------------ duals
@@ -379,6 +380,58 @@ __device__ __forceinline__ void optimal_control(const DevProblem& P, const doubl
       u[i] = -s;
     }
   }
+}
+
+// ------------------------------------------------------------------ plant
+// Closed-loop plant x' = f(x, u) = f0(x) + Bu u for a given control u
+// (attitude: v' = E(v) w, w' = J^-1 (R(v) h x w) + J^-1 B u; LQ: A x + B u).
+__device__ __forceinline__ void plant_rhs(const DevProblem& P, const double* x, const double* u, double* f) {
+  if (P.kind == SG_PROBLEM_ATTITUDE) {
+    double f0[6], g[6];
+    const double lam0[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    attitude_f0_grad<double, double>(P, x, lam0, f0, g);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      f[i] = f0[i] + P.Bu[3 * i] * u[0] + P.Bu[3 * i + 1] * u[1] + P.Bu[3 * i + 2] * u[2];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      double s = P.Bu[3 * i] * u[0] + P.Bu[3 * i + 1] * u[1] + P.Bu[3 * i + 2] * u[2];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) s += P.A[6 * i + j] * x[j];
+      f[i] = s;
+    }
+  }
+}
+
+// Running cost L(x, u) (Section 2) for a given control.
+__device__ __forceinline__ double running_cost_xu(const DevProblem& P, const double* x, const double* u) {
+  if (P.kind == SG_PROBLEM_ATTITUDE) {
+    double sv = 0.0, sw = 0.0, su = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      sv += x[i] * x[i];
+      sw += x[3 + i] * x[3 + i];
+      su += u[i] * u[i];
+    }
+    return 0.5 * (P.wv * sv + P.ww * sw + P.r * su);
+  }
+  double xqx = 0.0, uru = 0.0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) s += P.Q[6 * i + j] * x[j];
+    xqx += x[i] * s;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s += P.R[3 * i + j] * u[j];
+    uru += u[i] * s;
+  }
+  return 0.5 * (xqx + uru);
 }
 
 // Host: derive the device problem from the ABI struct.  Returns false if R is singular.

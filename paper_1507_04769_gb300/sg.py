@@ -63,6 +63,8 @@ def _load():
     lib.sg_autotune_solve.argtypes = [C.POINTER(Problem), P, I64, P, P, I32, C.POINTER(SolveOpts), P,
                                       C.c_size_t, P, P, P, P, P, C.POINTER(SolveOpts), C.POINTER(D), I32, P]
     lib.sg_autotune_solve.restype = C.c_int
+    lib.sg_simulate_closed_loop.argtypes = [C.POINTER(Problem), P, P, I64, I32, D, I32, P, P, P, P, P]
+    lib.sg_simulate_closed_loop.restype = C.c_int
     lib.sg_build_surpluses.argtypes = [P, P, I32, C.POINTER(P), P]
     lib.sg_surplus_info.argtypes = [P, C.POINTER(I64), C.POINTER(I32), C.POINTER(P)]
     lib.sg_surplus_free.argtypes = [P]
@@ -263,3 +265,24 @@ def eval_feedback(surplus: Surplus, xq: torch.Tensor, mode: int = EVAL_FP64,
         out = torch.empty((Q, surplus.k), dtype=torch.float64, device=xq.device)
     _check(LIB.sg_eval_feedback(surplus.handle, _ptr(xq), Q, mode, _ptr(out), _stream(stream)))
     return out
+
+
+# --------------------------------------------------------------- closed loop
+def simulate_closed_loop(problem: Problem, surplus: Surplus, x0, nsteps: int, dt: float,
+                         mode: int = EVAL_DF32, keep_trajectory=False, stream=None):
+    """sg_simulate_closed_loop: returns dict with xT (n, 6), cost (n,) and,
+    if asked, traj (n, nsteps+1, 6) and ctrl (n, nsteps, 3)."""
+    x0 = _dev(x0, torch.float64).reshape(-1, 6)
+    n = x0.shape[0]
+    dev = x0.device
+    out = {"xT": torch.empty((n, 6), dtype=torch.float64, device=dev),
+           "cost": torch.empty((n,), dtype=torch.float64, device=dev)}
+    if keep_trajectory:
+        out["traj"] = torch.empty((n, nsteps + 1, 6), dtype=torch.float64, device=dev)
+        out["ctrl"] = torch.empty((n, nsteps, 3), dtype=torch.float64, device=dev)
+    _check(LIB.sg_simulate_closed_loop(C.byref(problem), surplus.handle, _ptr(x0), n, nsteps, dt, mode,
+                                       _ptr(out["xT"]), _ptr(out["cost"]),
+                                       _ptr(out["traj"]) if keep_trajectory else None,
+                                       _ptr(out["ctrl"]) if keep_trajectory else None, _stream(stream)))
+    return out
+
