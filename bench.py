@@ -401,6 +401,24 @@ def gpu_arm(args):
                 "newton_iters_hist_fp64": np.bincount(r64["iters"].cpu().numpy()).tolist()}
         del ws64
 
+    # ---------------- serving: Poisson-arriving mixed requests, continuous batching
+    serving_rep = None
+    if not args.skip_serving and rank == 0:
+        from paper_1507_04769_gb300 import serving as srv
+        server = srv.Server(slots=4, memory_budget=64 << 30, precision=prec, eval_mode=eval_mode)
+        keys = [(2, 20.0), (3, 20.0), (4, 20.0)]
+        counts = server.warm(levels=(2, 3, 4, 5), model_keys=keys)
+        reqs = srv.make_requests(args.serve_requests, rate=args.serve_rate, node_counts=counts, seed=11,
+                                 model_keys=keys)
+        server.start()
+        done = srv.replay(server, reqs, realtime=True)
+        serving_rep = {"arrival_rate_per_s": args.serve_rate, "requests": len(done), "slots": 4,
+                       "memory_budget_gb": 64, "latency": srv.latency_report(done),
+                       "sizes": "bvp 1..4096 states (full grid of level 2..5 when the draw reaches it), "
+                                "T in {10,20,40}; eval 1..1e5 queries; sim 1..1024 trajectories x 2000 steps"}
+        del server
+        torch.cuda.synchronize()
+
     # ---------------- roofline of the dominant kernel
     roof, kernels = roofline(kt, iters, N_h, M, prec)
 
@@ -441,6 +459,7 @@ def gpu_arm(args):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_t / args.steps},
+        "serving": serving_rep,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
@@ -548,6 +567,9 @@ def main():
     ap.add_argument("--cpu-nodes", type=int, default=100)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-requests", type=int, default=80)
     ap.add_argument("--cpu-worker", nargs=2, type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_worker is not None:

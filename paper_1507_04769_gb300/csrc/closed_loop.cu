@@ -105,24 +105,30 @@ __global__ void __launch_bounds__(32 * kClWarps) k_closed_loop(ClArgs c) {
   for (int k = 0; k < c.nsteps; ++k) {
     double u[3];
     feedback<MODE>(c, x, tab, lane, u);
-    double k1[6], k2[6], k3[6], k4[6], xs[6];
-    plant_rhs(c.P, x, u, k1);
-    const double l1 = running_cost_xu(c.P, x, u);
+    // the FP64 plant step runs on lane 0 only (the FP64 pipe is narrow on
+    // this part) and the new state is broadcast to the warp
+    if (lane == 0) {
+      double k1[6], k2[6], k3[6], k4[6], xs[6];
+      plant_rhs(c.P, x, u, k1);
+      const double l1 = running_cost_xu(c.P, x, u);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) xs[i] = x[i] + 0.5 * dt * k1[i];
-    plant_rhs(c.P, xs, u, k2);
-    const double l2 = running_cost_xu(c.P, xs, u);
+      for (int i = 0; i < 6; ++i) xs[i] = x[i] + 0.5 * dt * k1[i];
+      plant_rhs(c.P, xs, u, k2);
+      const double l2 = running_cost_xu(c.P, xs, u);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) xs[i] = x[i] + 0.5 * dt * k2[i];
-    plant_rhs(c.P, xs, u, k3);
-    const double l3 = running_cost_xu(c.P, xs, u);
+      for (int i = 0; i < 6; ++i) xs[i] = x[i] + 0.5 * dt * k2[i];
+      plant_rhs(c.P, xs, u, k3);
+      const double l3 = running_cost_xu(c.P, xs, u);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) xs[i] = x[i] + dt * k3[i];
-    plant_rhs(c.P, xs, u, k4);
-    const double l4 = running_cost_xu(c.P, xs, u);
+      for (int i = 0; i < 6; ++i) xs[i] = x[i] + dt * k3[i];
+      plant_rhs(c.P, xs, u, k4);
+      const double l4 = running_cost_xu(c.P, xs, u);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) x[i] = x[i] + (dt / 6.0) * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
-    z = z + (dt / 6.0) * (l1 + 2.0 * l2 + 2.0 * l3 + l4);
+      for (int i = 0; i < 6; ++i) x[i] = x[i] + (dt / 6.0) * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+      z = z + (dt / 6.0) * (l1 + 2.0 * l2 + 2.0 * l3 + l4);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x[i] = __shfl_sync(0xffffffffu, x[i], 0);
     if (c.ctrl && lane < 3) {
       double mine = lane == 0 ? u[0] : (lane == 1 ? u[1] : u[2]);
       c.ctrl[(tr * int64_t(c.nsteps) + k) * 3 + lane] = mine;
@@ -142,7 +148,7 @@ __global__ void __launch_bounds__(32 * kClWarps) k_closed_loop(ClArgs c) {
       if (i == lane) mine = x[i];
     c.xT[tr * 6 + lane] = mine;
   }
-  if (lane == 0) c.cost[tr] = z;
+  if (lane == 0) c.cost[tr] = z;   // z lives on lane 0
 }
 
 }  // namespace sg
