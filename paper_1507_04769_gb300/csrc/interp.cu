@@ -346,6 +346,7 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   SG_TRY_CLEAN(cudaGetLastError());
   if (split_df(fine_n + 1, s->xf, s->xfdf, st) != SG_OK || split_df(M * k, s->Ws, s->Wdf, st) != SG_OK)
     return cleanup(cudaGetLastError(), "split_df");
+  if (pack_tf32(s, st) != SG_OK) return cleanup(cudaGetLastError(), "pack_tf32");
   SG_TRY_CLEAN(cudaStreamSynchronize(st));
 #undef SG_TRY_CLEAN
   cudaFree(d_fid);
@@ -377,6 +378,8 @@ extern "C" void sg_surplus_free(sg_surplus* s) {
   if (s->xf) cudaFree(s->xf);
   if (s->xfdf) cudaFree(s->xfdf);
   if (s->Wdf) cudaFree(s->Wdf);
+  if (s->bpack) cudaFree(s->bpack);
+  if (s->tc_err) cudaFree(s->tc_err);
   delete s;
 }
 

@@ -51,10 +51,14 @@ struct sg_surplus {
   double* xf = nullptr;           // finest 1-D set, 2^L + 1 points
   float2* xfdf = nullptr;         // finest 1-D set as (hi, lo) pairs
   float2* Wdf = nullptr;          // Ws as (hi, lo) pairs
+  float* bpack = nullptr;         // split-TF32 [W_hi|W_lo], [W_hi|0] per 32-node chunk (k <= 8)
+  int tc_chunks = 0;
+  int* tc_err = nullptr;          // set by the tensor-core kernel if a wait timed out
 };
 
 namespace sg {
 int eval_tf32x3(const EvalArgs& e, const sg_surplus* s, cudaStream_t st);
 int eval_df32(const EvalArgs& e, int d, cudaStream_t st);
 int split_df(int64_t n, const double* src, float2* dst, cudaStream_t st);
+int pack_tf32(sg_surplus* s, cudaStream_t st);
 }

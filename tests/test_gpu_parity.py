@@ -321,3 +321,44 @@ def test_full_size_batched_solve_sampled():
         assert rel(res["lambda0"].cpu().numpy()[idx], lam) <= 1e-8
         assert rel(res["u0"].cpu().numpy()[idx], u) <= 1e-8
         assert rel(res["V"].cpu().numpy()[idx], V) <= 1e-8
+
+
+# ------------------------------------------------------------------ 3xTF32 tensor-core contraction
+def _tf32x3_bound(og, w, xq):
+    """A-priori bound of the split-TF32 contraction: |du_q| <= gamma sum_m |phi_qm| |w_m|,
+    gamma = (d + 3) 2^-22 + ceil(log2 M) 2^-23 (TF32 splitting of both operands,
+    FP32 basis values and FP32 accumulation)."""
+    phi = ointerp.basis_table(og, ointerp.to_unit(og, xq))
+    gamma = (og.d + 3) * 2.0 ** -22 + np.ceil(np.log2(og.M)) * 2.0 ** -23
+    return gamma * (np.abs(phi) @ np.abs(w))
+
+
+@pytest.mark.parametrize("d,L,k", [(6, 2, 3), (6, 4, 3), (3, 5, 2), (6, 3, 8)])
+def test_tf32x3_within_stated_bound(d, L, k):
+    lo, hi = synth.box(d)
+    g = sg.Grid(d, L, lo, hi)
+    og = ogrid.Grid(d, L, lo, hi)
+    f = np.random.default_rng(30 + L).standard_normal((og.M, k))
+    S = sg.Surplus(g, cuda(f))
+    w = ointerp.surpluses(og, f)
+    xq = np.concatenate([synth.mixed_queries(333, lo, hi, seed=31), og.x[:5]])
+    u = sg.eval_feedback(S, cuda(xq), mode=sg.EVAL_TF32X3).cpu().numpy()
+    ref = ointerp.eval_surplus(og, w, xq)
+    bound = _tf32x3_bound(og, w, xq)
+    assert np.all(np.isfinite(u))
+    assert np.max(np.abs(u - ref) / bound) <= 1.0
+    assert rel(u, ref) <= 1e-5
+
+
+def test_tf32x3_full_size_sampled():
+    g = sg.Grid(6, 4, LO, HI)
+    og = ogrid.Grid(6, 4, LO, HI)
+    f = np.random.default_rng(4).standard_normal((og.M, 3))
+    S = sg.Surplus(g, cuda(f))
+    xq = synth.mixed_queries(1_000_000, LO, HI, seed=1)
+    u = sg.eval_feedback(S, cuda(xq), mode=sg.EVAL_TF32X3).cpu().numpy()
+    assert np.all(np.isfinite(u))
+    idx = np.random.default_rng(5).choice(xq.shape[0], 256, replace=False)
+    w = ointerp.surpluses(og, f)
+    ref = ointerp.eval_surplus(og, w, xq[idx])
+    assert np.max(np.abs(u[idx] - ref) / _tf32x3_bound(og, w, xq[idx])) <= 1.0
