@@ -393,13 +393,43 @@ def gpu_arm(args):
         torch.cuda.synchronize()
         t64 = a.elapsed_time(b) / 1e3 / args.steps
         c64 = int((r64["status"] == sg.CONVERGED).sum().item())
+        # per-kernel times of the FP64 form (one launch per phase) for its roofline
+        sg.LIB.sg_timing_enable(1)
+        r64 = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=sg.PREC_FP64, workspace=ws64,
+                            n_max=n_max)
+        torch.cuda.synchronize()
+        sg.LIB.sg_timing_enable(0)
+        kt64 = collect_kernel_times(sg)
+        it64 = r64["iters"].cpu().numpy().astype(np.int64)
+        _, kern64 = roofline(kt64, it64, N_h, M, sg.PREC_FP64)
         mixed_solve_s = phase_ms["solve"] / 1e3
         dl = (r64["lambda0"] - res["lambda0"]).abs().max().item() / r64["lambda0"].abs().max().item()
         fp64 = {"solves_per_s": c64 / t64, "solve_ms": 1e3 * t64,
                 "mixed_solve_ms": 1e3 * mixed_solve_s, "speedup_mixed_over_fp64": t64 / mixed_solve_s,
                 "max_rel_diff_lambda0_mixed_vs_fp64": dl,
-                "newton_iters_hist_fp64": np.bincount(r64["iters"].cpu().numpy()).tolist()}
+                "newton_iters_hist_fp64": np.bincount(r64["iters"].cpu().numpy()).tolist(),
+                "kernels": dict(list(kern64.items())[:5])}
         del ws64
+
+    # ---------------- interpolant modes on the 1e6 queries (FP64, DF32, 3xTF32)
+    eval_modes = {}
+    if rank == 0:
+        S_ref = sg.Surplus(g0, res_out["u0"])
+        ref = sg.eval_feedback(S_ref, xq_d, mode=sg.EVAL_FP64)
+        for name, md in (("fp64", sg.EVAL_FP64), ("df32", sg.EVAL_DF32), ("tf32x3", sg.EVAL_TF32X3)):
+            outm = torch.empty_like(ref)
+            for _ in range(2):
+                sg.eval_feedback(S_ref, xq_d, mode=md, out=outm)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record(stream)
+            sg.eval_feedback(S_ref, xq_d, mode=md, out=outm)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            err = ((outm - ref).abs().max() / ref.abs().max()).item()
+            eval_modes[name] = {"ms_per_1e6": ms * 1e6 / N_QUERIES, "evals_per_s": N_QUERIES / (ms / 1e3),
+                                "max_rel_err_vs_fp64": err}
 
     # ---------------- serving: Poisson-arriving mixed requests, continuous batching
     serving_rep = None
@@ -418,6 +448,24 @@ def gpu_arm(args):
                                 "T in {10,20,40}; eval 1..1e5 queries; sim 1..1024 trajectories x 2000 steps"}
         del server
         torch.cuda.synchronize()
+
+    # ---------------- FP64 / FP32 pipe peaks measured by the library's FMA-chain probe
+    probe = {}
+    if rank == 0:
+        import ctypes as C
+        scratch = torch.empty(152 * 8 * 256 * 8, dtype=torch.uint8, device=dev)
+        sg.LIB.sg_fma_probe.argtypes = [C.c_int, C.c_void_p, C.c_size_t, C.c_int, C.c_int, C.c_int,
+                                        C.POINTER(C.c_double), C.c_void_p]
+        for name, pr, n_it in (("fp64", sg.PREC_FP64, 256), ("fp32", sg.PREC_MIXED, 4096)):
+            fl = C.c_double()
+            for rep in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sg.LIB.sg_fma_probe(pr, C.c_void_p(scratch.data_ptr()), scratch.numel(), 152 * 8, 256, n_it,
+                                    C.byref(fl), C.c_void_p(stream.cuda_stream))
+                b.record(stream)
+                torch.cuda.synchronize()
+            probe[name + "_tflops"] = fl.value / (a.elapsed_time(b) / 1e3) / 1e12
 
     # ---------------- roofline of the dominant kernel
     roof, kernels = roofline(kt, iters, N_h, M, prec)
@@ -459,6 +507,8 @@ def gpu_arm(args):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_t / args.steps},
+        "eval_modes": eval_modes,
+        "pipe_peaks_probe": probe,
         "serving": serving_rep,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
@@ -509,8 +559,10 @@ def roofline(kt, iters, N_h, M, prec):
         "k_newton_persistent" + suffix: ("alu", (flops_condense_interval() + flops_abd_interval()
                                                   + flops_recover_interval()) * int_units, peak_lin, "TFLOP/s"),
         "k_point" + suffix: ("hbm", bytes_point(tsize) * pt_units, None, "GB/s"),
+        "k_condense_smem_fp64": ("alu", flops_condense_interval() * int_units, PEAK_FP64_TFLOPS, "TFLOP/s"),
         "k_eval_fp64": ("alu", flops_eval_query(M, 3) * N_QUERIES, PEAK_FP64_TFLOPS, "TFLOP/s"),
         "k_eval_df32": ("alu", flops_eval_query_df32(M, 3) * N_QUERIES, PEAK_FP32_TFLOPS, "TFLOP/s"),
+        "k_eval_tf32x3": ("alu", 2 * M * 3 * N_QUERIES, PEAK_FP32_TFLOPS, "TFLOP/s"),
     }
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = 6785.9

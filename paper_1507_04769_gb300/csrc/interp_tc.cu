@@ -8,12 +8,12 @@
 //   Phi_hi x [W_hi | W_lo | 0]  and  Phi_lo x [W_hi | 0 | 0],
 // so that u = D[:, 0:k] + D[:, k:2k] (k <= 8 outputs).
 //
-// One CTA (4 warps) per 128 queries; thread t owns query row t.  Per chunk of
-// 32 nodes the threads write their rows of Phi_hi and Phi_lo into shared
-// memory in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per
-// core matrix), thread 0 issues 4 x 2 MMAs of shape M=128, N=16, K=8 and
-// commits them to an mbarrier; the next chunk is written into the other buffer
-// while the tensor cores work.  Every wait on an mbarrier has an iteration
+// One CTA (8 warps) per 128 queries; threads t and t + 128 own query row t,
+// each for one K-step of 8 nodes.  Per chunk of 16 nodes the threads write
+// their rows of Phi_hi and Phi_lo into shared memory in the no-swizzle K-major
+// core-matrix layout (8 rows x 16 bytes per core matrix), thread 0 issues
+// 2 x 2 MMAs of shape M=128, N=16, K=8 and commits them to an mbarrier; the
+// next chunk is written into the other buffer while the tensor cores work.  Every wait on an mbarrier has an iteration
 // limit: on timeout the kernel records an error flag, writes NaN outputs,
 // releases its tensor memory and returns.
 #include "common.cuh"
@@ -23,12 +23,13 @@
 namespace sg {
 
 constexpr int kTcRows = 128;          // queries per CTA (= MMA M)
+constexpr int kTcThreads = 256;       // two threads per query row
 constexpr int kTcN = 16;              // MMA N (2k <= 16)
-constexpr int kTcChunk = 32;          // nodes per chunk (4 MMA K-steps of 8)
+constexpr int kTcChunk = 16;          // nodes per chunk (2 MMA K-steps of 8, one per thread of a row)
 constexpr int kTcAStep = kTcRows * 32;          // bytes of one K-step of A (128 rows x 8 tf32)
-constexpr int kTcABytes = 4 * kTcAStep;         // one chunk of Phi_hi or Phi_lo: 16 KB
+constexpr int kTcABytes = 2 * kTcAStep;         // one chunk of Phi_hi or Phi_lo: 8 KB
 constexpr int kTcBStep = kTcN * 32;             // bytes of one K-step of B (16 rows x 8 tf32)
-constexpr int kTcBBytes = 4 * kTcBStep;         // one chunk of one B matrix: 2 KB
+constexpr int kTcBBytes = 2 * kTcBStep;         // one chunk of one B matrix: 1 KB
 constexpr int kTcBPack = 2 * kTcBBytes / 4;     // floats per chunk of [B1 | B2]
 constexpr unsigned kTcSpinLimit = 1u << 24;     // bounded mbarrier wait
 
@@ -129,11 +130,12 @@ struct TcArgs {
   int* err;
 };
 
-__global__ void __launch_bounds__(kTcRows) k_eval_tf32x3(TcArgs t) {
+__global__ void __launch_bounds__(kTcThreads) k_eval_tf32x3(TcArgs t) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const EvalArgs& e = t.e;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int64_t q = blockIdx.x * int64_t(kTcRows) + tid;
+  const int row = tid & (kTcRows - 1), half = tid / kTcRows;
+  const int64_t q = blockIdx.x * int64_t(kTcRows) + row;
   const bool live = q < e.Q;
   const int nf = e.nf;
   // layout: A buffers (2 x [hi, lo]) | B buffers (2 x [B1, B2]) | tables | barriers
@@ -143,9 +145,10 @@ __global__ void __launch_bounds__(kTcRows) k_eval_tf32x3(TcArgs t) {
   uint64_t* bars = reinterpret_cast<uint64_t*>(tab + size_t(t.d) * nf * kTcRows);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2);
 
-  for (int dim = 0; dim < t.d; ++dim) {
+  // the two threads of a row share the dimensions of its 1-D tables
+  for (int dim = half; dim < t.d; dim += 2) {
     const double u = live ? (e.xq[q * t.d + dim] - e.lo[dim]) / e.width[dim] : 0.5;
-    basis_row_f32(static_cast<float>(u), e.level, e.xf, tab + (dim * nf) * kTcRows + tid, kTcRows);
+    basis_row_f32(static_cast<float>(u), e.level, e.xf, tab + (dim * nf) * kTcRows + row, kTcRows);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tmem_holder)));
@@ -172,33 +175,32 @@ __global__ void __launch_bounds__(kTcRows) k_eval_tf32x3(TcArgs t) {
     }
     unsigned char* ahi = abuf + (2 * buf) * kTcABytes;
     unsigned char* alo = ahi + kTcABytes;
-    // row tid of Phi for the chunk's 32 nodes, in groups of 4 (one 16-byte
-    // row of a core matrix): element (r, k) of K-step s at
+    // this thread's K-step (8 nodes) of row `row`, as two 16-byte core-matrix
+    // rows: element (r, k) of K-step s at
     //   s * kTcAStep + ((r / 8) * 2 + (k % 8) / 4) * 128 + (r % 8) * 16 + (k % 4) * 4
 #pragma unroll
-    for (int g4 = 0; g4 < kTcChunk / 4; ++g4) {
+    for (int c2 = 0; c2 < 2; ++c2) {
       float hv[4], lv[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int64_t m = int64_t(c) * kTcChunk + g4 * 4 + j;
+        const int64_t m = int64_t(c) * kTcChunk + half * 8 + c2 * 4 + j;
         float phi = 0.0f;
         if (m < e.M) {
           const uint16_t* o = e.ops + m * kMaxDim;
-          phi = tab[o[0] * kTcRows + tid];
-          for (int a = 1; a < e.amax; ++a) phi *= tab[o[a] * kTcRows + tid];
+          phi = tab[o[0] * kTcRows + row];
+          for (int a = 1; a < e.amax; ++a) phi *= tab[o[a] * kTcRows + row];
         }
         hv[j] = tf32_round(phi);
         lv[j] = tf32_round(phi - hv[j]);
       }
-      const int s = g4 / 2, cc = g4 % 2;
-      const int off = s * kTcAStep + ((tid / 8) * 2 + cc) * 128 + (tid % 8) * 16;
+      const int off = half * kTcAStep + ((row / 8) * 2 + c2) * 128 + (row % 8) * 16;
       *reinterpret_cast<float4*>(ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
       *reinterpret_cast<float4*>(alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
     }
     // the chunk of [B1 | B2], pre-packed in the same layout
     const float4* src = reinterpret_cast<const float4*>(t.bpack + size_t(c) * kTcBPack);
     float4* dst = reinterpret_cast<float4*>(bbuf + (2 * buf) * kTcBBytes);
-    for (int x = tid; x < kTcBPack / 4; x += kTcRows) dst[x] = src[x];
+    for (int x = tid; x < kTcBPack / 4; x += kTcThreads) dst[x] = src[x];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(kTcRows) k_eval_tf32x3(TcArgs t) {
       const uint32_t a_hi = smem_u32(ahi), a_lo = smem_u32(alo);
       const uint32_t b1 = smem_u32(bbuf + (2 * buf) * kTcBBytes), b2 = b1 + kTcBBytes;
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
+      for (int s = 0; s < 2; ++s) {
         const uint64_t da_hi = smem_desc(a_hi + s * kTcAStep, 128, 256);
         const uint64_t da_lo = smem_desc(a_lo + s * kTcAStep, 128, 256);
         const uint64_t db1 = smem_desc(b1 + s * kTcBStep, 128, 256);
@@ -232,7 +234,10 @@ __global__ void __launch_bounds__(kTcRows) k_eval_tf32x3(TcArgs t) {
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   float v[16];
-  {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+  if (warp < 4) {
+    // warp w reads accumulator rows (tensor-memory lanes) 32w .. 32w + 31
     const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
     uint32_t r[16];
     asm volatile(
@@ -246,18 +251,14 @@ __global__ void __launch_bounds__(kTcRows) k_eval_tf32x3(TcArgs t) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
   }
   const bool all_ok = __syncthreads_and(ok);
-  if (live) {
+  if (live && half == 0) {
     for (int cix = 0; cix < e.k; ++cix) {
       float hi = 0.f, lo = 0.f;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if (j == cix) {
-          hi = v[j];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
+      for (int j = 0; j < 16; ++j) {
+        if (j == cix) hi = v[j];
         if (j == e.k + cix) lo = v[j];
+      }
       e.out[q * e.k + cix] = all_ok ? static_cast<double>(hi) + static_cast<double>(lo) : NAN;
     }
   }
@@ -322,7 +323,7 @@ int eval_tf32x3(const EvalArgs& e, const sg_surplus* s, cudaStream_t st) {
   SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    static_cast<int>(smem)));
   const unsigned blocks = static_cast<unsigned>(ceil_div(e.Q, kTcRows));
-  SG_TIMED("k_eval_tf32x3", st, (k_eval_tf32x3<<<blocks, kTcRows, smem, st>>>(t)));
+  SG_TIMED("k_eval_tf32x3", st, (k_eval_tf32x3<<<blocks, kTcThreads, smem, st>>>(t)));
   SG_LAUNCH_CHECK("k_eval_tf32x3");
   return SG_OK;
 }

@@ -259,16 +259,31 @@ __device__ __forceinline__ void char_jacobian(const DevProblem& P, const double*
     }
     attitude_f0_grad<D, T>(P, x, lam, f0, g);
     const T wdiag[6] = {T(P.wv), T(P.wv), T(P.wv), T(P.ww), T(P.ww), T(P.ww)};
+    // rows are assembled in registers and written as 16-byte vectors
 #pragma unroll
-    for (int r = 0; r < 6; ++r) {
+    for (int r = 0; r < 12; ++r) {
+      T row[12];
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
-        Jm[12 * r + c] = f0[r].d[c];                         // f0_x
-        Jm[12 * (6 + r) + c] = -g[r].d[c] - (r == c ? wdiag[r] : T(0));  // -(l_xx + phi_xx)
-        Jm[12 * (6 + r) + 6 + c] = -f0[c].d[r];              // -f0_x'
-        T k = T(0);
-        if (r >= 3 && c >= 3) k = T(P.Kw[3 * (r - 3) + (c - 3)]);
-        Jm[12 * r + 6 + c] = -k;                              // -K
+        if (r < 6) {
+          row[c] = f0[r].d[c];                                             // f0_x
+          T k = T(0);
+          if (r >= 3 && c >= 3) k = T(P.Kw[3 * (r - 3) + (c - 3)]);
+          row[6 + c] = -k;                                                 // -K
+        } else {
+          row[c] = -g[r - 6].d[c] - (r - 6 == c ? wdiag[r - 6] : T(0));    // -(l_xx + phi_xx)
+          row[6 + c] = -f0[c].d[r - 6];                                    // -f0_x'
+        }
+      }
+      if constexpr (sizeof(T) == 4) {
+        float4* dst = reinterpret_cast<float4*>(Jm + 12 * r);
+#pragma unroll
+        for (int q4 = 0; q4 < 3; ++q4)
+          dst[q4] = make_float4(row[4 * q4], row[4 * q4 + 1], row[4 * q4 + 2], row[4 * q4 + 3]);
+      } else {
+        double2* dst = reinterpret_cast<double2*>(Jm + 12 * r);
+#pragma unroll
+        for (int q2 = 0; q2 < 6; ++q2) dst[q2] = make_double2(row[2 * q2], row[2 * q2 + 1]);
       }
     }
     if (Fout) {
