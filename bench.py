@@ -94,6 +94,35 @@ def _rank_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(x: float, device) -> float:
+    """Maximum of a per-rank scalar (seconds) over the process group; the
+    identity without one. Timing only: the data path has no collective."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(n: int, device) -> int:
+    """Sum of a per-rank count over the process group (converged solves of all
+    ranks); the identity without one."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return int(n)
+    t = torch.tensor([int(n)], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(t.item())
+
+
+def rank_query_seed(rank: int) -> int:
+    """Seed of the query batch of one rank: every rank evaluates its own batch."""
+    return 1 + rank
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -231,7 +260,7 @@ def gpu_arm(args):
     g0 = sg.Grid(D, LEVEL, lo, hi)
     M = g0.M
     T_h, N_h = synth.mixed_horizons(M, seed=2)
-    xq_h = synth.mixed_queries(N_QUERIES, lo, hi, seed=1 + rank)
+    xq_h = synth.mixed_queries(N_QUERIES, lo, hi, seed=rank_query_seed(rank))
     T_d = torch.as_tensor(T_h, device=dev)
     N_d = torch.as_tensor(N_h, dtype=torch.int32, device=dev)
     xq_d = torch.as_tensor(xq_h, device=dev)
@@ -246,6 +275,9 @@ def gpu_arm(args):
     x0_d = torch.empty((M, 6), dtype=torch.float64, device=dev)
     x0_d.copy_(g0.coords)
     tune_ms = None
+    if args.only_steps:
+        args.form = "phase"
+        args.skip_cpu = args.skip_fp64 = args.skip_serving = True
     if args.form == "auto":
         form, tune_ms = sg.autotune_solve(prob, x0_d, T_d, N_d, tol=TOL, precision=prec, n_max=n_max,
                                           workspace=ws)
@@ -285,6 +317,7 @@ def gpu_arm(args):
     status = res["status"].cpu().numpy()
     iters = res["iters"].cpu().numpy().astype(np.int64)
     conv_per_step = int(np.sum(status == sg.CONVERGED))
+    conv_all_ranks = sum_over_ranks(conv_per_step, dev)
 
     # ---------------- timed region
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
@@ -329,15 +362,20 @@ def gpu_arm(args):
     step_ms = [ev[s][0].elapsed_time(ev[s][4]) for s in range(args.steps)]
     phase_ms = {name: sum(ev[s][i].elapsed_time(ev[s][i + 1]) for s in range(args.steps)) / args.steps
                 for i, name in enumerate(["grid", "solve", "surplus", "eval"])}
-    t_local = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    total_solves = conv_per_step * args.steps * world
+    t_max = max_over_ranks(sum(step_ms) / 1e3, dev)
+    total_solves = conv_all_ranks * args.steps
     value = total_solves / t_max
+
+    if args.only_steps:
+        roof, kernels = roofline(kt, iters, N_h, M, prec)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": total_solves / t_max, "unit": UNIT,
+                              "only_steps": True, "ms_per_step": 1e3 * t_max / args.steps, "roofline": roof,
+                              "kernels": kernels}), flush=True)
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return 0
 
     # ---------------- end to end through the public API with host buffers
     T_pin = torch.as_tensor(T_h).pin_memory()
@@ -362,6 +400,8 @@ def gpu_arm(args):
         e2e_step()
         flush.zero_()
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
     for s in range(args.steps):
@@ -371,10 +411,10 @@ def gpu_arm(args):
         torch.cuda.synchronize()
         flush.zero_()
     torch.cuda.synchronize()
-    e2e_t = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
+    e2e_t = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, dev)
     h2d = T_pin.numel() * 8 + N_pin.numel() * 4 + xq_pin.numel() * 8
     d2h = u_pin.numel() * 8 + sum(t.numel() * t.element_size() for t in node_pin.values())
-    e2e_value = conv_per_step * args.steps * world / e2e_t  # max over ranks not needed per-rank equal
+    e2e_value = conv_all_ranks * args.steps / e2e_t
 
     # ---------------- FP64 form on the same GPU (speedup of the mixed form)
     fp64 = None
@@ -620,6 +660,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--only-steps", action="store_true",
+                    help="warm-up and timed steps only, one launch per phase (for kernel launch lists)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-requests", type=int, default=80)
     ap.add_argument("--cpu-worker", nargs=2, type=int, default=None, help=argparse.SUPPRESS)

@@ -1,0 +1,91 @@
+"""Host-side logic of bench.py: the N > 1 path on CPU with gloo ranks, and the
+reference arm's JSON line (the oracle timed on a bounded sample)."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # per-rank seconds: the job time is the slowest rank's
+        t = bench.max_over_ranks(1.0 + rank, torch.device("cpu"))
+        # converged counts add up over ranks (weak scaling: every rank its own instance)
+        n = bench.sum_over_ranks(100 + rank, torch.device("cpu"))
+        seed = bench.rank_query_seed(rank)
+        dist.barrier()
+        q.put((rank, t, n, seed))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_timing_and_counts():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    out = sorted(q.get(timeout=5) for _ in range(world))
+    assert [o[1] for o in out] == [2.0, 2.0]          # max over ranks
+    assert [o[2] for o in out] == [201, 201]          # sum over ranks
+    assert len({o[3] for o in out}) == world          # distinct query batches per rank
+
+
+def test_helpers_without_process_group():
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5, torch.device("cpu")) == 3.5
+    assert bench.sum_over_ranks(7, torch.device("cpu")) == 7
+
+
+def _run_bench(args, env_extra):
+    env = dict(os.environ)
+    env.update(env_extra)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, capture_output=True,
+                          text=True, env=env, timeout=600, cwd=ROOT)
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    r = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "3"],
+                   {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
+
+
+@pytest.mark.slow
+def test_reference_arm_json_line():
+    r = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"], {})
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line
+    assert line["unit"] == "solves/s" and line["higher_is_better"] is True
+    assert line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["e2e"]["value"] == line["value"]
