@@ -40,6 +40,7 @@ UNIT = "solves/s"
 LEVEL, D = 4, 6
 N_QUERIES = 1_000_000
 TOL = 1e-8
+SEG_LEN = 16   # intervals per segment of the library's segmented staircase
 WORKLOAD = ("attitude6d_L4_1457nodes_T{10,20,40}_N{64,128,256}_mixedprec"
             "+surplus+1e6queries")
 
@@ -66,6 +67,18 @@ def flops_abd_interval() -> float:
     return ge + 2 * 144 + 144 + 12
 
 
+def flops_abd_seg_interval() -> float:
+    """Per interior mesh point of a segment: elimination of 12 columns of the
+    24 x 37 panel [carry rows; block row] (36 - k columns updated in the
+    23 - k rows left at step k, plus the multipliers)."""
+    return float(sum((23 - k) + 2 * (23 - k) * (36 - k) for k in range(12)) + 12)
+
+
+def flops_abd_segback_interval() -> float:
+    """Per interior mesh point: two 12 x 12 products and a 12 x 12 triangular solve."""
+    return 2 * 2 * 144 + 144 + 12
+
+
 def flops_recover_interval() -> float:
     """Per interval: 24 x 24 product and 24 x 24 triangular solve."""
     return 2 * 576 + 576 + 24
@@ -84,8 +97,9 @@ def flops_eval_query(M: int, k: int) -> float:
 def flops_eval_query_df32(M: int, k: int) -> float:
     """Per query on the FP32 pipe (pair-of-floats arithmetic, FMA = 2 flops):
     per node and output 15 (exact product 3, cross terms 4, exact sum 6, tail
-    2) and about 17 for the basis product (1.7 pair multiplications of 10)."""
-    return M * (15 * k + 17)
+    2) and 12 for the basis product (1.7 unnormalised pair multiplications of
+    7 on average over the level-4 nodes)."""
+    return M * (15 * k + 12)
 
 
 # ------------------------------------------------------------------ helpers
@@ -589,12 +603,17 @@ def roofline(kt, iters, N_h, M, prec):
     peak_lin = PEAK_FP32_TFLOPS if prec == 1 else PEAK_FP64_TFLOPS
     int_units = float(np.sum(iters * N_h))           # interval-iterations per solve
     pt_units = float(np.sum(iters * (3 * N_h + 1)))  # point-iterations per solve
+    seg = -(-N_h // SEG_LEN)                            # segments per node
+    seg_units = float(np.sum(iters * (N_h - seg)))      # interior segment points (panels)
+    red_units = float(np.sum(iters * seg))              # reduced block rows
     steps_timed = None
     models = {
         "k_condense" + suffix: ("alu", flops_condense_interval() * int_units, peak_lin, "TFLOP/s"),
         "k_condense_reg_fp32": ("alu", flops_condense_interval() * int_units, PEAK_FP32_TFLOPS, "TFLOP/s"),
         "k_abd" + suffix: ("alu", flops_abd_interval() * int_units, peak_lin, "TFLOP/s"),
-        "k_abd_reg" + suffix: ("alu", flops_abd_interval() * int_units, peak_lin, "TFLOP/s"),
+        "k_abd_seg" + suffix: ("alu", flops_abd_seg_interval() * seg_units, peak_lin, "TFLOP/s"),
+        "k_abd_red" + suffix: ("alu", flops_abd_interval() * red_units, peak_lin, "TFLOP/s"),
+        "k_abd_segback" + suffix: ("alu", flops_abd_segback_interval() * seg_units, peak_lin, "TFLOP/s"),
         "k_recover" + suffix: ("alu", flops_recover_interval() * int_units, peak_lin, "TFLOP/s"),
         "k_newton_persistent" + suffix: ("alu", (flops_condense_interval() + flops_abd_interval()
                                                   + flops_recover_interval()) * int_units, peak_lin, "TFLOP/s"),

@@ -191,8 +191,8 @@ int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t n,
  * buffers exactly as for sg_solve_bvps, and there is no d_work argument.
  *   - Batches whose workspace (sg_solve_workspace_bytes(n, n_max_intervals,
  *     precision)) exceeds SG_STATIC_SCRATCH_BYTES are rejected with SG_EINVAL
- *     and a message giving both sizes.  That allows 28 nodes at N = 64 in FP64
- *     (53 mixed), 14 at N = 128 (26), 7 at N = 256 (13) per call.
+ *     and a message giving both sizes.  That allows 22 nodes at N = 64 in FP64
+ *     (43 mixed), 11 at N = 128 (21), 5 at N = 256 (10) per call.
  *   - The first call on each device looks up the array's device address with
  *     cudaGetSymbolAddress (with that device current) and caches it; make that
  *     first call before any stream capture begins on the device.

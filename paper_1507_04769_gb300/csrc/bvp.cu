@@ -30,6 +30,8 @@ static Workspace carve(void* base, int64_t n, int Nmax, size_t tsize) {
   w.Cond = take(n * int64_t(Nmax) * kBlk * tsize);
   w.Rec = take(n * int64_t(Nmax) * kRec * tsize);
   w.Abd = take(n * int64_t(Nmax) * kBlk * tsize);
+  w.Seg = take(n * int64_t(Nmax) * kSegBlk * tsize);
+  w.Red = take(n * int64_t(seg_count(Nmax)) * kBlk * tsize);
   w.part = reinterpret_cast<double*>(take(n * int64_t(Nmax) * 2 * sizeof(double)));
   w.ns = reinterpret_cast<NodeState*>(take(n * sizeof(NodeState)));
   w.counters = reinterpret_cast<int*>(take(256));
@@ -149,6 +151,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
   const unsigned gnode_warp = static_cast<unsigned>(ceil_div(a.n * 32, 128));
   const unsigned gwarp_int = static_cast<unsigned>(ceil_div(nint, 4));
   const unsigned gwarp_node = static_cast<unsigned>(ceil_div(a.n, 4));
+  const unsigned gwarp_seg = static_cast<unsigned>(ceil_div(a.n * seg_count(a.Nmax), 4));
   const size_t cond_smem = sizeof(double) * kCondWarps * 36 * kCols;
   if constexpr (sizeof(T) == sizeof(double)) {
     SG_CUDA_TRY(cudaFuncSetAttribute(k_condense_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -201,7 +204,9 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
                (k_condense_smem<<<static_cast<unsigned>(ceil_div(nint, kCondWarps)), 32 * kCondWarps, cond_smem,
                                   st>>>(a, w)));
     }
-    SG_TIMED(kname<T>("k_abd_reg"), st, (k_abd_reg<T><<<gwarp_node, 128, 0, st>>>(a, w)));
+    SG_TIMED(kname<T>("k_abd_seg"), st, (k_abd_seg<T><<<gwarp_seg, 128, 0, st>>>(a, w)));
+    SG_TIMED(kname<T>("k_abd_red"), st, (k_abd_red<T><<<gwarp_node, 128, 0, st>>>(a, w)));
+    SG_TIMED(kname<T>("k_abd_segback"), st, (k_abd_segback<T><<<gwarp_seg, 128, 0, st>>>(a, w)));
     SG_TIMED(kname<T>("k_recover"), st, (k_recover<T><<<gwarp_int, 128, 0, st>>>(a, w)));
     SG_TIMED("k_ls_begin", st, (k_ls_begin<<<gnode_thr, 128, 0, st>>>(a, w)));
     SG_LAUNCH_CHECK("newton kernels");
@@ -303,6 +308,7 @@ static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, dou
   const unsigned gnw = static_cast<unsigned>(ceil_div(a.n * 32, 128));
   const unsigned gwi = static_cast<unsigned>(ceil_div(nint, 4));
   const unsigned gwn = static_cast<unsigned>(ceil_div(a.n, 4));
+  const unsigned gws = static_cast<unsigned>(ceil_div(a.n * seg_count(a.Nmax), 4));
   const size_t cond_smem = sizeof(double) * kCondWarps * 36 * kCols;
   cudaGraph_t root;
   cudaError_t e = cudaGraphCreate(&root, 0);
@@ -330,7 +336,9 @@ static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, dou
   } else {
     nb.kernel(k_condense_smem, static_cast<unsigned>(ceil_div(nint, kCondWarps)), 32 * kCondWarps, cond_smem, a, w);
   }
-  nb.kernel(k_abd_reg<T>, gwn, 128, 0, a, w);
+  nb.kernel(k_abd_seg<T>, gws, 128, 0, a, w);
+  nb.kernel(k_abd_red<T>, gwn, 128, 0, a, w);
+  nb.kernel(k_abd_segback<T>, gws, 128, 0, a, w);
   nb.kernel(k_recover<T>, gwi, 128, 0, a, w);
   nb.kernel(k_ls_begin, gnt, 128, 0, a, w);
   nb.kernel(k_set_cond_one, 1, 1, 0, hl);

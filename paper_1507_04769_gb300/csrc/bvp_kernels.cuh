@@ -7,10 +7,10 @@
 //               elimination of the two interior stages (24 columns, partial
 //               pivoting over the 24 interior rows) leaves the 12 x 25 block
 //               row [S | T | rhs] that couples y_i and y_{i+1}
-//   k_abd_reg   staircase elimination with partial pivoting over
+//   k_abd_*     staircase elimination with partial pivoting over
 //               [x(0) rows; block rows; lambda(T) rows] and back substitution
-//               for the mesh-point corrections (serial over the intervals of a
-//               node, parallel over nodes)
+//               for the mesh-point corrections, segmented so that the serial
+//               chain per node is short (parallel over nodes and segments)
 //   k_recover   interior-stage corrections from the stored pivot rows
 //   k_trial     FP64 residual at Y + alpha D, per interval; it also stores the
 //               stage residual rows (the right-hand side of the next
@@ -61,6 +61,11 @@ constexpr int kRec = 24 * kRecLd;
 constexpr int kBlkLd = 28;       // row stride of a 12-row block of 25 columns
 constexpr int kBlk = 12 * kBlkLd;
 constexpr int kResRows = 36;     // stage residual rows per interval
+constexpr int kSegLen = 16;      // intervals per segment of the segmented staircase
+constexpr int kSegLd = 40;       // row stride of a segment pivot row: F | U | V | rhs (37) + pad
+constexpr int kSegBlk = 12 * kSegLd;
+
+__host__ __device__ __forceinline__ int seg_count(int N) { return (N + kSegLen - 1) / kSegLen; }
 
 struct Workspace {
   double* Y;       // n x P x 12, current iterate
@@ -70,6 +75,8 @@ struct Workspace {
   void* Cond;      // n x Nmax x kBlk (T), condensed block rows
   void* Rec;       // n x Nmax x kRec (T), interior pivot rows
   void* Abd;       // n x Nmax x kBlk (T), staircase pivot rows
+  void* Seg;       // n x Nmax x kSegBlk (T), pivot rows of the segment eliminations
+  void* Red;       // n x seg_count(Nmax) x kBlk (T), reduced block rows of the segments
   double* part;    // n x Nmax x 2, partial |F|^2 and |F|_inf
   NodeState* ns;   // n
   int* counters;   // 2
@@ -300,6 +307,42 @@ __device__ __forceinline__ void store_row25(T* __restrict__ dst, const T (&r)[25
   dst[24] = r[24];
 }
 
+// 37-entry rows (F | Y | Z | rhs) as 40-entry vectors (16-byte accesses).
+template <typename T>
+__device__ __forceinline__ void store_row40(T* __restrict__ dst, const T (&r)[37]) {
+  if constexpr (sizeof(T) == 4) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) d4[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    d4[9] = make_float4(r[36], 0.0f, 0.0f, 0.0f);
+  } else {
+    double2* d2 = reinterpret_cast<double2*>(dst);
+#pragma unroll
+    for (int q = 0; q < 18; ++q) d2[q] = make_double2(r[2 * q], r[2 * q + 1]);
+    d2[18] = make_double2(r[36], 0.0);
+    d2[19] = make_double2(0.0, 0.0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_row40(const T* __restrict__ src, T (&r)[40]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      const float4 v = s4[q];
+      r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+    }
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int q = 0; q < 20; ++q) {
+      const double2 v = s2[q];
+      r[2 * q] = v.x; r[2 * q + 1] = v.y;
+    }
+  }
+}
+
 // Twelve pivot steps with partial pivoting on 25-column rows held one per
 // lane.  cand: this lane's row takes part.  The pivot row of step k keeps
 // 1/pivot at column k; plane[k] is the lane that held it.
@@ -330,24 +373,54 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
 }
 
 // ---------------------------------------------------------------- condensation
-// Register-resident FP32 form: warp per interval.  Lane r < 24 holds interior
-// equation row r (stages 2 and 3); lanes 24..31 hold stage-4 rows 24..31 and
-// lanes 0..3 also hold stage-4 rows 32..35.  Pivoting is over the 24 interior
-// rows; rows never move: the pivot row is broadcast by shuffles and every
-// other row updates itself in registers.  The pivot rows (in pivot order) are
-// stored for the stage recovery; the stage-4 rows end up holding the
-// condensed block row in columns 24..48.
+// Register-resident FP32 form: warp per interval.  Lane r holds equation row
+// r of the 36 x 49 system: lanes 0..23 the interior rows (stages 2 and 3),
+// lanes 24..31 the stage-4 rows 24..31.  Pivoting is over the 24 interior
+// rows and rows never move.  At step k the pivot lane writes its row
+// (columns from k rounded down to a multiple of 4) to the shared-memory pivot
+// table, and every lane reads it back with 16-byte broadcast loads: one load
+// brings four columns, where a shuffle brings one.  The table, in pivot order,
+// is then the stored interior pivot rows for the stage recovery.  The four
+// stage-4 rows 32..35 are built in shared memory and eliminated afterwards
+// against the same table with the columns spread over the lanes, so no lane
+// carries a second row through the main elimination.
+constexpr int kCondPivLd = kRecLd;                   // 52 floats per pivot row
+constexpr int kCondSmemFloats = 28 * kCondPivLd;     // 24 pivot rows + 4 late stage-4 rows
+
 __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const Workspace& w, int64_t node,
-                                                      int i, int N, int lane) {
+                                                      int i, int N, int lane, float* __restrict__ sm) {
   const int64_t wid = node * a.Nmax + i;
   const float hf = static_cast<float>(a.T[node]) / static_cast<float>(N);
   const int64_t pbase = node * npts(a.Nmax) + 3 * int64_t(i);
   const float* J = static_cast<const float*>(w.Jm) + pbase * 144;
   const float* res = static_cast<const float*>(w.Res) + wid * kResRows;
+  float* piv_s = sm;                        // [24][kCondPivLd]
+  float* late_s = sm + 24 * kCondPivLd;     // [4][kCondPivLd], rows 32..35
+
+  // late rows r = 32 + q (stage 4, component 8 + q), column-parallel build:
+  // column c < 24 -> interior stage 2 + c / 12; 24..35 -> y_i; 36..47 -> y_{i+1}
+  for (int e = lane; e < 4 * kCols; e += 32) {
+    const int q = e / kCols, c = e % kCols;
+    const int comp = 8 + q;
+    float v;
+    if (c == 48) {
+      v = -res[32 + q];
+    } else {
+      const int j = c < 24 ? 1 + c / 12 : (c < 36 ? 0 : 3);
+      const int cc = c < 24 ? c % 12 : (c < 36 ? c - 24 : c - 36);
+      v = -hf * kLobAf[3][j] * J[j * 144 + comp * 12 + cc];
+      if (cc == comp) {
+        if (j == 3) v += 1.0f;
+        if (j == 0) v -= 1.0f;
+      }
+    }
+    late_s[q * kCondPivLd + c] = v;
+  }
 
   // row r = 12 (k - 1) + comp for stage k = 1, 2, 3 (Lobatto stages 2, 3, 4)
-  auto build = [&](int r, float* row) {
-    const int k = r / 12 + 1, comp = r % 12;
+  float ra[kCols];
+  {
+    const int k = lane / 12 + 1, comp = lane % 12;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float cf = -hf * kLobAf[k][j];
@@ -356,10 +429,10 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const float4 v = src[q];
-        row[c0 + 4 * q + 0] = cf * v.x;
-        row[c0 + 4 * q + 1] = cf * v.y;
-        row[c0 + 4 * q + 2] = cf * v.z;
-        row[c0 + 4 * q + 3] = cf * v.w;
+        ra[c0 + 4 * q + 0] = cf * v.x;
+        ra[c0 + 4 * q + 1] = cf * v.y;
+        ra[c0 + 4 * q + 2] = cf * v.z;
+        ra[c0 + 4 * q + 3] = cf * v.w;
       }
     }
     // +I on the stage's own point, -I on y_i (compare against every column
@@ -368,74 +441,110 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     const int minus = 24 + comp;
 #pragma unroll
     for (int c = 0; c < 48; ++c) {
-      if (c == plus) row[c] += 1.0f;
-      if (c == minus) row[c] -= 1.0f;
+      if (c == plus) ra[c] += 1.0f;
+      if (c == minus) ra[c] -= 1.0f;
     }
-    row[48] = -res[r];
-  };
+    ra[48] = -res[lane];
+  }
 
-  float ra[kCols], rb[kCols];
-  build(lane, ra);
-  const bool has_b = lane < 4;
-  if (has_b) build(32 + lane, rb);
   const bool interior = lane < 24;
   bool done = false;
-  int my_step = -1;
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < 24; ++k) {
+    constexpr int kLast = kCols / 4;   // float4 index holding column 48
+    const int q0 = k / 4;
     const int p = warp_pivot_lane<float>(ra[k], interior && !done, lane);
-    const float piv = __shfl_sync(0xffffffffu, ra[k], p);
+    if (lane == p) {
+      float4* dst = reinterpret_cast<float4*>(piv_s + k * kCondPivLd);
+#pragma unroll
+      for (int q = q0; q < kLast; ++q) dst[q] = make_float4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
+      dst[kLast] = make_float4(ra[48], 0.0f, 0.0f, 0.0f);
+      done = true;
+    }
+    __syncwarp();
+    const float4* src = reinterpret_cast<const float4*>(piv_s + k * kCondPivLd);
+    const float4 first = src[q0];
+    const float piv = (k & 3) == 0 ? first.x : (k & 3) == 1 ? first.y : (k & 3) == 2 ? first.z : first.w;
     const bool good = piv != 0.0f && isfinite(piv);
     ok = ok && good;
     const float inv = good ? 1.0f / piv : 0.0f;
-    const bool is_p = lane == p;
-    const float la = (interior && done) || is_p ? 0.0f : ra[k] * inv;
-    const float lb = has_b ? rb[k] * inv : 0.0f;
+    const float la = (interior && done) ? 0.0f : ra[k] * inv;
 #pragma unroll
-    for (int c = k + 1; c < kCols; ++c) {
-      const float pc = __shfl_sync(0xffffffffu, ra[c], p);
-      ra[c] = fmaf(-la, pc, ra[c]);
-      rb[c] = fmaf(-lb, pc, rb[c]);
-    }
-    if (is_p) {
-      done = true;
-      my_step = k;
+    for (int q = q0; q <= kLast; ++q) {
+      const float4 v = q == q0 ? first : src[q];
+      const float pv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int c = 4 * q + t;
+        if (c > k && c < kCols) ra[c] = fmaf(-la, pv[t], ra[c]);
+      }
     }
   }
   if (!ok && lane == 0) w.ns[node].singular = 1;
-  const int64_t blk = node * a.Nmax + i;
-  float* rec = static_cast<float*>(w.Rec) + blk * kRec;
-  float* cond = static_cast<float*>(w.Cond) + blk * kBlk;
-  if (interior) {
-    float4* dst = reinterpret_cast<float4*>(rec + my_step * kRecLd);
+
+  // late rows against the pivot table: lane holds columns lane and lane + 32
+  const bool has_hi = lane + 32 < kCols;   // lanes 0..16 hold columns 32..48
+  float lo[4], hi[4];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) dst[q] = make_float4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
-    rec[my_step * kRecLd + 48] = ra[48];
-  } else {
+  for (int q = 0; q < 4; ++q) {
+    lo[q] = late_s[q * kCondPivLd + lane];
+    hi[q] = has_hi ? late_s[q * kCondPivLd + lane + 32] : 0.0f;
+  }
+#pragma unroll 4
+  for (int k = 0; k < 24; ++k) {
+    const float* prow = piv_s + k * kCondPivLd;
+    const float pk = prow[k];
+    const float inv = (pk != 0.0f && isfinite(pk)) ? 1.0f / pk : 0.0f;
+    const float u_lo = prow[lane];
+    const float u_hi = has_hi ? prow[lane + 32] : 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float l = __shfl_sync(0xffffffffu, lo[q], k) * inv;
+      if (lane > k) lo[q] = fmaf(-l, u_lo, lo[q]);
+      hi[q] = fmaf(-l, u_hi, hi[q]);
+    }
+  }
+
+  // outputs: pivot rows (pivot order) for the recovery, condensed block row
+  // [S | T | rhs] = columns 24..48 of the stage-4 rows
+  const int64_t blk = node * a.Nmax + i;
+  float4* rec4 = reinterpret_cast<float4*>(static_cast<float*>(w.Rec) + blk * kRec);
+  const float4* piv4 = reinterpret_cast<const float4*>(piv_s);
+  constexpr int kRow4 = kCondPivLd / 4;   // 13
+  for (int e = lane; e < 24 * kRow4; e += 32) {
+    const int r = e / kRow4, q = e % kRow4;
+    if (q >= r / 4) rec4[e] = piv4[e];     // the part at and right of the diagonal
+  }
+  float* cond = static_cast<float*>(w.Cond) + blk * kBlk;
+  if (!interior) {
     float tmp[25];
 #pragma unroll
     for (int c = 0; c < 25; ++c) tmp[c] = ra[24 + c];
     store_row25<float>(cond + (lane - 24) * kBlkLd, tmp);
   }
-  if (has_b) {
-    float tmp[25];
 #pragma unroll
-    for (int c = 0; c < 25; ++c) tmp[c] = rb[24 + c];
-    store_row25<float>(cond + (8 + lane) * kBlkLd, tmp);
+  for (int q = 0; q < 4; ++q) {
+    if (lane >= 24) cond[(8 + q) * kBlkLd + (lane - 24)] = lo[q];
+    if (has_hi) cond[(8 + q) * kBlkLd + (lane + 8)] = hi[q];
   }
+  __syncwarp();   // the table is reused by the warp's next interval
 }
 
-__global__ void __launch_bounds__(128) k_condense_reg(SolveArgs a, Workspace w) {
+constexpr int kCondRegWarps = 4;
+
+__global__ void __launch_bounds__(32 * kCondRegWarps) k_condense_reg(SolveArgs a, Workspace w) {
+  __shared__ __align__(16) float sm[kCondRegWarps][kCondSmemFloats];
   const int lane = threadIdx.x & 31;
-  const int64_t wid = blockIdx.x * int64_t(4) + (threadIdx.x >> 5);
+  const int warp = threadIdx.x >> 5;
+  const int64_t wid = blockIdx.x * int64_t(kCondRegWarps) + warp;
   if (wid >= a.n * a.Nmax) return;
   const int64_t node = wid / a.Nmax;
   const int i = static_cast<int>(wid % a.Nmax);
   if (!w.ns[node].active) return;
   const int N = a.N[node];
   if (i >= N) return;
-  condense_interval_reg(a, w, node, i, N, lane);
+  condense_interval_reg(a, w, node, i, N, lane, sm[warp]);
 }
 
 // Shared-memory FP64 form (used by the FP64 solve): the 36 x 49 system of one
@@ -511,14 +620,18 @@ __global__ void __launch_bounds__(32 * kCondWarps) k_condense_smem(SolveArgs a, 
 // y_{i+1} into the next panel.  The next block row is prefetched into lanes
 // 0..11 while the current panel is eliminated.  The lambda(T) rows close the
 // system; back substitution then runs from the last mesh point to the first.
+//
+// The blocks may be the N interval block rows of the node (pt_stride = 3:
+// block i couples mesh points 3i and 3i + 3) or the reduced block rows of the
+// segmented form (block s couples the segment ends, pt_stride = 3 x segment
+// length); the last block always ends at mesh point 3N.
 template <typename T>
-__device__ __forceinline__ bool abd_node_reg(const SolveArgs& a, const Workspace& w, int64_t node, int N,
-                                             int lane) {
+__device__ __forceinline__ bool abd_staircase(const SolveArgs& a, const Workspace& w, int64_t node, int N,
+                                              const T* __restrict__ cond, int nblk, int pt_stride,
+                                              T* __restrict__ abd, int lane) {
   const int64_t pb = node * npts(a.Nmax);
   const double* Y = w.Y + pb * 12;
   const double* x0 = a.x0 + node * 6;
-  const T* cond = static_cast<const T*>(w.Cond) + node * a.Nmax * int64_t(kBlk);
-  T* abd = static_cast<T*>(w.Abd) + node * a.Nmax * int64_t(kBlk);
   double* D = w.D + pb * 12;
   const bool rowlane = lane < 18;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -541,8 +654,8 @@ __device__ __forceinline__ bool abd_node_reg(const SolveArgs& a, const Workspace
   bool done = false;
   int rank = 0;
   int plane[12];
-  for (int i = 0; i < N; ++i) {
-    if (i + 1 < N && lane < 12) load_row25<T>(cond + int64_t(i + 1) * kBlk + lane * kBlkLd, nx);
+  for (int i = 0; i < nblk; ++i) {
+    if (i + 1 < nblk && lane < 12) load_row25<T>(cond + int64_t(i + 1) * kBlk + lane * kBlkLd, nx);
     done = false;
     int my_step = -1;
     panel_eliminate12<T>(r, rowlane, done, my_step, plane, ok, lane);
@@ -609,8 +722,8 @@ __device__ __forceinline__ bool abd_node_reg(const SolveArgs& a, const Workspace
     row[c] = T(0);
     pre[c] = T(0);
   }
-  if (lane < 12) load_row25<T>(abd + int64_t(N - 1) * kBlk + lane * kBlkLd, row);
-  for (int ii = N - 1; ii >= 0; --ii) {
+  if (lane < 12) load_row25<T>(abd + int64_t(nblk - 1) * kBlk + lane * kBlkLd, row);
+  for (int ii = nblk - 1; ii >= 0; --ii) {
     if (ii > 0 && lane < 12) load_row25<T>(abd + int64_t(ii - 1) * kBlk + lane * kBlkLd, pre);
     T tt = row[24];
 #pragma unroll
@@ -626,7 +739,7 @@ __device__ __forceinline__ bool abd_node_reg(const SolveArgs& a, const Workspace
 #pragma unroll
       for (int c = 0; c < 12; ++c)
         if (c == lane) mine = dy[c];
-      D[3 * int64_t(ii) * 12 + lane] = double(mine);
+      D[int64_t(ii) * pt_stride * 12 + lane] = double(mine);
     }
 #pragma unroll
     for (int c = 0; c < 25; ++c) row[c] = pre[c];
@@ -634,14 +747,216 @@ __device__ __forceinline__ bool abd_node_reg(const SolveArgs& a, const Workspace
   return ok;
 }
 
+// The whole staircase of one node over its N interval block rows.
 template <typename T>
-__global__ void __launch_bounds__(128) k_abd_reg(SolveArgs a, Workspace w) {
+__device__ __forceinline__ bool abd_node_reg(const SolveArgs& a, const Workspace& w, int64_t node, int N,
+                                             int lane) {
+  const T* cond = static_cast<const T*>(w.Cond) + node * a.Nmax * int64_t(kBlk);
+  T* abd = static_cast<T*>(w.Abd) + node * a.Nmax * int64_t(kBlk);
+  return abd_staircase<T>(a, w, node, N, cond, N, 3, abd, lane);
+}
+
+// ---------------------------------------------------------------- segmented staircase
+// The serial chain of the staircase is N panels long.  The segmented form
+// cuts the mesh of a node into segments of kSegLen intervals and runs three
+// kernels:
+//   k_abd_seg      warp per (node, segment): eliminates the segment's interior
+//                  mesh points.  A panel holds the 12 carry rows [F | G | r]
+//                  (coupling the segment's first point y_a with y_i) and the
+//                  block row i [0 | S_i | T_i | r_i]; twelve pivot steps with
+//                  partial pivoting over all 24 rows remove y_i, leave 12
+//                  pivot rows [F | U | V | r] (1/pivot on U's diagonal) and 12
+//                  new carry rows on (y_a, y_{i+1}).  After the last panel the
+//                  carry rows are the segment's reduced block row on
+//                  (y_a, y_b), in the same 12 x 25 format as a block row.
+//   k_abd_red      warp per node: the staircase over the reduced block rows
+//                  and the boundary rows gives the segment ends.
+//   k_abd_segback  warp per (node, segment): back substitution through the
+//                  stored pivot rows for the interior mesh points.
+// This is Gaussian elimination with partial pivoting restricted to the block
+// rows of a segment, the structured pairwise reduction of block rows of
+// Wright (SIAM J. Sci. Stat. Comput. 13, 1992) taken sequentially inside a
+// segment; the chain becomes kSegLen + N / kSegLen panels.
+template <typename T>
+__global__ void __launch_bounds__(128) k_abd_seg(SolveArgs a, Workspace w) {
+  constexpr int kStage = 12 * kBlkLd;
+  __shared__ __align__(16) T sm[4][2 * kSegLd + kStage];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int smax = seg_count(a.Nmax);
+  const int64_t wid = blockIdx.x * int64_t(4) + warp;
+  const int64_t node = wid / smax;
+  const int s = static_cast<int>(wid % smax);
+  if (node >= a.n) return;
+  if (!w.ns[node].active) return;
+  const int N = a.N[node];
+  if (s >= seg_count(N)) return;
+  const int i0 = s * kSegLen;
+  const int i1 = i0 + kSegLen < N ? i0 + kSegLen : N;
+  T* pivbuf = sm[warp];
+  T* stage = sm[warp] + 2 * kSegLd;
+  const T* cond = static_cast<const T*>(w.Cond) + node * a.Nmax * int64_t(kBlk);
+  T* seg = static_cast<T*>(w.Seg) + node * a.Nmax * int64_t(kSegBlk);
+  const unsigned lt_mask = (1u << lane) - 1u;
+
+  // r = [F (y_a) 0..11 | Y (y_i) 12..23 | Z (y_{i+1}) 24..35 | rhs 36]
+  T r[37];
+#pragma unroll
+  for (int c = 0; c < 37; ++c) r[c] = T(0);
+  {
+    T row[25];
+    if (lane < 12) {   // carry = block row i0 on (y_a, y_{a+1})
+      load_row25<T>(cond + int64_t(i0) * kBlk + lane * kBlkLd, row);
+#pragma unroll
+      for (int c = 0; c < 24; ++c) r[c] = row[c];
+      r[36] = row[24];
+    } else if (lane < 24 && i0 + 1 < i1) {   // block row i0 + 1 on (y_{a+1}, y_{a+2})
+      load_row25<T>(cond + int64_t(i0 + 1) * kBlk + (lane - 12) * kBlkLd, row);
+#pragma unroll
+      for (int c = 0; c < 24; ++c) r[12 + c] = row[c];
+      r[36] = row[24];
+    }
+  }
+  const bool cand = lane < 24;
+  bool carry = lane < 12;
+  bool ok = true;
+  for (int i = i0 + 1; i < i1; ++i) {
+    if (i + 1 < i1) {   // stage block row i + 1 for the lanes that become free
+      const T* src = cond + int64_t(i + 1) * kBlk;
+      if constexpr (sizeof(T) == 4) {
+        for (int e = lane; e < kStage / 4; e += 32)
+          reinterpret_cast<float4*>(stage)[e] = reinterpret_cast<const float4*>(src)[e];
+      } else {
+        for (int e = lane; e < kStage / 2; e += 32)
+          reinterpret_cast<double2*>(stage)[e] = reinterpret_cast<const double2*>(src)[e];
+      }
+    }
+    bool done = false;
+    int my_step = -1;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const int p = warp_pivot_lane<T>(r[12 + k], cand && !done, lane);
+      T* pb = pivbuf + (k & 1) * kSegLd;
+      if (lane == p) {
+        store_row40<T>(pb, r);
+        done = true;
+        my_step = k;
+      }
+      __syncwarp();
+      T prow[40];
+      load_row40<T>(pb, prow);
+      const T piv = prow[12 + k];
+      const bool good = piv != T(0) && isfinite(piv);
+      ok = ok && good;
+      const T inv = good ? T(1) / piv : T(0);
+      const T la = (cand && !done) ? r[12 + k] * inv : T(0);
+#pragma unroll
+      for (int c = 0; c < 37; ++c)
+        if (c < 12 || c > 12 + k) r[c] = fma(-la, prow[c], r[c]);
+      if (lane == p) r[12 + k] = inv;
+    }
+    if (done) store_row40<T>(seg + (int64_t(i) * 12 + my_step) * kSegLd, r);
+    // next panel: the carry rows move y_{i+1} into the y_i slot; the pivot
+    // lanes take block row i + 1 from the stage, in lane order
+    const int rank = __popc(__ballot_sync(0xffffffffu, done) & lt_mask);
+    carry = cand && !done;
+    if (carry) {
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        r[12 + c] = r[24 + c];
+        r[24 + c] = T(0);
+      }
+    } else if (done && i + 1 < i1) {
+      const T* src = stage + rank * kBlkLd;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        r[c] = T(0);
+        r[12 + c] = src[c];
+        r[24 + c] = src[12 + c];
+      }
+      r[36] = src[24];
+    }
+    __syncwarp();   // stage and pivot buffer reads done before the next panel writes
+  }
+  if (!__all_sync(0xffffffffu, ok) && lane == 0) w.ns[node].singular = 1;
+  // reduced block row of the segment: the carry rows [F | Y | rhs]
+  const int rank = __popc(__ballot_sync(0xffffffffu, carry) & lt_mask);
+  if (carry) {
+    T row[25];
+#pragma unroll
+    for (int c = 0; c < 24; ++c) row[c] = r[c];
+    row[24] = r[36];
+    T* red = static_cast<T*>(w.Red) + (node * smax + s) * int64_t(kBlk);
+    store_row25<T>(red + rank * kBlkLd, row);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_abd_red(SolveArgs a, Workspace w) {
   const int lane = threadIdx.x & 31;
   const int64_t node = blockIdx.x * int64_t(4) + (threadIdx.x >> 5);
   if (node >= a.n) return;
   if (!w.ns[node].active) return;
-  const bool ok = abd_node_reg<T>(a, w, node, a.N[node], lane);
+  const int N = a.N[node];
+  const int smax = seg_count(a.Nmax);
+  const T* red = static_cast<const T*>(w.Red) + node * smax * int64_t(kBlk);
+  T* abd = static_cast<T*>(w.Abd) + node * a.Nmax * int64_t(kBlk);
+  const bool ok = abd_staircase<T>(a, w, node, N, red, seg_count(N), 3 * kSegLen, abd, lane);
   if (!ok && lane == 0) w.ns[node].singular = 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_abd_segback(SolveArgs a, Workspace w) {
+  const int lane = threadIdx.x & 31;
+  const int smax = seg_count(a.Nmax);
+  const int64_t wid = blockIdx.x * int64_t(4) + (threadIdx.x >> 5);
+  const int64_t node = wid / smax;
+  const int s = static_cast<int>(wid % smax);
+  if (node >= a.n) return;
+  if (!w.ns[node].active) return;
+  const int N = a.N[node];
+  if (s >= seg_count(N)) return;
+  const int i0 = s * kSegLen;
+  const int i1 = i0 + kSegLen < N ? i0 + kSegLen : N;
+  if (i1 - i0 < 2) return;
+  double* D = w.D + node * npts(a.Nmax) * 12;
+  const T* seg = static_cast<const T*>(w.Seg) + node * a.Nmax * int64_t(kSegBlk);
+  T dya[12], dyn[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    dya[c] = T(D[3 * int64_t(i0) * 12 + c]);
+    dyn[c] = T(D[3 * int64_t(i1) * 12 + c]);
+  }
+  for (int i = i1 - 1; i > i0; --i) {
+    // lane k holds pivot row k of panel i: [F | U (1/pivot at k) | V | rhs]
+    T r[37];
+#pragma unroll
+    for (int c = 0; c < 37; ++c) r[c] = T(0);
+    if (lane < 12) {
+      T row[40];
+      load_row40<T>(seg + (int64_t(i) * 12 + lane) * kSegLd, row);
+#pragma unroll
+      for (int c = 0; c < 37; ++c) r[c] = row[c];
+    }
+    T tt = r[36];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      tt = fma(-r[c], dya[c], tt);
+      tt = fma(-r[24 + c], dyn[c], tt);
+    }
+#pragma unroll
+    for (int k = 11; k >= 0; --k) {
+      const T dk = __shfl_sync(0xffffffffu, tt * r[12 + k], k);
+      dyn[k] = dk;
+      tt = (lane < k) ? fma(-r[12 + k], dk, tt) : tt;
+    }
+    if (lane < 12) {
+      T mine = T(0);
+#pragma unroll
+      for (int c = 0; c < 12; ++c)
+        if (c == lane) mine = dyn[c];
+      D[3 * int64_t(i) * 12 + lane] = double(mine);
+    }
+  }
 }
 
 // Interior-stage corrections from the stored condensation pivot rows.

@@ -15,10 +15,11 @@
 namespace sg {
 
 // Shared-memory scratch per warp: the FP64 condensation system (36 x 49
-// doubles) or the recovery rows (24 x 52 of T), whichever is larger.
+// doubles), or for FP32 the condensation's pivot table (28 x 52 floats, which
+// also covers the 24 x 52 recovery rows).
 template <typename T>
 __host__ __device__ constexpr int persist_smem_per_warp() {
-  return sizeof(T) == sizeof(double) ? 36 * kCols * 8 : kRec * 4;
+  return sizeof(T) == sizeof(double) ? 36 * kCols * 8 : kCondSmemFloats * 4;
 }
 
 // FP64 residual at Y + alpha D for the whole node, by one warp.  The
@@ -121,7 +122,7 @@ __device__ void solve_node_persistent(const SolveArgs& a, const Workspace& w, in
       bool ok = true;
       for (int i = 0; i < N; ++i) {
         if constexpr (sizeof(T) == sizeof(float)) {
-          condense_interval_reg(a, w, node, i, N, lane);
+          condense_interval_reg(a, w, node, i, N, lane, reinterpret_cast<float*>(scratch));
         } else {
           condense_interval_smem(a, w, node, i, N, lane, reinterpret_cast<double*>(scratch));
         }

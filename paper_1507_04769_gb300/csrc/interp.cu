@@ -263,33 +263,37 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
     }
   }
   level_start.push_back(M);
+  // evaluation order: by the number of active dimensions (so that a kernel
+  // can take each group with a fixed-length basis product), then the
+  // function ids lexicographically
+  std::vector<int> na_of(M, 0);
+  for (int64_t n = 0; n < M; ++n)
+    for (int dim = 0; dim < d; ++dim) na_of[n] += fid[n * d + dim] != 0;
   std::vector<int32_t> order(M);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    if (na_of[a] != na_of[b]) return na_of[a] < na_of[b];
     for (int dim = 0; dim < d; ++dim) {
       if (fid[a * d + dim] != fid[b * d + dim]) return fid[a * d + dim] < fid[b * d + dim];
     }
     return false;
   });
-  std::vector<uint8_t> fid_sorted(M * d), start(M), nact(M, 0);
+  std::vector<uint8_t> nact(M, 0);
   std::vector<uint16_t> ops(M * kMaxDim, 0);
-  for (int64_t r = 0; r < M; ++r) {
+  for (int a = 0; a <= kMaxDim + 1; ++a) s->grp[a] = M;
+  for (int64_t r = M - 1; r >= 0; --r) {
     const int32_t n = order[r];
-    for (int dim = 0; dim < d; ++dim) fid_sorted[r * d + dim] = fid[int64_t(n) * d + dim];
-    int st0 = 0;
-    if (r > 0) {
-      while (st0 < d && fid_sorted[r * d + st0] == fid_sorted[(r - 1) * d + st0]) ++st0;
-      if (st0 == d) st0 = d - 1;
-    }
-    start[r] = static_cast<uint8_t>(st0);
     int na = 0;
     for (int dim = 0; dim < d; ++dim) {
-      const int id = fid_sorted[r * d + dim];
+      const int id = fid[int64_t(n) * d + dim];
       if (id != 0) ops[r * kMaxDim + na++] = static_cast<uint16_t>(dim * s->nf + id);
     }
     nact[r] = static_cast<uint8_t>(na);
     if (na > s->amax) s->amax = na;
+    for (int a = 0; a <= na; ++a) s->grp[a] = r < s->grp[a] ? r : s->grp[a];
   }
+  // grp[a] = first node with at least a active dimensions (non-decreasing)
+  for (int a = kMaxDim; a >= 0; --a) s->grp[a] = s->grp[a] < s->grp[a + 1] ? s->grp[a] : s->grp[a + 1];
 
   uint8_t* d_fid = nullptr;
   int16_t* d_fpt = nullptr;
@@ -308,8 +312,6 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   if ((e = (expr)) != cudaSuccess) return cleanup(e, #expr);
   SG_TRY_CLEAN(cudaMalloc(&s->W, M * k * sizeof(double)));
   SG_TRY_CLEAN(cudaMalloc(&s->Ws, M * k * sizeof(double)));
-  SG_TRY_CLEAN(cudaMalloc(&s->fid_sorted, M * d));
-  SG_TRY_CLEAN(cudaMalloc(&s->start, M));
   SG_TRY_CLEAN(cudaMalloc(&s->nact, M));
   SG_TRY_CLEAN(cudaMalloc(&s->ops, M * kMaxDim * sizeof(uint16_t)));
   SG_TRY_CLEAN(cudaMalloc(&s->box, 2 * d * sizeof(double)));
@@ -328,8 +330,6 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   SG_TRY_CLEAN(cudaMemcpyAsync(s->box, box.data(), 2 * d * sizeof(double), cudaMemcpyHostToDevice, st));
   SG_TRY_CLEAN(cudaMemcpyAsync(d_fid, fid.data(), M * d, cudaMemcpyHostToDevice, st));
   SG_TRY_CLEAN(cudaMemcpyAsync(d_fpt, fpt.data(), M * d * sizeof(int16_t), cudaMemcpyHostToDevice, st));
-  SG_TRY_CLEAN(cudaMemcpyAsync(s->fid_sorted, fid_sorted.data(), M * d, cudaMemcpyHostToDevice, st));
-  SG_TRY_CLEAN(cudaMemcpyAsync(s->start, start.data(), M, cudaMemcpyHostToDevice, st));
   SG_TRY_CLEAN(cudaMemcpyAsync(s->nact, nact.data(), M, cudaMemcpyHostToDevice, st));
   SG_TRY_CLEAN(cudaMemcpyAsync(s->ops, ops.data(), M * kMaxDim * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
   SG_TRY_CLEAN(cudaMemcpyAsync(d_order, order.data(), M * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -370,8 +370,6 @@ extern "C" void sg_surplus_free(sg_surplus* s) {
   if (!s) return;
   if (s->W) cudaFree(s->W);
   if (s->Ws) cudaFree(s->Ws);
-  if (s->fid_sorted) cudaFree(s->fid_sorted);
-  if (s->start) cudaFree(s->start);
   if (s->nact) cudaFree(s->nact);
   if (s->ops) cudaFree(s->ops);
   if (s->box) cudaFree(s->box);
@@ -399,8 +397,6 @@ extern "C" int sg_eval_feedback(const sg_surplus* s, const double* d_xq, int64_t
   e.nf = s->nf;
   e.level = s->level;
   e.amax = s->amax;
-  e.fid = s->fid_sorted;
-  e.start = s->start;
   e.nact = s->nact;
   e.ops = s->ops;
   e.W = s->Ws;
@@ -409,6 +405,7 @@ extern "C" int sg_eval_feedback(const sg_surplus* s, const double* d_xq, int64_t
   e.xf = s->xf;
   e.xfdf = s->xfdf;
   e.Wdf = s->Wdf;
+  for (int a = 0; a <= kMaxDim + 1; ++a) e.grp[a] = s->grp[a];
   e.out = d_out;
   if (mode == SG_EVAL_FP64) return eval_fp64(e, s->d, st);
   if (mode == SG_EVAL_TF32X3) return eval_tf32x3(e, s, st);

@@ -17,8 +17,6 @@ struct EvalArgs {
   int nf;
   int level;
   int amax;               // largest number of active dimensions over the nodes
-  const uint8_t* fid;     // M x d, evaluation order
-  const uint8_t* start;   // M
   const uint8_t* nact;    // M: number of active (level >= 2) dimensions
   const uint16_t* ops;    // M x kMaxDim: table offsets dim * nf + id of the active dimensions
   const double* W;        // M x k, evaluation order
@@ -27,6 +25,7 @@ struct EvalArgs {
   const double* xf;       // 2^L + 1 points of the finest 1-D set
   const float2* xfdf;     // the same points as (hi, lo) float pairs
   const float2* Wdf;      // M x k surpluses as (hi, lo) pairs, evaluation order
+  int64_t grp[kMaxDim + 2];  // grp[a]: first node (evaluation order) with >= a active dimensions
   double* out;            // Q x k
 };
 
@@ -43,9 +42,8 @@ struct sg_surplus {
   int64_t M = 0;
   double* W = nullptr;            // M x k, grid order
   double* Ws = nullptr;           // M x k, evaluation order
-  uint8_t* fid_sorted = nullptr;  // M x d
-  uint8_t* start = nullptr;       // M
-  uint8_t* nact = nullptr;        // M
+  uint8_t* nact = nullptr;        // M, evaluation order (sorted by this count)
+  int64_t grp[sg::kMaxDim + 2] = {};  // first node with >= a active dimensions
   uint16_t* ops = nullptr;        // M x kMaxDim
   double* box = nullptr;          // lo[d], (hi-lo)[d]
   double* xf = nullptr;           // finest 1-D set, 2^L + 1 points

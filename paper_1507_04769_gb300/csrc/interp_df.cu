@@ -19,120 +19,192 @@
 
 namespace sg {
 
-constexpr int kFoldBlock = 64;     // nodes per FP64 fold of the compensated sums
-constexpr int kChunk = 128;        // nodes staged in shared memory at a time
+constexpr int kFoldBlock = 64;     // nodes per FP64 fold of the compensated sums (per warp)
+constexpr int kDfQ = 32;           // queries per block (one per lane)
+constexpr int kDfWarps = 4;        // warps per block; warp w takes the nodes m = w (mod kDfWarps)
+constexpr int kDfThreads = 32 * kDfWarps;
+constexpr int kDfChunk = 128;      // nodes staged in shared memory at a time
 
-// Node loop of the pair-of-floats evaluation.  Every node has exactly A table
-// factors (padded with table entry 0, the exact constant 1), so the loop has
-// no data-dependent branch.  Offsets and surpluses of kChunk nodes are staged
-// in shared memory by the whole block with coalesced loads.
+// Product of a pair with a pair, left unnormalised: the result (p, e) has
+// p = fl(a.hi b.hi) and e = the exact rounding error of p plus the cross
+// terms, so p + e carries the product to about 2^-46 relative.  Skipping the
+// renormalisation is safe because |e| stays below about 2^-22 |p| and every
+// consumer (the next product, the compensated dot) treats hi and lo only
+// through products and exact sums.
+__device__ __forceinline__ df df_mul_raw(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return {p, e};
+}
+
+struct DfAcc {
+  double total;
+  float ah, al;
+};
+
+// Nodes [n0, n1) of the staged chunk with exactly A active factors; this
+// warp takes those with index = warp (mod kDfWarps).  off_s: byte offsets of
+// the node's table rows (kMaxDim slots), w_s: K surplus pairs per node.
 template <int K, int A>
-__global__ void __launch_bounds__(kEvalThreads) k_eval_df32(EvalArgs e, int d) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tab = reinterpret_cast<float2*>(smem_raw);
-  const int nf = e.nf;
-  float2* wch = tab + size_t(d) * nf * kEvalThreads;                 // kChunk x K
-  uint16_t* och = reinterpret_cast<uint16_t*>(wch + kChunk * K);    // kChunk x A
-  const int tid = threadIdx.x;
-  const int64_t q = blockIdx.x * int64_t(kEvalThreads) + tid;
-  const bool live = q < e.Q;
-  for (int dim = 0; dim < d; ++dim) {
-    const double u = live ? (e.xq[q * d + dim] - e.lo[dim]) / e.width[dim] : 0.5;
-    basis_row_df(u, e.level, e.xfdf, tab + (dim * nf) * kEvalThreads + tid, kEvalThreads);
-  }
-  double total[K];
-  float ah[K], al[K];
-#pragma unroll
-  for (int c = 0; c < K; ++c) {
-    total[c] = 0.0;
-    ah[c] = 0.0f;
-    al[c] = 0.0f;
-  }
-  auto T = [&](int off) {
-    const float2 v = tab[off * kEvalThreads + tid];
-    return df{v.x, v.y};
-  };
-  int since_fold = 0;
-  for (int64_t m0 = 0; m0 < e.M; m0 += kChunk) {
-    const int cn = e.M - m0 < kChunk ? static_cast<int>(e.M - m0) : kChunk;
-    __syncthreads();   // tables written / previous chunk consumed
-    for (int x = tid; x < cn * K; x += kEvalThreads) wch[x] = e.Wdf[m0 * K + x];
-    for (int x = tid; x < cn * A; x += kEvalThreads) {
-      const int nn = x / A, j = x % A;
-      och[x] = e.ops[(m0 + nn) * kMaxDim + j];
-    }
-    __syncthreads();
+__device__ __forceinline__ void df_group(const unsigned char* __restrict__ tab_q, const uint32_t* __restrict__ off_s,
+                                         const float2* __restrict__ w_s, int n0, int n1, int warp, DfAcc (&acc)[K],
+                                         int& since_fold) {
+  int nn = n0 + ((warp - n0) % kDfWarps + kDfWarps) % kDfWarps;
 #pragma unroll 2
-    for (int nn = 0; nn < cn; ++nn) {
-      df phi = T(och[nn * A]);
+  for (; nn < n1; nn += kDfWarps) {
+    df phi = {1.0f, 0.0f};
+    if constexpr (A > 0) {
+      uint32_t o[A];
+      if constexpr (A <= 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(off_s + nn * kMaxDim);
+        const uint32_t t[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int j = 1; j < A; ++j) phi = df_mul(phi, T(och[nn * A + j]));
+        for (int a = 0; a < A; ++a) o[a] = t[a];
+      } else {
+        const uint4 v0 = *reinterpret_cast<const uint4*>(off_s + nn * kMaxDim);
+        const uint4 v1 = *reinterpret_cast<const uint4*>(off_s + nn * kMaxDim + 4);
+        const uint32_t t[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int a = 0; a < A; ++a) o[a] = t[a];
+      }
+      const float2 f0 = *reinterpret_cast<const float2*>(tab_q + o[0]);
+      phi = {f0.x, f0.y};
+#pragma unroll
+      for (int a = 1; a < A; ++a) {
+        const float2 f = *reinterpret_cast<const float2*>(tab_q + o[a]);
+        phi = df_mul_raw(phi, {f.x, f.y});
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const float2 wc = w_s[nn * K + c];
+      // exact product phi.hi * w.hi = p + pe; cross terms to t
+      const float p = __fmul_rn(phi.hi, wc.x);
+      const float pe = __fmaf_rn(phi.hi, wc.x, -p);
+      const float t = __fadd_rn(__fmaf_rn(phi.hi, wc.y, __fmul_rn(phi.lo, wc.x)), pe);
+      // Knuth's two_sum of the running sum and p
+      const float s = __fadd_rn(acc[c].ah, p);
+      const float bb = __fsub_rn(s, acc[c].ah);
+      const float se = __fadd_rn(__fsub_rn(acc[c].ah, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+      acc[c].ah = s;
+      acc[c].al = __fadd_rn(acc[c].al, __fadd_rn(se, t));
+    }
+    if (++since_fold == kFoldBlock) {
+      since_fold = 0;
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        const float2 wc = wch[nn * K + c];
-        const float p = __fmul_rn(phi.hi, wc.x);
-        const float pe = __fmaf_rn(phi.hi, wc.x, -p);
-        const float t = __fadd_rn(__fmaf_rn(phi.hi, wc.y, __fmul_rn(phi.lo, wc.x)), pe);
-        const float s = __fadd_rn(ah[c], p);
-        const float bb = __fsub_rn(s, ah[c]);
-        const float se = __fadd_rn(__fsub_rn(ah[c], __fsub_rn(s, bb)), __fsub_rn(p, bb));
-        ah[c] = s;
-        al[c] = __fadd_rn(al[c], __fadd_rn(se, t));
-      }
-      if (++since_fold == kFoldBlock) {
-        since_fold = 0;
-#pragma unroll
-        for (int c = 0; c < K; ++c) {
-          total[c] += static_cast<double>(ah[c]) + static_cast<double>(al[c]);
-          ah[c] = 0.0f;
-          al[c] = 0.0f;
-        }
+        acc[c].total += static_cast<double>(acc[c].ah) + static_cast<double>(acc[c].al);
+        acc[c].ah = 0.0f;
+        acc[c].al = 0.0f;
       }
     }
   }
-  if (live) {
+}
+
+// Block = kDfQ queries x kDfWarps node streams.  The d x nf basis table of
+// each query (pairs) is built once in shared memory and shared by the
+// block's warps; lane q of every warp evaluates query q over its share of the
+// nodes, and the warps' partial sums are added in FP64 in a fixed order.
+// Nodes come in the evaluation order, grouped by their number of active
+// dimensions A, so every group runs a loop with a fixed-length product.
+template <int K>
+__global__ void __launch_bounds__(kDfThreads) k_eval_df32(EvalArgs e, int d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nf = e.nf;
+  const int tab_bytes = d * nf * kDfQ * static_cast<int>(sizeof(float2));
+  float2* tab = reinterpret_cast<float2*>(smem_raw);                                  // [d*nf][kDfQ]
+  uint32_t* off_s = reinterpret_cast<uint32_t*>(smem_raw + tab_bytes);                 // [kDfChunk][kMaxDim]
+  float2* w_s = reinterpret_cast<float2*>(off_s + kDfChunk * kMaxDim);                 // [kDfChunk][K]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t qbase = blockIdx.x * int64_t(kDfQ);
+
+  // basis tables: (query, dim) tasks over the block
+  for (int task = tid; task < kDfQ * d; task += kDfThreads) {
+    const int ql = task % kDfQ, dim = task / kDfQ;
+    const int64_t q = qbase + ql;
+    const double u = q < e.Q ? (e.xq[q * d + dim] - e.lo[dim]) / e.width[dim] : 0.5;
+    basis_row_df(u, e.level, e.xfdf, tab + (dim * nf) * kDfQ + ql, kDfQ);
+  }
+  const unsigned char* tab_q = reinterpret_cast<const unsigned char*>(tab + lane);
+
+  DfAcc acc[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c)
-      e.out[q * K + c] = total[c] + (static_cast<double>(ah[c]) + static_cast<double>(al[c]));
+  for (int c = 0; c < K; ++c) acc[c] = {0.0, 0.0f, 0.0f};
+  int since_fold = 0;
+  for (int64_t m0 = 0; m0 < e.M; m0 += kDfChunk) {
+    const int cn = e.M - m0 < kDfChunk ? static_cast<int>(e.M - m0) : kDfChunk;
+    __syncthreads();   // tables written / previous chunk consumed
+    for (int x = tid; x < cn * kMaxDim; x += kDfThreads) {
+      const int nn = x / kMaxDim, j = x % kMaxDim;
+      // table row (dim * nf + id) -> byte offset within the query column
+      off_s[x] = static_cast<uint32_t>(e.ops[(m0 + nn) * kMaxDim + j]) * (kDfQ * sizeof(float2));
+    }
+    for (int x = tid; x < cn * K; x += kDfThreads) w_s[x] = e.Wdf[m0 * K + x];
+    __syncthreads();
+    // groups of equal active-dimension count that meet this chunk
+    for (int a = 0; a <= kMaxDim; ++a) {
+      const int64_t g0 = e.grp[a] > m0 ? e.grp[a] : m0;
+      const int64_t g1 = e.grp[a + 1] < m0 + cn ? e.grp[a + 1] : m0 + cn;
+      if (g0 >= g1) continue;
+      const int n0 = static_cast<int>(g0 - m0), n1 = static_cast<int>(g1 - m0);
+      switch (a) {
+        case 0: df_group<K, 0>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
+        case 1: df_group<K, 1>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
+        case 2: df_group<K, 2>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
+        case 3: df_group<K, 3>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
+        case 4: df_group<K, 4>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
+        case 5: df_group<K, 5>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
+        case 6: df_group<K, 6>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
+        case 7: df_group<K, 7>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
+        default: df_group<K, 8>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
+      }
+    }
+  }
+  // warps' partial sums, added in warp order
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(smem_raw);   // [kDfWarps][kDfQ][K], over the tables
+#pragma unroll
+  for (int c = 0; c < K; ++c)
+    red[(warp * kDfQ + lane) * K + c] =
+        acc[c].total + (static_cast<double>(acc[c].ah) + static_cast<double>(acc[c].al));
+  __syncthreads();
+  if (warp == 0) {
+    const int64_t q = qbase + lane;
+    if (q < e.Q) {
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        double v = red[lane * K + c];
+        for (int w = 1; w < kDfWarps; ++w) v += red[(w * kDfQ + lane) * K + c];
+        e.out[q * K + c] = v;
+      }
+    }
   }
 }
 
 template <int K>
-static int launch_df32_k(const EvalArgs& e, int d, int A, cudaStream_t st) {
-  const size_t smem = sizeof(float2) * d * e.nf * kEvalThreads + sizeof(float2) * kChunk * K +
-                      sizeof(uint16_t) * kChunk * kMaxDim;
+static int launch_df32_k(const EvalArgs& e, int d, cudaStream_t st) {
+  const size_t tab = sizeof(float2) * d * e.nf * kDfQ;
+  const size_t red = sizeof(double) * kDfWarps * kDfQ * K;
+  const size_t smem = (tab > red ? tab : red) + sizeof(uint32_t) * kDfChunk * kMaxDim + sizeof(float2) * kDfChunk * K;
   if (smem > 220 * 1024) return fail(SG_EUNSUPPORTED, "sg_eval_feedback: grid level too high for the DF32 kernel");
-  const unsigned blocks = static_cast<unsigned>(ceil_div(e.Q, kEvalThreads));
-#define SG_DF_A(AA)                                                                                  \
-  case AA:                                                                                           \
-    SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_df32<K, AA>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     static_cast<int>(smem)));                                       \
-    SG_TIMED("k_eval_df32", st, (k_eval_df32<K, AA><<<blocks, kEvalThreads, smem, st>>>(e, d)));     \
-    break;
-  switch (A) {
-    SG_DF_A(1)
-    SG_DF_A(2)
-    SG_DF_A(3)
-    SG_DF_A(4)
-    SG_DF_A(5)
-    SG_DF_A(6)
-    SG_DF_A(7)
-    SG_DF_A(8)
-    default: return fail(SG_EINVAL, "sg_eval_feedback: bad active-dimension count");
-  }
-#undef SG_DF_A
+  if (sizeof(float2) * d * e.nf * kDfQ > 0xffffffffu)
+    return fail(SG_EUNSUPPORTED, "sg_eval_feedback: table too large for the DF32 kernel");
+  const unsigned blocks = static_cast<unsigned>(ceil_div(e.Q, kDfQ));
+  SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_df32<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  SG_TIMED("k_eval_df32", st, (k_eval_df32<K><<<blocks, kDfThreads, smem, st>>>(e, d)));
   SG_LAUNCH_CHECK("k_eval_df32");
   return SG_OK;
 }
 
 int eval_df32(const EvalArgs& e, int d, cudaStream_t st) {
-  const int A = e.amax < 1 ? 1 : e.amax;
   switch (e.k) {
-    case 1: return launch_df32_k<1>(e, d, A, st);
-    case 2: return launch_df32_k<2>(e, d, A, st);
-    case 3: return launch_df32_k<3>(e, d, A, st);
-    case 4: return launch_df32_k<4>(e, d, A, st);
-    case 6: return launch_df32_k<6>(e, d, A, st);
+    case 1: return launch_df32_k<1>(e, d, st);
+    case 2: return launch_df32_k<2>(e, d, st);
+    case 3: return launch_df32_k<3>(e, d, st);
+    case 4: return launch_df32_k<4>(e, d, st);
+    case 6: return launch_df32_k<6>(e, d, st);
     default: return fail(SG_EUNSUPPORTED, "sg_eval_feedback: SG_EVAL_DF32 supports k = 1, 2, 3, 4, 6");
   }
 }
