@@ -280,6 +280,14 @@ int sg_timing_collect(int max_kernels, char* names, int name_len, double* total_
 int sg_fma_probe(int precision, void* d_scratch, size_t scratch_bytes, int blocks, int threads,
                  int iters, double* flops_per_launch, void* stream);
 
+/* Evaluates the library's FP64 sine and cosine (the ones inside the
+ * characteristic right-hand side: Taylor polynomials on |x| <= pi/4, the CUDA
+ * library beyond) at n points.  d_x, d_s, d_c: n doubles each on the device
+ * (caller-owned).  Used to test those functions against a reference and an
+ * error bound.  Asynchronous on `stream`; SG_EINVAL for n < 0 or null
+ * pointers with n > 0. */
+int sg_sincos_probe(const double* d_x, int64_t n, double* d_s, double* d_c, void* stream);
+
 /* ---------------------------------------------------------------- closed loop
  * sg_simulate_closed_loop - the on-line phase of Section 3.3 run against the
  * plant: zero-order hold as in the model predictive control of Section 5.  At

@@ -146,7 +146,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
   const int64_t npoint = a.n * P;
   const int64_t nint = a.n * a.Nmax;
   const unsigned gp = static_cast<unsigned>(ceil_div(npoint, 128));
-  const unsigned gi = static_cast<unsigned>(ceil_div(nint, 128));
+  const unsigned gi = static_cast<unsigned>(a.n * trial_chunks(a.Nmax));
   const unsigned gnode_thr = static_cast<unsigned>(ceil_div(a.n, 128));
   const unsigned gnode_warp = static_cast<unsigned>(ceil_div(a.n * 32, 128));
   const unsigned gwarp_int = static_cast<unsigned>(ceil_div(nint, 4));
@@ -303,7 +303,7 @@ static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, dou
   const int64_t P = npts(a.Nmax);
   const int64_t nint = a.n * a.Nmax;
   const unsigned gp = static_cast<unsigned>(ceil_div(a.n * P, 128));
-  const unsigned gi = static_cast<unsigned>(ceil_div(nint, 128));
+  const unsigned gi = static_cast<unsigned>(a.n * trial_chunks(a.Nmax));
   const unsigned gnt = static_cast<unsigned>(ceil_div(a.n, 128));
   const unsigned gnw = static_cast<unsigned>(ceil_div(a.n * 32, 128));
   const unsigned gwi = static_cast<unsigned>(ceil_div(nint, 4));

@@ -57,6 +57,7 @@ struct NodeState {
 
 constexpr int kCols = 49;        // 24 interior + 12 (y_i) + 12 (y_{i+1}) + rhs
 constexpr int kRecLd = 52;       // row stride of a stored interior pivot row (16-byte multiple)
+constexpr int kRecInv = 49;      // column of a stored pivot row holding 1/pivot
 constexpr int kRec = 24 * kRecLd;
 constexpr int kBlkLd = 28;       // row stride of a 12-row block of 25 columns
 constexpr int kBlk = 12 * kBlkLd;
@@ -132,69 +133,97 @@ __global__ void k_init(SolveArgs a, Workspace w) {
 }
 
 // ---------------------------------------------------------------- residual
-// FP64 residual at Y + alpha D for one interval: stage rows 2..4 (the first
-// interval adds the x(0) rows, the last the lambda(T) rows).  Writes the
-// partial |.|_2^2 and |.|_inf, and the 36 stage rows (precision T) for the
-// next condensation.
+// FP64 residual at Y + alpha D.  A block takes kTrialIv consecutive intervals
+// of one node: first every thread evaluates F at one collocation point of the
+// chunk (3 kTrialIv + 1 <= 128 points, so the shared end points are evaluated
+// once), then the stage rows 2..4 of each interval are formed from the
+// points in shared memory (the first interval adds the x(0) rows, the last
+// the lambda(T) rows).  Writes the partial |.|_2^2 and |.|_inf per interval
+// and the 36 stage rows (precision T) for the next condensation.
+constexpr int kTrialIv = 42;                     // intervals per block
+constexpr int kTrialPts = 3 * kTrialIv + 1;      // 127 points
+
+__host__ __device__ __forceinline__ int trial_chunks(int Nmax) { return (Nmax + kTrialIv - 1) / kTrialIv; }
+
 template <typename T>
-__global__ void k_trial(SolveArgs a, Workspace w) {
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= a.n * a.Nmax) return;
-  const int64_t node = t / a.Nmax;
-  const int i = static_cast<int>(t % a.Nmax);
+__global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
+  __shared__ double ys[kTrialPts][12];
+  __shared__ double fs[kTrialPts][12];
+  __shared__ double part_s[3 * kTrialIv][2];
+  const int tid = threadIdx.x;
+  const int nchunk = trial_chunks(a.Nmax);
+  const int64_t node = blockIdx.x / nchunk;
+  const int i0 = static_cast<int>(blockIdx.x % nchunk) * kTrialIv;
+  if (node >= a.n) return;
   const NodeState& s = w.ns[node];
   if (!s.searching) return;
   const int N = a.N[node];
-  if (i >= N) return;
-  const double h = a.T[node] / N;
+  if (i0 >= N) return;
+  const int niv = N - i0 < kTrialIv ? N - i0 : kTrialIv;
   const double alpha = s.alpha;
-  const int64_t base = (node * npts(a.Nmax) + 3 * int64_t(i)) * 12;
-  double y[4][12], F[4][12];
+  const int64_t base = node * npts(a.Nmax) + 3 * int64_t(i0);
+  if (tid <= 3 * niv) {
+    double y[12], F[12];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-#pragma unroll
-    for (int c = 0; c < 12; ++c) y[j][c] = __fma_rn(alpha, w.D[base + 12 * j + c], w.Y[base + 12 * j + c]);
-    char_rhs(a.P, y[j], F[j]);
-  }
-  T* res = static_cast<T*>(w.Res) + t * kResRows;
-  double ss = 0.0, mx = 0.0;
-  bool bad = false;
-#pragma unroll
-  for (int k = 1; k < 4; ++k) {
+    for (int c = 0; c < 12; ++c) y[c] = __fma_rn(alpha, w.D[(base + tid) * 12 + c], w.Y[(base + tid) * 12 + c]);
+    char_rhs(a.P, y, F);
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
-      const double r = y[k][c] - y[0][c] -
-                       h * (kLobA[k][0] * F[0][c] + kLobA[k][1] * F[1][c] + kLobA[k][2] * F[2][c] +
-                            kLobA[k][3] * F[3][c]);
-      res[12 * (k - 1) + c] = static_cast<T>(r);
+      ys[tid][c] = y[c];
+      fs[tid][c] = F[c];
+    }
+  }
+  __syncthreads();
+  const double h = a.T[node] / N;
+  if (tid < 3 * niv) {
+    // interval j = tid / 3 of the chunk, stage row block k = tid % 3 + 1
+    const int j = tid / 3, k = tid % 3 + 1;
+    const int p0 = 3 * j;
+    T* res = static_cast<T*>(w.Res) + (node * a.Nmax + i0 + j) * kResRows + 12 * (k - 1);
+    double ss = 0.0, mx = 0.0;
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      const double r = ys[p0 + k][c] - ys[p0][c] -
+                       h * (kLobA[k][0] * fs[p0][c] + kLobA[k][1] * fs[p0 + 1][c] + kLobA[k][2] * fs[p0 + 2][c] +
+                            kLobA[k][3] * fs[p0 + 3][c]);
+      res[c] = static_cast<T>(r);
       bad = bad || !isfinite(r);
       ss += r * r;
       mx = fmax(mx, fabs(r));
     }
-  }
-  if (i == 0) {
-    const double* x0 = a.x0 + node * 6;
-    for (int c = 0; c < 6; ++c) {
-      const double r = y[0][c] - x0[c];
-      bad = bad || !isfinite(r);
-      ss += r * r;
-      mx = fmax(mx, fabs(r));
+    if (k == 1 && i0 + j == 0) {
+      const double* x0 = a.x0 + node * 6;
+      for (int c = 0; c < 6; ++c) {
+        const double r = ys[0][c] - x0[c];
+        bad = bad || !isfinite(r);
+        ss += r * r;
+        mx = fmax(mx, fabs(r));
+      }
     }
-  }
-  if (i == N - 1) {
-    for (int c = 0; c < 6; ++c) {
-      const double r = y[3][6 + c] - terminal_grad(a.P, y[3], c);
-      bad = bad || !isfinite(r);
-      ss += r * r;
-      mx = fmax(mx, fabs(r));
+    if (k == 3 && i0 + j == N - 1) {
+      for (int c = 0; c < 6; ++c) {
+        const double r = ys[p0 + 3][6 + c] - terminal_grad(a.P, ys[p0 + 3], c);
+        bad = bad || !isfinite(r);
+        ss += r * r;
+        mx = fmax(mx, fabs(r));
+      }
     }
+    if (bad) {
+      ss = INFINITY;
+      mx = INFINITY;
+    }
+    part_s[tid][0] = ss;
+    part_s[tid][1] = mx;
   }
-  if (bad) {
-    ss = INFINITY;
-    mx = INFINITY;
+  __syncthreads();
+  if (tid < niv) {
+    const double ss = part_s[3 * tid][0] + part_s[3 * tid + 1][0] + part_s[3 * tid + 2][0];
+    const double mx = fmax(fmax(part_s[3 * tid][1], part_s[3 * tid + 1][1]), part_s[3 * tid + 2][1]);
+    const int64_t t = node * a.Nmax + i0 + tid;
+    w.part[2 * t] = ss;
+    w.part[2 * t + 1] = mx;
   }
-  w.part[2 * t] = ss;
-  w.part[2 * t + 1] = mx;
 }
 
 // Warp per node: reduce the partial norms in a fixed order and decide.
@@ -307,6 +336,11 @@ __device__ __forceinline__ void store_row25(T* __restrict__ dst, const T (&r)[25
   dst[24] = r[24];
 }
 
+// Correctly rounded reciprocal (the same value as 1 / x, without the
+// division's slow-path branch).
+__device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
+
 // 37-entry rows (F | Y | Z | rhs) as 40-entry vectors (16-byte accesses).
 template <typename T>
 __device__ __forceinline__ void store_row40(T* __restrict__ dst, const T (&r)[37]) {
@@ -373,19 +407,25 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
 }
 
 // ---------------------------------------------------------------- condensation
-// Register-resident FP32 form: warp per interval.  Lane r holds equation row
-// r of the 36 x 49 system: lanes 0..23 the interior rows (stages 2 and 3),
-// lanes 24..31 the stage-4 rows 24..31.  Pivoting is over the 24 interior
-// rows and rows never move.  At step k the pivot lane writes its row
-// (columns from k rounded down to a multiple of 4) to the shared-memory pivot
-// table, and every lane reads it back with 16-byte broadcast loads: one load
-// brings four columns, where a shuffle brings one.  The table, in pivot order,
-// is then the stored interior pivot rows for the stage recovery.  The four
-// stage-4 rows 32..35 are built in shared memory and eliminated afterwards
-// against the same table with the columns spread over the lanes, so no lane
-// carries a second row through the main elimination.
-constexpr int kCondPivLd = kRecLd;                   // 52 floats per pivot row
-constexpr int kCondSmemFloats = 28 * kCondPivLd;     // 24 pivot rows + 4 late stage-4 rows
+// Register-resident FP32 form, warp per interval, in two phases.
+//
+// The 36 x 49 system splits into the 24 interior columns (stages 2 and 3,
+// eliminated) and the 25 passive columns [y_i | y_{i+1} | rhs].
+//   Phase A (rows on lanes): lane r holds interior row r (r < 24) or stage-4
+//   row r (24..31); lanes 24..27 also hold stage-4 rows 32..35.  Only the 24
+//   interior columns live in registers.  Partial pivoting over the interior
+//   rows; at step k the pivot lane publishes its row and 1/pivot in the
+//   shared-memory table U (16-byte broadcast reads), and every row records
+//   its multiplier l(r, k) in L.
+//   Phase B (columns on lanes): lane c < 25 owns passive column c.  With the
+//   pivot order p_k, the passive part of pivot row k is
+//       Q_k = P(p_k) - sum_{j<k} l(p_k, j) Q_j
+//   and the condensed stage-4 rows are P(r) - sum_k l(r, k) Q_k, where P is
+//   the original passive block (built into shared memory).
+// Rows never move.  The stored recovery rows are [U_k | Q_k] in pivot order
+// (raw pivot on the diagonal), the condensed block row is [S | T | rhs].
+constexpr int kCondLd = 28;                          // row stride of P, L and U (floats)
+constexpr int kCondSmemFloats = 36 * kCondLd * 2 + 24 * kCondLd + 32;   // P, L, U, pivot order
 
 __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const Workspace& w, int64_t node,
                                                       int i, int N, int lane, float* __restrict__ sm) {
@@ -394,33 +434,16 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
   const int64_t pbase = node * npts(a.Nmax) + 3 * int64_t(i);
   const float* J = static_cast<const float*>(w.Jm) + pbase * 144;
   const float* res = static_cast<const float*>(w.Res) + wid * kResRows;
-  float* piv_s = sm;                        // [24][kCondPivLd]
-  float* late_s = sm + 24 * kCondPivLd;     // [4][kCondPivLd], rows 32..35
+  float* P_s = sm;                         // [36][kCondLd] passive columns, original
+  float* L_s = sm + 36 * kCondLd;          // [36][kCondLd] multipliers l(r, k)
+  float* U_s = sm + 72 * kCondLd;          // [24][kCondLd] pivot rows (interior part), 1/pivot at 24
+  int* perm_s = reinterpret_cast<int*>(sm + 96 * kCondLd);   // [24] pivot row of step k
 
-  // late rows r = 32 + q (stage 4, component 8 + q), column-parallel build:
-  // column c < 24 -> interior stage 2 + c / 12; 24..35 -> y_i; 36..47 -> y_{i+1}
-  for (int e = lane; e < 4 * kCols; e += 32) {
-    const int q = e / kCols, c = e % kCols;
-    const int comp = 8 + q;
-    float v;
-    if (c == 48) {
-      v = -res[32 + q];
-    } else {
-      const int j = c < 24 ? 1 + c / 12 : (c < 36 ? 0 : 3);
-      const int cc = c < 24 ? c % 12 : (c < 36 ? c - 24 : c - 36);
-      v = -hf * kLobAf[3][j] * J[j * 144 + comp * 12 + cc];
-      if (cc == comp) {
-        if (j == 3) v += 1.0f;
-        if (j == 0) v -= 1.0f;
-      }
-    }
-    late_s[q * kCondPivLd + c] = v;
-  }
-
-  // row r = 12 (k - 1) + comp for stage k = 1, 2, 3 (Lobatto stages 2, 3, 4)
-  float ra[kCols];
-  {
-    const int k = lane / 12 + 1, comp = lane % 12;
+  // row r = 12 (k - 1) + comp for stage k = 1, 2, 3 (Lobatto stages 2, 3, 4):
+  // interior part to act[24], passive part to P_s[r]
+  auto build = [&](int r, float (&act)[24]) {
+    const int k = r / 12 + 1, comp = r % 12;
+    float v[48];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float cf = -hf * kLobAf[k][j];
@@ -428,112 +451,135 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
       const int c0 = j == 0 ? 24 : (j == 3 ? 36 : 12 * (j - 1));
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const float4 v = src[q];
-        ra[c0 + 4 * q + 0] = cf * v.x;
-        ra[c0 + 4 * q + 1] = cf * v.y;
-        ra[c0 + 4 * q + 2] = cf * v.z;
-        ra[c0 + 4 * q + 3] = cf * v.w;
+        const float4 x = src[q];
+        v[c0 + 4 * q + 0] = cf * x.x;
+        v[c0 + 4 * q + 1] = cf * x.y;
+        v[c0 + 4 * q + 2] = cf * x.z;
+        v[c0 + 4 * q + 3] = cf * x.w;
       }
     }
-    // +I on the stage's own point, -I on y_i (compare against every column
-    // so that register indices stay static)
-    const int plus = k < 3 ? 12 * (k - 1) + comp : 36 + comp;
-    const int minus = 24 + comp;
+    // +I on the stage's own point, -I on y_i
 #pragma unroll
-    for (int c = 0; c < 48; ++c) {
-      if (c == plus) ra[c] += 1.0f;
-      if (c == minus) ra[c] -= 1.0f;
+    for (int t = 0; t < 12; ++t) {
+      if (t == comp) {
+        if (k == 1) v[t] += 1.0f;
+        if (k == 2) v[12 + t] += 1.0f;
+        if (k == 3) v[36 + t] += 1.0f;
+        v[24 + t] -= 1.0f;
+      }
     }
-    ra[48] = -res[lane];
+#pragma unroll
+    for (int c = 0; c < 24; ++c) act[c] = v[c];
+    float4* dst = reinterpret_cast<float4*>(P_s + r * kCondLd);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) dst[q] = make_float4(v[24 + 4 * q], v[25 + 4 * q], v[26 + 4 * q], v[27 + 4 * q]);
+    P_s[r * kCondLd + 24] = -res[r];
+  };
+
+  const bool hasb = lane >= 24 && lane < 28;
+  float ra[24], rb[24];
+  build(lane, ra);
+  if (hasb) {
+    build(8 + lane, rb);   // rows 32..35
+  } else {
+#pragma unroll
+    for (int c = 0; c < 24; ++c) rb[c] = 0.0f;
   }
 
+  // ---- phase A: interior columns
   const bool interior = lane < 24;
   bool done = false;
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < 24; ++k) {
-    constexpr int kLast = kCols / 4;   // float4 index holding column 48
     const int q0 = k / 4;
     const int p = warp_pivot_lane<float>(ra[k], interior && !done, lane);
     if (lane == p) {
-      float4* dst = reinterpret_cast<float4*>(piv_s + k * kCondPivLd);
+      const float pv = ra[k];
+      const float inv = (pv != 0.0f && isfinite(pv)) ? __frcp_rn(pv) : 0.0f;
+      float4* dst = reinterpret_cast<float4*>(U_s + k * kCondLd);
 #pragma unroll
-      for (int q = q0; q < kLast; ++q) dst[q] = make_float4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
-      dst[kLast] = make_float4(ra[48], 0.0f, 0.0f, 0.0f);
+      for (int q = q0; q < 6; ++q) dst[q] = make_float4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
+      dst[6] = make_float4(inv, 0.0f, 0.0f, 0.0f);
+      perm_s[k] = lane;
       done = true;
     }
     __syncwarp();
-    const float4* src = reinterpret_cast<const float4*>(piv_s + k * kCondPivLd);
-    const float4 first = src[q0];
-    const float piv = (k & 3) == 0 ? first.x : (k & 3) == 1 ? first.y : (k & 3) == 2 ? first.z : first.w;
-    const bool good = piv != 0.0f && isfinite(piv);
-    ok = ok && good;
-    const float inv = good ? 1.0f / piv : 0.0f;
+    const float4* src = reinterpret_cast<const float4*>(U_s + k * kCondLd);
+    const float inv = src[6].x;
+    ok = ok && inv != 0.0f;
     const float la = (interior && done) ? 0.0f : ra[k] * inv;
+    const float lb = hasb ? rb[k] * inv : 0.0f;
 #pragma unroll
-    for (int q = q0; q <= kLast; ++q) {
-      const float4 v = q == q0 ? first : src[q];
-      const float pv[4] = {v.x, v.y, v.z, v.w};
+    for (int q = q0; q < 6; ++q) {
+      const float4 u4 = src[q];
+      const float u[4] = {u4.x, u4.y, u4.z, u4.w};
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int c = 4 * q + t;
-        if (c > k && c < kCols) ra[c] = fmaf(-la, pv[t], ra[c]);
+        if (c > k) {
+          ra[c] = fmaf(-la, u[t], ra[c]);
+          rb[c] = fmaf(-lb, u[t], rb[c]);
+        }
       }
     }
+    L_s[lane * kCondLd + k] = la;
+    if (hasb) L_s[(8 + lane) * kCondLd + k] = lb;
   }
   if (!ok && lane == 0) w.ns[node].singular = 1;
+  __syncwarp();
 
-  // late rows against the pivot table: lane holds columns lane and lane + 32
-  const bool has_hi = lane + 32 < kCols;   // lanes 0..16 hold columns 32..48
-  float lo[4], hi[4];
+  // ---- phase B: passive columns
+  const int64_t blk = node * a.Nmax + i;
+  float* rec = static_cast<float*>(w.Rec) + blk * kRec;
+  float* cond = static_cast<float*>(w.Cond) + blk * kBlk;
+  const bool col = lane < 25;
+  const int cl = col ? lane : 0;
+  float Q[24];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    lo[q] = late_s[q * kCondPivLd + lane];
-    hi[q] = has_hi ? late_s[q * kCondPivLd + lane + 32] : 0.0f;
+  for (int k = 0; k < 24; ++k) {
+    const int pk = perm_s[k];
+    float x = P_s[pk * kCondLd + cl];
+    const float4* l4 = reinterpret_cast<const float4*>(L_s + pk * kCondLd);
+#pragma unroll
+    for (int q = 0; q < (k + 3) / 4; ++q) {
+      const float4 lv = l4[q];
+      const float l[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (4 * q + t < k) x = fmaf(-l[t], Q[4 * q + t], x);
+    }
+    Q[k] = x;
+    if (col) rec[k * kRecLd + 24 + lane] = x;
   }
 #pragma unroll 4
-  for (int k = 0; k < 24; ++k) {
-    const float* prow = piv_s + k * kCondPivLd;
-    const float pk = prow[k];
-    const float inv = (pk != 0.0f && isfinite(pk)) ? 1.0f / pk : 0.0f;
-    const float u_lo = prow[lane];
-    const float u_hi = has_hi ? prow[lane + 32] : 0.0f;
+  for (int r = 24; r < 36; ++r) {
+    float f = P_s[r * kCondLd + cl];
+    const float4* l4 = reinterpret_cast<const float4*>(L_s + r * kCondLd);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float l = __shfl_sync(0xffffffffu, lo[q], k) * inv;
-      if (lane > k) lo[q] = fmaf(-l, u_lo, lo[q]);
-      hi[q] = fmaf(-l, u_hi, hi[q]);
+    for (int q = 0; q < 6; ++q) {
+      const float4 lv = l4[q];
+      f = fmaf(-lv.x, Q[4 * q], f);
+      f = fmaf(-lv.y, Q[4 * q + 1], f);
+      f = fmaf(-lv.z, Q[4 * q + 2], f);
+      f = fmaf(-lv.w, Q[4 * q + 3], f);
     }
+    if (col) cond[(r - 24) * kBlkLd + lane] = f;
   }
-
-  // outputs: pivot rows (pivot order) for the recovery, condensed block row
-  // [S | T | rhs] = columns 24..48 of the stage-4 rows
-  const int64_t blk = node * a.Nmax + i;
-  float4* rec4 = reinterpret_cast<float4*>(static_cast<float*>(w.Rec) + blk * kRec);
-  const float4* piv4 = reinterpret_cast<const float4*>(piv_s);
-  constexpr int kRow4 = kCondPivLd / 4;   // 13
-  for (int e = lane; e < 24 * kRow4; e += 32) {
-    const int r = e / kRow4, q = e % kRow4;
-    if (q >= r / 4) rec4[e] = piv4[e];     // the part at and right of the diagonal
+  // interior part of the recovery rows: U_k (at and right of the diagonal)
+  // and 1/pivot
+  for (int e = lane; e < 24 * 6; e += 32) {
+    const int k = e / 6, q = e % 6;
+    if (q >= k / 4)
+      reinterpret_cast<float4*>(rec + k * kRecLd)[q] = reinterpret_cast<const float4*>(U_s + k * kCondLd)[q];
   }
-  float* cond = static_cast<float*>(w.Cond) + blk * kBlk;
-  if (!interior) {
-    float tmp[25];
-#pragma unroll
-    for (int c = 0; c < 25; ++c) tmp[c] = ra[24 + c];
-    store_row25<float>(cond + (lane - 24) * kBlkLd, tmp);
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (lane >= 24) cond[(8 + q) * kBlkLd + (lane - 24)] = lo[q];
-    if (has_hi) cond[(8 + q) * kBlkLd + (lane + 8)] = hi[q];
-  }
-  __syncwarp();   // the table is reused by the warp's next interval
+  if (lane < 24) rec[lane * kRecLd + kRecInv] = U_s[lane * kCondLd + 24];
+  __syncwarp();   // the tables are reused by the warp's next interval
 }
 
 constexpr int kCondRegWarps = 4;
 
-__global__ void __launch_bounds__(32 * kCondRegWarps) k_condense_reg(SolveArgs a, Workspace w) {
+__global__ void __launch_bounds__(32 * kCondRegWarps, 5) k_condense_reg(SolveArgs a, Workspace w) {
   __shared__ __align__(16) float sm[kCondRegWarps][kCondSmemFloats];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -591,6 +637,10 @@ __device__ __forceinline__ void condense_interval_smem(const SolveArgs& a, const
   const int64_t blk = node * a.Nmax + i;
   double* rec = static_cast<double*>(w.Rec) + blk * kRec;
   for (int e = lane; e < 24 * kCols; e += 32) rec[(e / kCols) * kRecLd + e % kCols] = M[e];
+  if (lane < 24) {
+    const double pv = M[lane * kCols + lane];
+    rec[lane * kRecLd + kRecInv] = (pv != 0.0 && isfinite(pv)) ? 1.0 / pv : 0.0;
+  }
   double* cond = static_cast<double*>(w.Cond) + blk * kBlk;
   for (int e = lane; e < 12 * 25; e += 32) {
     const int r = e / 25, c = e % 25;
@@ -847,7 +897,7 @@ __global__ void __launch_bounds__(128) k_abd_seg(SolveArgs a, Workspace w) {
       const T piv = prow[12 + k];
       const bool good = piv != T(0) && isfinite(piv);
       ok = ok && good;
-      const T inv = good ? T(1) / piv : T(0);
+      const T inv = good ? recip_rn(piv) : T(0);
       const T la = (cand && !done) ? r[12 + k] * inv : T(0);
 #pragma unroll
       for (int c = 0; c < 37; ++c)
@@ -959,32 +1009,59 @@ __global__ void __launch_bounds__(128) k_abd_segback(SolveArgs a, Workspace w) {
   }
 }
 
-// Interior-stage corrections from the stored condensation pivot rows.
+// Interior-stage corrections from the stored condensation pivot rows: lane
+// k < 24 holds pivot row k = [U_k (interior, pivot at k) | Q_k (y_i, y_{i+1},
+// rhs) | 1/pivot at column 49] in registers.  acc_k = rhs_k - Q_k [dy_i;
+// dy_{i+1}], then back substitution through U by shuffles.
 template <typename T>
 __device__ __forceinline__ void recover_interval(const SolveArgs& a, const Workspace& w, int64_t node, int i,
-                                                 int lane, T* U) {
+                                                 int lane) {
   const int64_t wid = node * a.Nmax + i;
   const T* rec = static_cast<const T*>(w.Rec) + wid * kRec;
-  for (int e = lane; e < kRec; e += 32) U[e] = rec[e];
   double* D = w.D + (node * npts(a.Nmax) + 3 * int64_t(i)) * 12;
   const T dyl = lane < 12 ? T(D[lane]) : T(0);
   const T dyr = lane < 12 ? T(D[36 + lane]) : T(0);
-  __syncwarp();
-  T acc = lane < 24 ? U[lane * kRecLd + 48] : T(0);
+  T row[kRecLd];
+  if (lane < 24) {
+    if constexpr (sizeof(T) == 4) {
+      const float4* s4 = reinterpret_cast<const float4*>(rec + lane * kRecLd);
+#pragma unroll
+      for (int q = 0; q < kRecLd / 4; ++q) {
+        const float4 v = s4[q];
+        row[4 * q] = v.x; row[4 * q + 1] = v.y; row[4 * q + 2] = v.z; row[4 * q + 3] = v.w;
+      }
+    } else {
+      const double2* s2 = reinterpret_cast<const double2*>(rec + lane * kRecLd);
+#pragma unroll
+      for (int q = 0; q < kRecLd / 2; ++q) {
+        const double2 v = s2[q];
+        row[2 * q] = v.x; row[2 * q + 1] = v.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < kRecLd; ++c) row[c] = T(0);
+  }
+  T acc = row[48];
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
     const T l = __shfl_sync(0xffffffffu, dyl, c);
     const T r = __shfl_sync(0xffffffffu, dyr, c);
-    if (lane < 24) acc -= U[lane * kRecLd + 24 + c] * l + U[lane * kRecLd + 36 + c] * r;
+    acc = fma(-row[24 + c], l, acc);
+    acc = fma(-row[36 + c], r, acc);
   }
-  const T x = warp_backsolve<T, 24>(U, kRecLd, acc, lane);
+  T x = T(0);
+#pragma unroll
+  for (int c = 23; c >= 0; --c) {
+    const T xc = __shfl_sync(0xffffffffu, acc * row[kRecInv], c);
+    if (lane == c) x = xc;
+    acc = lane < c ? fma(-row[c], xc, acc) : acc;
+  }
   if (lane < 24) D[12 + lane] = double(x);   // points 3i+1 and 3i+2 are contiguous
-  __syncwarp();
 }
 
 template <typename T>
 __global__ void k_recover(SolveArgs a, Workspace w) {
-  __shared__ __align__(16) T rows_s[4][kRec];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t wid = blockIdx.x * int64_t(4) + warp;
   if (wid >= a.n * a.Nmax) return;
@@ -992,7 +1069,7 @@ __global__ void k_recover(SolveArgs a, Workspace w) {
   const int i = static_cast<int>(wid % a.Nmax);
   if (!w.ns[node].active) return;
   if (i >= a.N[node]) return;
-  recover_interval<T>(a, w, node, i, lane, rows_s[warp]);
+  recover_interval<T>(a, w, node, i, lane);
 }
 
 // ---------------------------------------------------------------- update

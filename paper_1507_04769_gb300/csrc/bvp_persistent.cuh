@@ -15,8 +15,7 @@
 namespace sg {
 
 // Shared-memory scratch per warp: the FP64 condensation system (36 x 49
-// doubles), or for FP32 the condensation's pivot table (28 x 52 floats, which
-// also covers the 24 x 52 recovery rows).
+// doubles), or the FP32 condensation's tables.
 template <typename T>
 __host__ __device__ constexpr int persist_smem_per_warp() {
   return sizeof(T) == sizeof(double) ? 36 * kCols * 8 : kCondSmemFloats * 4;
@@ -130,7 +129,7 @@ __device__ void solve_node_persistent(const SolveArgs& a, const Workspace& w, in
       __syncwarp();
       ok = abd_node_reg<T>(a, w, node, N, lane) && ok;
       __syncwarp();
-      for (int i = 0; i < N; ++i) recover_interval<T>(a, w, node, i, lane, reinterpret_cast<T*>(scratch));
+      for (int i = 0; i < N; ++i) recover_interval<T>(a, w, node, i, lane);
       __syncwarp();
       // the condensation reports zero pivots through the node state
       const bool sing = !__all_sync(0xffffffffu, ok) || w.ns[node].singular;

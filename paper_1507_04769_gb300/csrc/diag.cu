@@ -144,3 +144,30 @@ extern "C" int sg_fma_probe(int precision, void* d_scratch, size_t scratch_bytes
   if (flops_per_launch) *flops_per_launch = 2.0 * 8 * 16 * double(iters) * blocks * threads;
   return SG_OK;
 }
+
+// ---------------------------------------------------------------- sincos probe
+#include "problems.cuh"
+
+namespace sg {
+__global__ void k_sincos_probe(int64_t n, const double* __restrict__ x, double* __restrict__ s,
+                               double* __restrict__ c) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  double sv, cv;
+  dsincos(x[t], &sv, &cv);
+  s[t] = sv;
+  c[t] = cv;
+}
+}  // namespace sg
+
+extern "C" int sg_sincos_probe(const double* d_x, int64_t n, double* d_s, double* d_c, void* stream) {
+  sg::clear_error();
+  if (n < 0) return sg::fail(SG_EINVAL, "sg_sincos_probe: n < 0");
+  if (n == 0) return SG_OK;
+  if (!d_x || !d_s || !d_c) return sg::fail(SG_EINVAL, "sg_sincos_probe: null device pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SG_TIMED("k_sincos_probe", st,
+           (sg::k_sincos_probe<<<static_cast<unsigned>(sg::ceil_div(n, 256)), 256, 0, st>>>(n, d_x, d_s, d_c)));
+  SG_LAUNCH_CHECK("k_sincos_probe");
+  return SG_OK;
+}

@@ -73,21 +73,6 @@ __device__ bool warp_eliminate(T* M, int lane) {
   return ok;
 }
 
-// Back substitution U x = t for an n x n upper-triangular U (row stride ldu)
-// in shared memory; lane r < n holds t_r on entry and x_r on exit.
-template <typename T, int NN>
-__device__ __forceinline__ T warp_backsolve(const T* U, int ldu, T t, int lane) {
-  T x = T(0);
-#pragma unroll
-  for (int c = NN - 1; c >= 0; --c) {
-    T xc_local = (lane == c) ? t / U[c * ldu + c] : T(0);
-    T xc = __shfl_sync(0xffffffffu, xc_local, c);
-    if (lane == c) x = xc;
-    if (lane < c) t -= U[lane * ldu + c] * xc;
-  }
-  return x;
-}
-
 // Deterministic warp sum / max (fixed butterfly order).
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

@@ -37,7 +37,39 @@ struct DevProblem {
 };
 
 // ------------------------------------------------------------------ duals
-__device__ __forceinline__ void dsincos(double a, double* s, double* c) { sincos(a, s, c); }
+// FP64 sine and cosine.  On |a| <= pi/4 (where the Euler angles of the
+// attitude problem stay) they are the Taylor polynomials of sin and cos about
+// 0, through a^17 and a^18, evaluated by Horner's rule in a^2; the first
+// omitted terms are below 1e-19 there, so the result is within a few units in
+// the last place.  Larger arguments take the CUDA library sincos.
+__device__ __forceinline__ void dsincos(double a, double* s, double* c) {
+  if (fabs(a) <= 0.78539816339744831) {
+    const double z = a * a;
+    // sin a = a (1 - z/3! + z^2/5! - ... + z^8/17!)
+    double ps = 1.0 / 355687428096000.0;                  // 1/17!
+    ps = fma(ps, z, -1.0 / 1307674368000.0);              // 1/15!
+    ps = fma(ps, z, 1.0 / 6227020800.0);                  // 1/13!
+    ps = fma(ps, z, -1.0 / 39916800.0);                   // 1/11!
+    ps = fma(ps, z, 1.0 / 362880.0);                      // 1/9!
+    ps = fma(ps, z, -1.0 / 5040.0);                       // 1/7!
+    ps = fma(ps, z, 1.0 / 120.0);                         // 1/5!
+    ps = fma(ps, z, -1.0 / 6.0);                          // 1/3!
+    *s = fma(a * z, ps, a);
+    // cos a = 1 - z/2! + z^2/4! - ... + z^9/18!
+    double pc = 1.0 / 6402373705728000.0;                 // 1/18!
+    pc = fma(pc, z, -1.0 / 20922789888000.0);             // 1/16!
+    pc = fma(pc, z, 1.0 / 87178291200.0);                 // 1/14!
+    pc = fma(pc, z, -1.0 / 479001600.0);                  // 1/12!
+    pc = fma(pc, z, 1.0 / 3628800.0);                     // 1/10!
+    pc = fma(pc, z, -1.0 / 40320.0);                      // 1/8!
+    pc = fma(pc, z, 1.0 / 720.0);                         // 1/6!
+    pc = fma(pc, z, -1.0 / 24.0);                         // 1/4!
+    pc = fma(pc, z, 0.5);                                 // 1/2!
+    *c = fma(-z, pc, 1.0);
+  } else {
+    sincos(a, s, c);
+  }
+}
 __device__ __forceinline__ void dsincos(float a, float* s, float* c) { sincosf(a, s, c); }
 __device__ __forceinline__ double recip(double a) { return 1.0 / a; }
 __device__ __forceinline__ float recip(float a) { return 1.0f / a; }

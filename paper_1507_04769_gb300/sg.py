@@ -70,8 +70,9 @@ def _load():
     lib.sg_surplus_free.argtypes = [P]
     lib.sg_surplus_free.restype = None
     lib.sg_eval_feedback.argtypes = [P, P, I64, I32, P, P]
+    lib.sg_sincos_probe.argtypes = [P, I64, P, P, P]
     for name in ("sg_build_grid", "sg_grid_info", "sg_solve_bvps", "sg_build_surpluses",
-                 "sg_surplus_info", "sg_eval_feedback"):
+                 "sg_surplus_info", "sg_eval_feedback", "sg_sincos_probe"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -265,6 +266,14 @@ def eval_feedback(surplus: Surplus, xq: torch.Tensor, mode: int = EVAL_FP64,
         out = torch.empty((Q, surplus.k), dtype=torch.float64, device=xq.device)
     _check(LIB.sg_eval_feedback(surplus.handle, _ptr(xq), Q, mode, _ptr(out), _stream(stream)))
     return out
+
+
+def sincos_probe(x: torch.Tensor, stream=None):
+    """sg_sincos_probe: the library's FP64 sine and cosine at x (device)."""
+    x = _dev(x, torch.float64).reshape(-1)
+    s, c = torch.empty_like(x), torch.empty_like(x)
+    _check(LIB.sg_sincos_probe(_ptr(x), x.numel(), _ptr(s), _ptr(c), _stream(stream)))
+    return s, c
 
 
 # --------------------------------------------------------------- closed loop

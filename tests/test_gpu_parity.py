@@ -362,3 +362,21 @@ def test_tf32x3_full_size_sampled():
     w = ointerp.surpluses(og, f)
     ref = ointerp.eval_surplus(og, w, xq[idx])
     assert np.max(np.abs(u[idx] - ref) / _tf32x3_bound(og, w, xq[idx])) <= 1.0
+
+
+@pytest.mark.gpu
+def test_library_sincos_within_few_ulp():
+    """The FP64 sine/cosine inside the right-hand side (Taylor polynomials on
+    |x| <= pi/4, the CUDA library beyond) against numpy's, within 4 ulp."""
+    rng = np.random.default_rng(7)
+    x = np.concatenate([rng.uniform(-np.pi / 4, np.pi / 4, 200_000),
+                        np.linspace(-np.pi / 4, np.pi / 4, 10_001),
+                        [0.0, -0.0, np.pi / 4, -np.pi / 4, np.nextafter(np.pi / 4, 1.0), 1e-300, -1e-12],
+                        rng.uniform(-20.0, 20.0, 50_000)])
+    s, c = sg.sincos_probe(torch.as_tensor(x, device="cuda"))
+    s, c = s.cpu().numpy(), c.cpu().numpy()
+    eps = np.finfo(np.float64).eps
+    for got, ref in ((s, np.sin(x)), (c, np.cos(x))):
+        err = np.abs(got - ref)
+        assert np.all(err <= 4 * eps * np.abs(ref) + 1e-300), float(np.max(err / np.maximum(np.abs(ref), 1e-300)))
+    assert s[np.where(x == 0.0)[0]].tolist() == [0.0, 0.0] and np.all(c[x == 0.0] == 1.0)
