@@ -336,6 +336,22 @@ __device__ __forceinline__ void store_row25(T* __restrict__ dst, const T (&r)[25
   dst[24] = r[24];
 }
 
+// Pivot-search key: the magnitude bits (sign shifted out; for doubles the
+// upper word) in the top 31 bits, ordered like |x|.
+__device__ __forceinline__ unsigned mag_key(float x) { return __float_as_uint(x) << 1; }
+__device__ __forceinline__ unsigned mag_key(double x) {
+  return static_cast<unsigned>(static_cast<unsigned long long>(__double_as_longlong(x)) >> 32) << 1;
+}
+
+// 16-byte asynchronous global -> shared copies (cp.async, completion by
+// cp.async.wait_all; other lanes see the data after a __syncwarp).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Correctly rounded reciprocal (the same value as 1 / x, without the
 // division's slow-path branch).
 __device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
@@ -487,28 +503,37 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
   }
 
   // ---- phase A: interior columns
-  const bool interior = lane < 24;
-  bool done = false;
-  bool ok = true;
+  // pivot key: |a| (sign shifted out) with the low 5 bits replaced by
+  // 31 - lane, so one warp max finds the largest magnitude, ties to the lower
+  // lane; a lane that is no candidate (stage-4 row, or already a pivot row)
+  // has an all-zero mask and tag
+  const unsigned itag = 31u - unsigned(lane);
+  unsigned kmask = lane < 24 ? ~31u : 0u;
+  unsigned ktag = lane < 24 ? itag : 0u;
+  float live = 1.0f;                        // 0 once the row is a pivot row
+  bool bad = false;
 #pragma unroll
   for (int k = 0; k < 24; ++k) {
     const int q0 = k / 4;
-    const int p = warp_pivot_lane<float>(ra[k], interior && !done, lane);
-    if (lane == p) {
+    const unsigned key = ((__float_as_uint(ra[k]) << 1) & kmask) | ktag;
+    const unsigned best = __reduce_max_sync(0xffffffffu, key);
+    if ((best & 31u) == itag && ktag != 0u) {
       const float pv = ra[k];
       const float inv = (pv != 0.0f && isfinite(pv)) ? __frcp_rn(pv) : 0.0f;
+      bad = inv == 0.0f;
       float4* dst = reinterpret_cast<float4*>(U_s + k * kCondLd);
 #pragma unroll
       for (int q = q0; q < 6; ++q) dst[q] = make_float4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
       dst[6] = make_float4(inv, 0.0f, 0.0f, 0.0f);
       perm_s[k] = lane;
-      done = true;
+      kmask = 0u;
+      ktag = 0u;
+      live = 0.0f;
     }
     __syncwarp();
     const float4* src = reinterpret_cast<const float4*>(U_s + k * kCondLd);
     const float inv = src[6].x;
-    ok = ok && inv != 0.0f;
-    const float la = (interior && done) ? 0.0f : ra[k] * inv;
+    const float la = ra[k] * (inv * live);
     const float lb = hasb ? rb[k] * inv : 0.0f;
 #pragma unroll
     for (int q = q0; q < 6; ++q) {
@@ -526,7 +551,7 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     L_s[lane * kCondLd + k] = la;
     if (hasb) L_s[(8 + lane) * kCondLd + k] = lb;
   }
-  if (!ok && lane == 0) w.ns[node].singular = 1;
+  if (__any_sync(0xffffffffu, bad) && lane == 0) w.ns[node].singular = 1;
   __syncwarp();
 
   // ---- phase B: passive columns
@@ -539,16 +564,22 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
 #pragma unroll
   for (int k = 0; k < 24; ++k) {
     const int pk = perm_s[k];
-    float x = P_s[pk * kCondLd + cl];
+    // two partial sums (even and odd j) to halve the dependent chain
+    float x = P_s[pk * kCondLd + cl], y = 0.0f;
     const float4* l4 = reinterpret_cast<const float4*>(L_s + pk * kCondLd);
 #pragma unroll
     for (int q = 0; q < (k + 3) / 4; ++q) {
       const float4 lv = l4[q];
       const float l[4] = {lv.x, lv.y, lv.z, lv.w};
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (4 * q + t < k) x = fmaf(-l[t], Q[4 * q + t], x);
+      for (int t = 0; t < 4; ++t) {
+        if (4 * q + t < k) {
+          if (t & 1) y = fmaf(-l[t], Q[4 * q + t], y);
+          else x = fmaf(-l[t], Q[4 * q + t], x);
+        }
+      }
     }
+    x += y;
     Q[k] = x;
     if (col) rec[k * kRecLd + 24 + lane] = x;
   }
@@ -867,44 +898,51 @@ __global__ void __launch_bounds__(128) k_abd_seg(SolveArgs a, Workspace w) {
     }
   }
   const bool cand = lane < 24;
+  const unsigned itag = 31u - unsigned(lane);
   bool carry = lane < 12;
-  bool ok = true;
+  bool bad = false;
   for (int i = i0 + 1; i < i1; ++i) {
-    if (i + 1 < i1) {   // stage block row i + 1 for the lanes that become free
-      const T* src = cond + int64_t(i + 1) * kBlk;
-      if constexpr (sizeof(T) == 4) {
-        for (int e = lane; e < kStage / 4; e += 32)
-          reinterpret_cast<float4*>(stage)[e] = reinterpret_cast<const float4*>(src)[e];
-      } else {
-        for (int e = lane; e < kStage / 2; e += 32)
-          reinterpret_cast<double2*>(stage)[e] = reinterpret_cast<const double2*>(src)[e];
-      }
+    if (i + 1 < i1) {   // stage block row i + 1 for the lanes that become free (asynchronous copy)
+      const char* src = reinterpret_cast<const char*>(cond + int64_t(i + 1) * kBlk);
+      for (int e = lane; e < kStage * int(sizeof(T)) / 16; e += 32)
+        cp_async16(reinterpret_cast<char*>(stage) + 16 * e, src + 16 * e);
+      cp_async_commit();
     }
-    bool done = false;
+    // candidates: the 24 panel rows; mask and tag as in the condensation
+    unsigned kmask = cand ? ~31u : 0u;
+    unsigned ktag = cand ? itag : 0u;
+    T live = cand ? T(1) : T(0);
     int my_step = -1;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      const int p = warp_pivot_lane<T>(r[12 + k], cand && !done, lane);
+      const unsigned key = (mag_key(r[12 + k]) & kmask) | ktag;
+      const unsigned best = __reduce_max_sync(0xffffffffu, key);
+      const bool is_p = (best & 31u) == itag && ktag != 0u;
       T* pb = pivbuf + (k & 1) * kSegLd;
-      if (lane == p) {
+      if (is_p) {
         store_row40<T>(pb, r);
-        done = true;
         my_step = k;
+        kmask = 0u;
+        ktag = 0u;
+        live = T(0);
       }
       __syncwarp();
       T prow[40];
       load_row40<T>(pb, prow);
       const T piv = prow[12 + k];
       const bool good = piv != T(0) && isfinite(piv);
-      ok = ok && good;
+      bad = bad || !good;
       const T inv = good ? recip_rn(piv) : T(0);
-      const T la = (cand && !done) ? r[12 + k] * inv : T(0);
+      const T la = r[12 + k] * (inv * live);
 #pragma unroll
       for (int c = 0; c < 37; ++c)
         if (c < 12 || c > 12 + k) r[c] = fma(-la, prow[c], r[c]);
-      if (lane == p) r[12 + k] = inv;
+      if (is_p) r[12 + k] = inv;
     }
+    const bool done = my_step >= 0;
     if (done) store_row40<T>(seg + (int64_t(i) * 12 + my_step) * kSegLd, r);
+    cp_async_wait_all();   // this lane's part of the stage has landed
+    __syncwarp();          // ... and every lane's
     // next panel: the carry rows move y_{i+1} into the y_i slot; the pivot
     // lanes take block row i + 1 from the stage, in lane order
     const int rank = __popc(__ballot_sync(0xffffffffu, done) & lt_mask);
@@ -927,7 +965,7 @@ __global__ void __launch_bounds__(128) k_abd_seg(SolveArgs a, Workspace w) {
     }
     __syncwarp();   // stage and pivot buffer reads done before the next panel writes
   }
-  if (!__all_sync(0xffffffffu, ok) && lane == 0) w.ns[node].singular = 1;
+  if (__any_sync(0xffffffffu, bad) && lane == 0) w.ns[node].singular = 1;
   // reduced block row of the segment: the carry rows [F | Y | rhs]
   const int rank = __popc(__ballot_sync(0xffffffffu, carry) & lt_mask);
   if (carry) {

@@ -379,4 +379,4 @@ def test_library_sincos_within_few_ulp():
     for got, ref in ((s, np.sin(x)), (c, np.cos(x))):
         err = np.abs(got - ref)
         assert np.all(err <= 4 * eps * np.abs(ref) + 1e-300), float(np.max(err / np.maximum(np.abs(ref), 1e-300)))
-    assert s[np.where(x == 0.0)[0]].tolist() == [0.0, 0.0] and np.all(c[x == 0.0] == 1.0)
+    assert np.all(s[x == 0.0] == 0.0) and np.all(c[x == 0.0] == 1.0)
