@@ -43,7 +43,7 @@ enum {
   SG_EUNSUPPORTED = 4   /* valid but not supported (e.g. dimension > 8)    */
 };
 
-enum { SG_PROBLEM_ATTITUDE = 0, SG_PROBLEM_LQ = 1 };
+enum { SG_PROBLEM_ATTITUDE = 0, SG_PROBLEM_LQ = 1, SG_PROBLEM_EXAMPLE3 = 2 };
 
 /* Precision of the Newton solve.
  * FP64:  everything in FP64.
@@ -54,8 +54,8 @@ enum { SG_PROBLEM_ATTITUDE = 0, SG_PROBLEM_LQ = 1 };
 enum { SG_PREC_FP64 = 0, SG_PREC_MIXED = 1 };
 
 /* Per-node Newton status written to d_status.  SG_BADINPUT: N outside
- * 1..n_max_intervals, T not positive and finite, or a non-finite x0 (that node
- * is skipped and its outputs are NaN). */
+ * 1..n_max_intervals, T negative or not finite, or a non-finite x0 (that node
+ * is skipped and its outputs are NaN).  T = 0 is a valid (empty) horizon. */
 enum { SG_CONVERGED = 0, SG_MAXITER = 1, SG_NONFINITE = 2, SG_SINGULAR = 3, SG_BADINPUT = 4 };
 
 /* Interpolant evaluation mode.
@@ -78,7 +78,13 @@ enum { SG_EVAL_FP64 = 0, SG_EVAL_TF32X3 = 1, SG_EVAL_DF32 = 2 };
  *   terminal cost 0.5 (tv |v(T)|^2 + tw |w(T)|^2).
  * SG_PROBLEM_LQ: x' = A x + Blq u, running cost 0.5 (x'Qx + u'Ru),
  *   terminal 0.5 x'QT x; R must be symmetric positive definite.
- * Unused fields of the other family are ignored. */
+ * SG_PROBLEM_EXAMPLE3 (Section 5, Example III): three states in x[0..2]
+ *   (x[3..5] must be 0 and stay 0), x1' = -x1 + x2, x2' = -x2 + x3 / g,
+ *   x3' = (-2 x1^2 + 2 x1 x2 - 2 x2^2 + 2 x2 x3 / g) x3 / g + g u with
+ *   g = 1 + x1^2 + x2^2, one control (u0[1..2] are written as 0), running cost
+ *   0.5 (x3^2 / g^2 + u^2), no terminal cost.  Time-invariant, so the value at
+ *   (t0, x0) is the solve from x0 over the horizon T_end - t0.  No parameters.
+ * Unused fields of the other families are ignored. */
 typedef struct sg_problem {
   int32_t kind;
   int32_t _pad;
@@ -155,7 +161,7 @@ void sg_grid_free(sg_grid* g);
  *   prob            host pointer to the problem
  *   d_x0            n x 6 initial states
  *   n               number of BVPs (>= 0; 0 is a no-op)
- *   d_T             n horizons (> 0)
+ *   d_T             n horizons (>= 0)
  *   d_N             n interval counts, 1 <= N[i] <= n_max_intervals
  *   n_max_intervals the maximum of d_N (host value; sizes the workspace slots)
  *   opts            host pointer (NULL = defaults)
@@ -287,6 +293,17 @@ int sg_fma_probe(int precision, void* d_scratch, size_t scratch_bytes, int block
  * error bound.  Asynchronous on `stream`; SG_EINVAL for n < 0 or null
  * pointers with n > 0. */
 int sg_sincos_probe(const double* d_x, int64_t n, double* d_s, double* d_c, void* stream);
+
+/* ---------------------------------------------------------------- error amplification
+ * sg_theorem1_bound - Theorem 1 (i), Section 4.2: the factor B with
+ * |e_bvp| < eps * B for nodal errors below eps on the CGL sparse grid with
+ * q = d + level, B = sum_{l=q-d+1}^{q} C(d-1, q-l) S_l, S_l the sum over
+ * |i| = l of Lambda_{i_1} ... Lambda_{i_d}, Lambda_i the Lebesgue-constant bound
+ * of Eq. lebesgue at N = 2^(i-1) (Lambda_1 = 1).  Host arithmetic, no GPU.
+ * *bound (host) receives B.  SG_EINVAL outside 1 <= d <= 64, d <= q <= d + 60.
+ * (The Monte-Carlo estimate of the same factor, Eq. ebvp_explicit2, is the
+ * interpolant of random nodal data: sg_build_surpluses + sg_eval_feedback.) */
+int sg_theorem1_bound(int d, int q, double* bound);
 
 /* ---------------------------------------------------------------- closed loop
  * sg_simulate_closed_loop - the on-line phase of Section 3.3 run against the

@@ -237,9 +237,106 @@ class LinearQuadratic:
         return np.block([[self.A, -self.K], [-self.Q, -self.A.T]])
 
 
+class Example3:
+    """Example III of Section 5: three states in components 0..2 of the
+    six-state layout (components 3..5 have zero dynamics and cost), one
+    control entering x3' through B(x) = g e3, g = 1 + x1^2 + x2^2;
+    l(x) = 0.5 x3^2 / g^2, L = l + 0.5 u^2, no terminal cost.
+    u* = -g lambda3 and H* = l + lambda' f0 - 0.5 g^2 lambda3^2, so
+        x'      = f0(x) - g^2 lambda3 e3
+        lambda' = -(grad l + grad_x(lambda' f0) - g lambda3^2 grad g)."""
+    n = 12
+    m = 1
+
+    def __init__(self, p=None):
+        self.p = p
+
+    @staticmethod
+    def _g(x):
+        return 1.0 + x[0] ** 2 + x[1] ** 2
+
+    def f0(self, x):
+        x1, x2, x3 = x[0], x[1], x[2]
+        g = self._g(x)
+        q = -2 * x1 ** 2 + 2 * x1 * x2 - 2 * x2 ** 2 + 2 * x2 * x3 / g
+        z = 0.0 * x1
+        return np.stack([-x1 + x2, -x2 + x3 / g, q * x3 / g, z, z, z])
+
+    def ustar(self, x, lam):
+        return (-self._g(x) * lam[2])[None, ...] if np.ndim(lam[2]) else np.array([-self._g(x) * lam[2]])
+
+    def grad_lf0(self, x, lam):
+        """grad_x (lambda' f0(x)), written out by hand (a test checks it
+        against a complex-step derivative)."""
+        x1, x2, x3 = x[0], x[1], x[2]
+        l1, l2, l3 = lam[0], lam[1], lam[2]
+        g = self._g(x)
+        q = -2 * x1 ** 2 + 2 * x1 * x2 - 2 * x2 ** 2 + 2 * x2 * x3 / g
+        dq1 = -4 * x1 + 2 * x2 - 4 * x1 * x2 * x3 / g ** 2
+        dq2 = 2 * x1 - 4 * x2 + 2 * x3 / g - 4 * x2 ** 2 * x3 / g ** 2
+        dq3 = 2 * x2 / g
+        df2 = (-2 * x1 * x3 / g ** 2, -1 - 2 * x2 * x3 / g ** 2, 1 / g)
+        df3 = (x3 * (dq1 / g - 2 * x1 * q / g ** 2), x3 * (dq2 / g - 2 * x2 * q / g ** 2), q / g + x3 * dq3 / g)
+        z = 0.0 * x1
+        return np.stack([-l1 + l2 * df2[0] + l3 * df3[0],
+                         l1 + l2 * df2[1] + l3 * df3[1],
+                         l2 * df2[2] + l3 * df3[2], z, z, z])
+
+    def grad_l(self, x):
+        x1, x2, x3 = x[0], x[1], x[2]
+        g = self._g(x)
+        z = 0.0 * x1
+        return np.stack([-2 * x1 * x3 ** 2 / g ** 3, -2 * x2 * x3 ** 2 / g ** 3, x3 / g ** 2, z, z, z])
+
+    def rhs(self, y):
+        x, lam = y[:6], y[6:]
+        g = self._g(x)
+        z = 0.0 * g
+        xdot = self.f0(x) - np.stack([z, z, g ** 2 * lam[2], z, z, z])
+        gradg = np.stack([2 * x[0], 2 * x[1], z, z, z, z])
+        ldot = -(self.grad_l(x) + self.grad_lf0(x, lam) - g * lam[2] ** 2 * gradg)
+        return np.concatenate([xdot, ldot])
+
+    def running_cost(self, y):
+        x, lam = y[:6], y[6:]
+        g = self._g(x)
+        return 0.5 * (x[2] ** 2 / g ** 2 + (g * lam[2]) ** 2)
+
+    def terminal(self, x):
+        return 0.0 * x[0]
+
+    def terminal_grad(self, x):
+        return 0.0 * x
+
+    def terminal_hess(self, x):
+        return np.zeros((6, 6))
+
+    def hamiltonian(self, y):
+        x, lam = y[:6], y[6:]
+        g = self._g(x)
+        u = -g * lam[2]
+        f = self.f0(x)
+        return self.running_cost(y) + (lam * f).sum(0) + lam[2] * g * u
+
+    @staticmethod
+    def value(tau, x):
+        """The closed form printed with Example III: V = 0.5 x3^2 / g^2 tanh(tau),
+        tau = T - t the remaining horizon."""
+        g = 1.0 + x[0] ** 2 + x[1] ** 2
+        return 0.5 * x[2] ** 2 / g ** 2 * np.tanh(tau)
+
+    @staticmethod
+    def feedback(tau, x):
+        """u* = -x3 / g tanh(tau) (printed with Example III)."""
+        g = 1.0 + x[0] ** 2 + x[1] ** 2
+        return -x[2] / g * np.tanh(tau)
+
+
 def make(params):
     if params.kind == synth.ATTITUDE:
         return Attitude(params)
+    if params.kind == synth.EXAMPLE3:
+        return Example3(params)
     return LinearQuadratic(params)
 
 

@@ -108,7 +108,7 @@ bool make_dev_problem(const sg_problem& in, DevProblem* out) {
         for (int m = 0; m < 3; ++m) s += in.Blq[3 * i + m] * p.G[6 * m + j];
         p.K[6 * i + j] = s;
       }
-  } else {
+  } else if (in.kind != SG_PROBLEM_EXAMPLE3) {
     return false;
   }
   *out = p;

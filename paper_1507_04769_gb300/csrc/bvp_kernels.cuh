@@ -122,7 +122,7 @@ __global__ void k_init(SolveArgs a, Workspace w) {
     NodeState s{};
     const int N = a.N[node];
     const double T = a.T[node];
-    bool ok = N >= 1 && N <= a.Nmax && T > 0.0 && T < INFINITY;
+    bool ok = N >= 1 && N <= a.Nmax && T >= 0.0 && T < INFINITY;
     for (int c = 0; c < 6; ++c) ok = ok && isfinite(x0[c]);
     s.alpha = 0.0;   // the first residual evaluation is at Y itself
     s.active = ok ? 1 : 0;
@@ -1191,7 +1191,7 @@ __global__ void k_outputs(SolveArgs a, Workspace w, double* lambda0, double* u0,
     const double* yN = Y + 3 * int64_t(N) * 12;
     V[node] = z + terminal_cost(a.P, yN);
     double u[3];
-    optimal_control(a.P, Y + 6, u);
+    optimal_control(a.P, Y, Y + 6, u);
     for (int c = 0; c < 6; ++c) lambda0[node * 6 + c] = Y[6 + c];
     for (int c = 0; c < 3; ++c) u0[node * 3 + c] = u[c];
     status[node] = s.status;

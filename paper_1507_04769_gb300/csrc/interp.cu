@@ -68,7 +68,7 @@ __global__ void k_fine_table(int level, const double* xf, double* tab1) {
 // One level of Eq. interpo: for the nodes n in [n0, n1) (all with |i| = s),
 // w_n = f_n - sum over coarser nodes m < n0 of phi_m(x_n) w_m.
 __global__ void k_surplus_level(int64_t n0, int64_t n1, int d, int k, int fine_n,
-                                const uint8_t* __restrict__ fid, const int16_t* __restrict__ fpt,
+                                const uint16_t* __restrict__ fid, const int16_t* __restrict__ fpt,
                                 const double* __restrict__ tab1, const double* __restrict__ f,
                                 double* __restrict__ W) {
   const int64_t n = n0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -234,7 +234,7 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   if (!g || !d_values || !out) return fail(SG_EINVAL, "sg_build_surpluses: null pointer");
   *out = nullptr;
   if (k < 1 || k > kMaxOut) return fail(SG_EINVAL, "sg_build_surpluses: k must be 1..16");
-  if (g->level > kMaxLevel) return fail(SG_EUNSUPPORTED, "sg_build_surpluses: level above 7");
+  if (g->level > kMaxLevel) return fail(SG_EUNSUPPORTED, "sg_build_surpluses: level above 8");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int d = g->d, L = g->level, fine_n = 1 << L;
   const int64_t M = g->M;
@@ -245,7 +245,7 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   s->M = M;
   s->nf = n_functions(L);
   // host: integer structure (function ids, fine positions, level ranges, order)
-  std::vector<uint8_t> fid(M * d);
+  std::vector<uint16_t> fid(M * d);
   std::vector<int16_t> fpt(M * d);
   std::vector<int64_t> level_start;
   int prev_sum = -1;
@@ -254,7 +254,7 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
     for (int dim = 0; dim < d; ++dim) {
       const int l = g->h_lev[n * d + dim], kk = g->h_kidx[n * d + dim];
       sum += l;
-      fid[n * d + dim] = static_cast<uint8_t>(function_id(l, kk));
+      fid[n * d + dim] = static_cast<uint16_t>(function_id(l, kk));
       fpt[n * d + dim] = static_cast<int16_t>(l == 1 ? fine_n / 2 : kk * (fine_n >> (l - 1)));
     }
     if (sum != prev_sum) {
@@ -295,7 +295,7 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   // grp[a] = first node with at least a active dimensions (non-decreasing)
   for (int a = kMaxDim; a >= 0; --a) s->grp[a] = s->grp[a] < s->grp[a + 1] ? s->grp[a] : s->grp[a + 1];
 
-  uint8_t* d_fid = nullptr;
+  uint16_t* d_fid = nullptr;
   int16_t* d_fpt = nullptr;
   double* d_tab1 = nullptr;
   int32_t* d_order = nullptr;
@@ -318,7 +318,7 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   SG_TRY_CLEAN(cudaMalloc(&s->xf, (fine_n + 1) * sizeof(double)));
   SG_TRY_CLEAN(cudaMalloc(&s->xfdf, (fine_n + 1) * sizeof(float2)));
   SG_TRY_CLEAN(cudaMalloc(&s->Wdf, M * k * sizeof(float2)));
-  SG_TRY_CLEAN(cudaMalloc(&d_fid, M * d));
+  SG_TRY_CLEAN(cudaMalloc(&d_fid, M * d * sizeof(uint16_t)));
   SG_TRY_CLEAN(cudaMalloc(&d_fpt, M * d * sizeof(int16_t)));
   SG_TRY_CLEAN(cudaMalloc(&d_tab1, size_t(s->nf) * (fine_n + 1) * sizeof(double)));
   SG_TRY_CLEAN(cudaMalloc(&d_order, M * sizeof(int32_t)));
@@ -328,7 +328,7 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
     box[d + dim] = g->h_hi[dim] - g->h_lo[dim];
   }
   SG_TRY_CLEAN(cudaMemcpyAsync(s->box, box.data(), 2 * d * sizeof(double), cudaMemcpyHostToDevice, st));
-  SG_TRY_CLEAN(cudaMemcpyAsync(d_fid, fid.data(), M * d, cudaMemcpyHostToDevice, st));
+  SG_TRY_CLEAN(cudaMemcpyAsync(d_fid, fid.data(), M * d * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
   SG_TRY_CLEAN(cudaMemcpyAsync(d_fpt, fpt.data(), M * d * sizeof(int16_t), cudaMemcpyHostToDevice, st));
   SG_TRY_CLEAN(cudaMemcpyAsync(s->nact, nact.data(), M, cudaMemcpyHostToDevice, st));
   SG_TRY_CLEAN(cudaMemcpyAsync(s->ops, ops.data(), M * kMaxDim * sizeof(uint16_t), cudaMemcpyHostToDevice, st));

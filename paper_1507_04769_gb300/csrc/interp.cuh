@@ -4,7 +4,7 @@
 #include "common.cuh"
 
 namespace sg {
-constexpr int kMaxLevel = 7;                 // finest 1-D set has 2^7 + 1 points
+constexpr int kMaxLevel = 8;                 // finest 1-D set has 2^8 + 1 points
 constexpr int kMaxFine = 1 << kMaxLevel;
 constexpr int kMaxOut = 16;
 constexpr int kEvalThreads = 128;

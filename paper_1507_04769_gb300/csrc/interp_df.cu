@@ -19,9 +19,8 @@
 
 namespace sg {
 
-constexpr int kFoldBlock = 64;     // nodes per FP64 fold of the compensated sums (per warp)
-constexpr int kDfQ = 32;           // queries per block (one per lane)
-constexpr int kDfWarps = 4;        // warps per block; warp w takes the nodes m = w (mod kDfWarps)
+constexpr int kFoldBlock = 64;     // nodes per FP64 fold of the compensated sums (per thread)
+constexpr int kDfWarps = 4;        // warps per block
 constexpr int kDfThreads = 32 * kDfWarps;
 constexpr int kDfChunk = 128;      // nodes staged in shared memory at a time
 
@@ -45,15 +44,16 @@ struct DfAcc {
 };
 
 // Nodes [n0, n1) of the staged chunk with exactly A active factors; this
-// warp takes those with index = warp (mod kDfWarps).  off_s: byte offsets of
-// the node's table rows (kMaxDim slots), w_s: K surplus pairs per node.
-template <int K, int A>
+// thread's node stream takes those with index = stream (mod NS).  off_s:
+// byte offsets of the node's table rows (kMaxDim slots), w_s: K surplus
+// pairs per node.
+template <int K, int A, int NS>
 __device__ __forceinline__ void df_group(const unsigned char* __restrict__ tab_q, const uint32_t* __restrict__ off_s,
-                                         const float2* __restrict__ w_s, int n0, int n1, int warp, DfAcc (&acc)[K],
-                                         int& since_fold) {
-  int nn = n0 + ((warp - n0) % kDfWarps + kDfWarps) % kDfWarps;
+                                         const float2* __restrict__ w_s, int n0, int n1, int stream,
+                                         DfAcc (&acc)[K], int& since_fold) {
+  int nn = n0 + ((stream - n0) % NS + NS) % NS;
 #pragma unroll 2
-  for (; nn < n1; nn += kDfWarps) {
+  for (; nn < n1; nn += NS) {
     df phi = {1.0f, 0.0f};
     if constexpr (A > 0) {
       uint32_t o[A];
@@ -103,31 +103,35 @@ __device__ __forceinline__ void df_group(const unsigned char* __restrict__ tab_q
   }
 }
 
-// Block = kDfQ queries x kDfWarps node streams.  The d x nf basis table of
-// each query (pairs) is built once in shared memory and shared by the
-// block's warps; lane q of every warp evaluates query q over its share of the
-// nodes, and the warps' partial sums are added in FP64 in a fixed order.
-// Nodes come in the evaluation order, grouped by their number of active
-// dimensions A, so every group runs a loop with a fixed-length product.
-template <int K>
+// Block = QB queries x NS = kDfWarps * 32 / QB node streams: lane q % QB of
+// the block evaluates query q over the nodes of its stream.  The d x nf basis
+// table of each query (pairs) is built once in shared memory and shared by
+// the block's streams; the streams' partial sums are added in FP64 in a
+// fixed order.  Nodes come in the evaluation order, grouped by their number
+// of active dimensions A, so every group runs a loop with a fixed-length
+// product.  QB = 32 for the usual levels; 16 or 8 when the d x nf tables of
+// 32 queries do not fit in shared memory (high levels).
+template <int K, int QB>
 __global__ void __launch_bounds__(kDfThreads) k_eval_df32(EvalArgs e, int d) {
+  constexpr int NS = kDfThreads / QB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nf = e.nf;
-  const int tab_bytes = d * nf * kDfQ * static_cast<int>(sizeof(float2));
-  float2* tab = reinterpret_cast<float2*>(smem_raw);                                  // [d*nf][kDfQ]
+  const int tab_bytes = d * nf * QB * static_cast<int>(sizeof(float2));
+  float2* tab = reinterpret_cast<float2*>(smem_raw);                                  // [d*nf][QB]
   uint32_t* off_s = reinterpret_cast<uint32_t*>(smem_raw + tab_bytes);                 // [kDfChunk][kMaxDim]
   float2* w_s = reinterpret_cast<float2*>(off_s + kDfChunk * kMaxDim);                 // [kDfChunk][K]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t qbase = blockIdx.x * int64_t(kDfQ);
+  const int tid = threadIdx.x;
+  const int ql = tid % QB, stream = tid / QB;
+  const int64_t qbase = blockIdx.x * int64_t(QB);
 
   // basis tables: (query, dim) tasks over the block
-  for (int task = tid; task < kDfQ * d; task += kDfThreads) {
-    const int ql = task % kDfQ, dim = task / kDfQ;
-    const int64_t q = qbase + ql;
+  for (int task = tid; task < QB * d; task += kDfThreads) {
+    const int tq = task % QB, dim = task / QB;
+    const int64_t q = qbase + tq;
     const double u = q < e.Q ? (e.xq[q * d + dim] - e.lo[dim]) / e.width[dim] : 0.5;
-    basis_row_df(u, e.level, e.xfdf, tab + (dim * nf) * kDfQ + ql, kDfQ);
+    basis_row_df(u, e.level, e.xfdf, tab + (dim * nf) * QB + tq, QB);
   }
-  const unsigned char* tab_q = reinterpret_cast<const unsigned char*>(tab + lane);
+  const unsigned char* tab_q = reinterpret_cast<const unsigned char*>(tab + ql);
 
   DfAcc acc[K];
 #pragma unroll
@@ -139,7 +143,7 @@ __global__ void __launch_bounds__(kDfThreads) k_eval_df32(EvalArgs e, int d) {
     for (int x = tid; x < cn * kMaxDim; x += kDfThreads) {
       const int nn = x / kMaxDim, j = x % kMaxDim;
       // table row (dim * nf + id) -> byte offset within the query column
-      off_s[x] = static_cast<uint32_t>(e.ops[(m0 + nn) * kMaxDim + j]) * (kDfQ * sizeof(float2));
+      off_s[x] = static_cast<uint32_t>(e.ops[(m0 + nn) * kMaxDim + j]) * (QB * sizeof(float2));
     }
     for (int x = tid; x < cn * K; x += kDfThreads) w_s[x] = e.Wdf[m0 * K + x];
     __syncthreads();
@@ -150,52 +154,62 @@ __global__ void __launch_bounds__(kDfThreads) k_eval_df32(EvalArgs e, int d) {
       if (g0 >= g1) continue;
       const int n0 = static_cast<int>(g0 - m0), n1 = static_cast<int>(g1 - m0);
       switch (a) {
-        case 0: df_group<K, 0>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
-        case 1: df_group<K, 1>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
-        case 2: df_group<K, 2>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
-        case 3: df_group<K, 3>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
-        case 4: df_group<K, 4>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
-        case 5: df_group<K, 5>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
-        case 6: df_group<K, 6>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
-        case 7: df_group<K, 7>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
-        default: df_group<K, 8>(tab_q, off_s, w_s, n0, n1, warp, acc, since_fold); break;
+        case 0: df_group<K, 0, NS>(tab_q, off_s, w_s, n0, n1, stream, acc, since_fold); break;
+        case 1: df_group<K, 1, NS>(tab_q, off_s, w_s, n0, n1, stream, acc, since_fold); break;
+        case 2: df_group<K, 2, NS>(tab_q, off_s, w_s, n0, n1, stream, acc, since_fold); break;
+        case 3: df_group<K, 3, NS>(tab_q, off_s, w_s, n0, n1, stream, acc, since_fold); break;
+        case 4: df_group<K, 4, NS>(tab_q, off_s, w_s, n0, n1, stream, acc, since_fold); break;
+        case 5: df_group<K, 5, NS>(tab_q, off_s, w_s, n0, n1, stream, acc, since_fold); break;
+        case 6: df_group<K, 6, NS>(tab_q, off_s, w_s, n0, n1, stream, acc, since_fold); break;
+        case 7: df_group<K, 7, NS>(tab_q, off_s, w_s, n0, n1, stream, acc, since_fold); break;
+        default: df_group<K, 8, NS>(tab_q, off_s, w_s, n0, n1, stream, acc, since_fold); break;
       }
     }
   }
-  // warps' partial sums, added in warp order
+  // streams' partial sums, added in stream order
   __syncthreads();
-  double* red = reinterpret_cast<double*>(smem_raw);   // [kDfWarps][kDfQ][K], over the tables
+  double* red = reinterpret_cast<double*>(smem_raw);   // [NS][QB][K], over the tables
 #pragma unroll
   for (int c = 0; c < K; ++c)
-    red[(warp * kDfQ + lane) * K + c] =
-        acc[c].total + (static_cast<double>(acc[c].ah) + static_cast<double>(acc[c].al));
+    red[(stream * QB + ql) * K + c] = acc[c].total + (static_cast<double>(acc[c].ah) + static_cast<double>(acc[c].al));
   __syncthreads();
-  if (warp == 0) {
-    const int64_t q = qbase + lane;
+  if (tid < QB) {
+    const int64_t q = qbase + tid;
     if (q < e.Q) {
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        double v = red[lane * K + c];
-        for (int w = 1; w < kDfWarps; ++w) v += red[(w * kDfQ + lane) * K + c];
+        double v = red[tid * K + c];
+        for (int st = 1; st < NS; ++st) v += red[(st * QB + tid) * K + c];
         e.out[q * K + c] = v;
       }
     }
   }
 }
 
-template <int K>
-static int launch_df32_k(const EvalArgs& e, int d, cudaStream_t st) {
-  const size_t tab = sizeof(float2) * d * e.nf * kDfQ;
-  const size_t red = sizeof(double) * kDfWarps * kDfQ * K;
-  const size_t smem = (tab > red ? tab : red) + sizeof(uint32_t) * kDfChunk * kMaxDim + sizeof(float2) * kDfChunk * K;
-  if (smem > 220 * 1024) return fail(SG_EUNSUPPORTED, "sg_eval_feedback: grid level too high for the DF32 kernel");
-  if (sizeof(float2) * d * e.nf * kDfQ > 0xffffffffu)
-    return fail(SG_EUNSUPPORTED, "sg_eval_feedback: table too large for the DF32 kernel");
-  const unsigned blocks = static_cast<unsigned>(ceil_div(e.Q, kDfQ));
-  SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_df32<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-  SG_TIMED("k_eval_df32", st, (k_eval_df32<K><<<blocks, kDfThreads, smem, st>>>(e, d)));
+template <int K, int QB>
+static size_t df32_smem(const EvalArgs& e, int d) {
+  const size_t tab = sizeof(float2) * d * e.nf * QB;
+  const size_t red = sizeof(double) * kDfThreads * K;
+  return (tab > red ? tab : red) + sizeof(uint32_t) * kDfChunk * kMaxDim + sizeof(float2) * kDfChunk * K;
+}
+
+template <int K, int QB>
+static int launch_df32_kq(const EvalArgs& e, int d, size_t smem, cudaStream_t st) {
+  const unsigned blocks = static_cast<unsigned>(ceil_div(e.Q, QB));
+  SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_df32<K, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(smem)));
+  SG_TIMED("k_eval_df32", st, (k_eval_df32<K, QB><<<blocks, kDfThreads, smem, st>>>(e, d)));
   SG_LAUNCH_CHECK("k_eval_df32");
   return SG_OK;
+}
+
+template <int K>
+static int launch_df32_k(const EvalArgs& e, int d, cudaStream_t st) {
+  constexpr size_t kLimit = 220 * 1024;
+  if (df32_smem<K, 32>(e, d) <= kLimit) return launch_df32_kq<K, 32>(e, d, df32_smem<K, 32>(e, d), st);
+  if (df32_smem<K, 16>(e, d) <= kLimit) return launch_df32_kq<K, 16>(e, d, df32_smem<K, 16>(e, d), st);
+  if (df32_smem<K, 8>(e, d) <= kLimit) return launch_df32_kq<K, 8>(e, d, df32_smem<K, 8>(e, d), st);
+  return fail(SG_EUNSUPPORTED, "sg_eval_feedback: grid level too high for the DF32 kernel");
 }
 
 int eval_df32(const EvalArgs& e, int d, cudaStream_t st) {

@@ -147,6 +147,23 @@ __device__ __forceinline__ Dual<T, N> recip(const Dual<T, N>& a) {
   return r;
 }
 template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator-(const Dual<T, N>& a, T s) {
+  Dual<T, N> r = a;
+  r.v = a.v - s;
+  return r;
+}
+
+// Scalar type of a plain or dual number (for constants in templated code).
+template <typename S>
+struct ScalarOf {
+  using type = S;
+};
+template <typename T, int N>
+struct ScalarOf<Dual<T, N>> {
+  using type = T;
+};
+
+template <typename T, int N>
 __device__ __forceinline__ void dsincos(const Dual<T, N>& a, Dual<T, N>* s, Dual<T, N>* c) {
   T sv, cv;
   dsincos(a.v, &sv, &cv);
@@ -241,9 +258,69 @@ __device__ __forceinline__ void attitude_f0_grad(const DevProblem& P, const S* x
 }
 
 
+// ------------------------------------------------------------------ Example III
+// Section 5, Example III: x1' = -x1 + x2, x2' = -x2 + x3 / g,
+// x3' = (-2 x1^2 + 2 x1 x2 - 2 x2^2 + 2 x2 x3 / g) x3 / g + g u with
+// g = 1 + x1^2 + x2^2, running cost 0.5 (x3^2 / g^2 + u^2), no terminal cost.
+// The three states sit in components 0..2 of the six-state layout; the
+// others have zero dynamics and cost (they stay 0 from x0 = 0).  With
+// B(x) = g e3: u* = -g lambda3 and H* = l + lambda' f0 - 0.5 g^2 lambda3^2, so
+//   x'      = f0 - g^2 lambda3 e3
+//   lambda' = -(grad l + f0_x' lambda - g lambda3^2 grad g).
+// Templated on the number type so that one source gives the FP64 right-hand
+// side and, with duals over (x1, x2, x3, lambda1..3), the Jacobian.
+template <typename S>
+__device__ __forceinline__ void ex3_char(const S* x, const S* lam, S* dx, S* dl) {
+  using R = typename ScalarOf<S>::type;
+  const S& x1 = x[0];
+  const S& x2 = x[1];
+  const S& x3 = x[2];
+  const S& l1 = lam[0];
+  const S& l2 = lam[1];
+  const S& l3 = lam[2];
+  const S g = x1 * x1 + x2 * x2 + R(1);
+  const S gi = recip(g);
+  const S gi2 = gi * gi;
+  const S x3gi = x3 * gi;
+  const S q = R(2) * (x1 * x2 - x1 * x1 - x2 * x2 + x2 * x3gi);
+  dx[0] = x2 - x1;
+  dx[1] = x3gi - x2;
+  dx[2] = q * x3gi - g * g * l3;
+  // partial derivatives of f0_2, q, f0_3
+  const S x3gi2 = x3 * gi2;
+  const S f2_1 = R(-2) * x1 * x3gi2;
+  const S f2_2 = R(-2) * x2 * x3gi2 - R(1);
+  const S q_1 = R(2) * (x2 - R(2) * x1) - R(4) * x1 * x2 * x3gi2;
+  const S q_2 = R(2) * (x1 - R(2) * x2) + R(2) * x3gi - R(4) * x2 * x2 * x3gi2;
+  const S q_3 = R(2) * x2 * gi;
+  const S f3_1 = x3gi * (q_1 - R(2) * x1 * q * gi);
+  const S f3_2 = x3gi * (q_2 - R(2) * x2 * q * gi);
+  const S f3_3 = q * gi + x3gi * q_3;
+  // grad l, l = 0.5 x3^2 / g^2
+  const S lx3 = x3 * gi2;
+  const S lx1 = R(-2) * x1 * x3gi * lx3;
+  const S lx2 = R(-2) * x2 * x3gi * lx3;
+  const S gl32 = g * l3 * l3;
+  dl[0] = -(lx1 - l1 + l2 * f2_1 + l3 * f3_1 - R(2) * x1 * gl32);
+  dl[1] = -(lx2 + l1 + l2 * f2_2 + l3 * f3_2 - R(2) * x2 * gl32);
+  dl[2] = -(lx3 + l2 * gi + l3 * f3_3);
+}
+
 // ------------------------------------------------------------------ RHS and Jacobian
 // F(y) for y = (x, lambda) in FP64.
 __device__ __forceinline__ void char_rhs(const DevProblem& P, const double* y, double* F) {
+  if (P.kind == SG_PROBLEM_EXAMPLE3) {
+    double dx[3], dl[3];
+    ex3_char<double>(y, y + 6, dx, dl);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      F[i] = dx[i];
+      F[3 + i] = 0.0;
+      F[6 + i] = dl[i];
+      F[9 + i] = 0.0;
+    }
+    return;
+  }
   if (P.kind == SG_PROBLEM_ATTITUDE) {
     double f0[6], g[6];
     attitude_f0_grad<double, double>(P, y, y + 6, f0, g);
@@ -279,6 +356,37 @@ __device__ __forceinline__ void char_rhs(const DevProblem& P, const double* y, d
 template <typename T>
 __device__ __forceinline__ void char_jacobian(const DevProblem& P, const double* y, T* Jm,
                                               double* Fout) {
+  if (P.kind == SG_PROBLEM_EXAMPLE3) {
+    using D = Dual<T, 6>;
+    D x[3], lam[3], dx[3], dl[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      x[i] = dconst<T, 6>(T(y[i]));
+      x[i].d[i] = T(1);
+      lam[i] = dconst<T, 6>(T(y[6 + i]));
+      lam[i].d[3 + i] = T(1);
+    }
+    ex3_char<D>(x, lam, dx, dl);
+    // rows 0..2 (x') and 6..8 (lambda'); columns 0..2 (x) and 6..8 (lambda)
+#pragma unroll
+    for (int r = 0; r < 12; ++r) {
+      T row[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) row[c] = T(0);
+      if (r < 3 || (r >= 6 && r < 9)) {
+        const D& f = r < 3 ? dx[r] : dl[r - 6];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          row[c] = f.d[c];
+          row[6 + c] = f.d[3 + c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 12; ++c) Jm[12 * r + c] = row[c];
+    }
+    if (Fout) char_rhs(P, y, Fout);
+    return;
+  }
   if (P.kind == SG_PROBLEM_ATTITUDE) {
     using D = Dual<T, 6>;
     D x[6], f0[6], g[6];
@@ -347,6 +455,11 @@ __device__ __forceinline__ void char_jacobian(const DevProblem& P, const double*
 
 // Running cost L(x, u*(x, lambda)) (Section 2) at y = (x, lambda).
 __device__ __forceinline__ double running_cost(const DevProblem& P, const double* y) {
+  if (P.kind == SG_PROBLEM_EXAMPLE3) {
+    const double g = 1.0 + y[0] * y[0] + y[1] * y[1];
+    const double u = -g * y[8];
+    return 0.5 * (y[2] * y[2] / (g * g) + u * u);
+  }
   if (P.kind == SG_PROBLEM_ATTITUDE) {
     double u[3], su = 0.0, sv = 0.0, sw = 0.0;
 #pragma unroll
@@ -385,6 +498,7 @@ __device__ __forceinline__ double running_cost(const DevProblem& P, const double
 
 // Terminal cost h(x(T)), its gradient and Hessian.
 __device__ __forceinline__ double terminal_cost(const DevProblem& P, const double* x) {
+  if (P.kind == SG_PROBLEM_EXAMPLE3) return 0.0;
   if (P.kind == SG_PROBLEM_ATTITUDE)
     return 0.5 * (P.tv * (x[0] * x[0] + x[1] * x[1] + x[2] * x[2]) +
                   P.tw * (x[3] * x[3] + x[4] * x[4] + x[5] * x[5]));
@@ -400,6 +514,7 @@ __device__ __forceinline__ double terminal_cost(const DevProblem& P, const doubl
 }
 
 __device__ __forceinline__ double terminal_grad(const DevProblem& P, const double* x, int i) {
+  if (P.kind == SG_PROBLEM_EXAMPLE3) return 0.0;
   if (P.kind == SG_PROBLEM_ATTITUDE) return (i < 3 ? P.tv : P.tw) * x[i];
   double s = 0.0;
 #pragma unroll
@@ -408,13 +523,19 @@ __device__ __forceinline__ double terminal_grad(const DevProblem& P, const doubl
 }
 
 __device__ __forceinline__ double terminal_hess(const DevProblem& P, int i, int j) {
+  if (P.kind == SG_PROBLEM_EXAMPLE3) return 0.0;
   if (P.kind == SG_PROBLEM_ATTITUDE) return i == j ? (i < 3 ? P.tv : P.tw) : 0.0;
   return P.QT[6 * i + j];
 }
 
-// u*(x, lambda) = -G lambda.
-__device__ __forceinline__ void optimal_control(const DevProblem& P, const double* lam, double* u) {
-  if (P.kind == SG_PROBLEM_ATTITUDE) {
+// u*(x, lambda) = -R^-1 B(x)' lambda.
+__device__ __forceinline__ void optimal_control(const DevProblem& P, const double* x, const double* lam,
+                                                double* u) {
+  if (P.kind == SG_PROBLEM_EXAMPLE3) {
+    u[0] = -(1.0 + x[0] * x[0] + x[1] * x[1]) * lam[2];
+    u[1] = 0.0;
+    u[2] = 0.0;
+  } else if (P.kind == SG_PROBLEM_ATTITUDE) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
       u[i] = -(P.Gw[3 * i] * lam[3] + P.Gw[3 * i + 1] * lam[4] + P.Gw[3 * i + 2] * lam[5]);
@@ -433,7 +554,15 @@ __device__ __forceinline__ void optimal_control(const DevProblem& P, const doubl
 // Closed-loop plant x' = f(x, u) = f0(x) + Bu u for a given control u
 // (attitude: v' = E(v) w, w' = J^-1 (R(v) h x w) + J^-1 B u; LQ: A x + B u).
 __device__ __forceinline__ void plant_rhs(const DevProblem& P, const double* x, const double* u, double* f) {
-  if (P.kind == SG_PROBLEM_ATTITUDE) {
+  if (P.kind == SG_PROBLEM_EXAMPLE3) {
+    const double lam0[3] = {0.0, 0.0, 0.0};
+    double dx[3], dl[3];
+    ex3_char<double>(x, lam0, dx, dl);
+    f[0] = dx[0];
+    f[1] = dx[1];
+    f[2] = dx[2] + (1.0 + x[0] * x[0] + x[1] * x[1]) * u[0];
+    f[3] = f[4] = f[5] = 0.0;
+  } else if (P.kind == SG_PROBLEM_ATTITUDE) {
     double f0[6], g[6];
     const double lam0[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     attitude_f0_grad<double, double>(P, x, lam0, f0, g);
@@ -453,6 +582,10 @@ __device__ __forceinline__ void plant_rhs(const DevProblem& P, const double* x, 
 
 // Running cost L(x, u) (Section 2) for a given control.
 __device__ __forceinline__ double running_cost_xu(const DevProblem& P, const double* x, const double* u) {
+  if (P.kind == SG_PROBLEM_EXAMPLE3) {
+    const double g = 1.0 + x[0] * x[0] + x[1] * x[1];
+    return 0.5 * (x[2] * x[2] / (g * g) + u[0] * u[0]);
+  }
   if (P.kind == SG_PROBLEM_ATTITUDE) {
     double sv = 0.0, sw = 0.0, su = 0.0;
 #pragma unroll

@@ -16,7 +16,7 @@ from . import build as _build
 
 # --------------------------------------------------------------- constants
 SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_EUNSUPPORTED = 0, 1, 2, 3, 4
-PROBLEM_ATTITUDE, PROBLEM_LQ = 0, 1
+PROBLEM_ATTITUDE, PROBLEM_LQ, PROBLEM_EXAMPLE3 = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 CONVERGED, MAXITER, NONFINITE, SINGULAR, BADINPUT = 0, 1, 2, 3, 4
 EVAL_FP64, EVAL_TF32X3, EVAL_DF32 = 0, 1, 2
@@ -71,6 +71,8 @@ def _load():
     lib.sg_surplus_free.restype = None
     lib.sg_eval_feedback.argtypes = [P, P, I64, I32, P, P]
     lib.sg_sincos_probe.argtypes = [P, I64, P, P, P]
+    lib.sg_theorem1_bound.argtypes = [I32, I32, C.POINTER(D)]
+    lib.sg_theorem1_bound.restype = C.c_int
     for name in ("sg_build_grid", "sg_grid_info", "sg_solve_bvps", "sg_build_surpluses",
                  "sg_surplus_info", "sg_eval_feedback", "sg_sincos_probe"):
         getattr(lib, name).restype = C.c_int
@@ -109,9 +111,12 @@ class _DevView:
 
 # --------------------------------------------------------------- problems
 def problem_from(params) -> Problem:
-    """Builds the ABI struct from synthetic parameters (AttitudeParams / LQParams)."""
+    """Builds the ABI struct from synthetic parameters (AttitudeParams /
+    LQParams / Example3Params)."""
     p = Problem()
-    if params.kind == PROBLEM_ATTITUDE:
+    if params.kind == PROBLEM_EXAMPLE3:
+        p.kind = PROBLEM_EXAMPLE3
+    elif params.kind == PROBLEM_ATTITUDE:
         p.kind = PROBLEM_ATTITUDE
         p.J[:] = [float(v) for v in np.asarray(params.J).ravel()]
         p.hmom[:] = [float(v) for v in np.asarray(params.hmom).ravel()]
@@ -266,6 +271,31 @@ def eval_feedback(surplus: Surplus, xq: torch.Tensor, mode: int = EVAL_FP64,
         out = torch.empty((Q, surplus.k), dtype=torch.float64, device=xq.device)
     _check(LIB.sg_eval_feedback(surplus.handle, _ptr(xq), Q, mode, _ptr(out), _stream(stream)))
     return out
+
+
+def theorem1_bound(d: int, q: int) -> float:
+    """sg_theorem1_bound: the Theorem 1 factor bounding |e_bvp| / eps."""
+    out = C.c_double()
+    _check(LIB.sg_theorem1_bound(d, q, C.byref(out)))
+    return out.value
+
+
+def mc_error_amplification(d: int, level: int, n_points: int, seed: int = 0, symmetric: bool = False,
+                           mode: int = EVAL_DF32, device="cuda") -> float:
+    """Monte-Carlo estimate of |e_bvp| / eps (Section 4.2, Eq. ebvp_explicit2):
+    the interpolant of independent nodal errors drawn uniformly from [0, 1]
+    (as printed; [-1, 1] with symmetric=True), maximised over n_points uniform
+    points of [0, 1]^d.  Grid, surpluses and evaluation run in the library."""
+    lo, hi = np.zeros(d), np.ones(d)
+    g = Grid(d, level, lo, hi)
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    eps = torch.rand((g.M, 1), generator=gen, dtype=torch.float64)
+    if symmetric:
+        eps = 2.0 * eps - 1.0
+    xq = torch.rand((n_points, d), generator=gen, dtype=torch.float64)
+    S = Surplus(g, eps.to(device))
+    e = eval_feedback(S, xq.to(device), mode=mode)
+    return float(e.abs().max().item())
 
 
 def sincos_probe(x: torch.Tensor, stream=None):

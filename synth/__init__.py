@@ -18,6 +18,7 @@ import numpy as np
 
 ATTITUDE = 0
 LQ = 1
+EXAMPLE3 = 2
 
 BOX_HALF = np.pi / 4.0
 
@@ -50,6 +51,31 @@ class LQParams:
     R: np.ndarray   # (3,3)
     QT: np.ndarray  # (6,6)
     kind: int = field(default=LQ, init=False)
+
+
+@dataclass
+class Example3Params:
+    """Example III of Section 5 (three states, one control, no parameters).
+    The value function is interpolated on a (t, x) grid over
+    t in [0, t_end], x in [-2, 2]^3; the horizon of a node at time t is
+    t_end - t."""
+    t_end: float = 5.0
+    kind: int = field(default=EXAMPLE3, init=False)
+
+
+def example3_params() -> Example3Params:
+    return Example3Params()
+
+
+def example3_box():
+    """The (t, x1, x2, x3) region D of Example III: [0, 5] x [-2, 2]^3."""
+    return np.array([0.0, -2.0, -2.0, -2.0]), np.array([5.0, 2.0, 2.0, 2.0])
+
+
+def example3_mesh(horizon, h: float = 5.0 / 32.0):
+    """Intervals per node for horizons t_end - t: the mesh width closest to h
+    from above (at least one interval; a zero horizon keeps one)."""
+    return np.maximum(1, np.ceil(np.asarray(horizon) / h - 1e-9)).astype(np.int32)
 
 
 def attitude_params(seed: int = 0) -> AttitudeParams:
