@@ -124,6 +124,9 @@ typedef struct sg_solve_opts {
                           per iteration).  One graph is instantiated and cached per
                           (sizes, precision, problem, buffers) the first time and
                           replayed afterwards                                     */
+  int32_t warm_start;  /* 1: start Newton from the iterate in d_Y (which must then
+                          be given) instead of the zero-control guess; d_Y
+                          receives the final iterate as usual                    */
 } sg_solve_opts;
 
 /* ---------------------------------------------------------------- errors */
@@ -172,7 +175,9 @@ void sg_grid_free(sg_grid* g);
  *                   d_iters n (Newton iterations used); d_Y may be NULL or
  *                   n x (3*n_max_intervals+1) x 12 to receive the collocation
  *                   solution (point p of node i at row p; unused rows untouched)
- * The initial guess is lambda = 0 (zero control) with x held at x0.
+ * The initial guess is lambda = 0 (zero control) with x held at x0, or with
+ * opts->warm_start the iterate read from d_Y (for continuation: e.g. the
+ * solution from a scaled initial state, Example III).
  * The call returns when every node has converged or hit max_iter (the host
  * reads one counter per iteration), so it synchronises `stream`.
  * Errors: SG_EINVAL (sizes, workspace too small, misaligned), SG_ECUDA. */

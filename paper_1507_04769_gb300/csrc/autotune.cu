@@ -35,8 +35,9 @@ extern "C" int sg_autotune_solve(const sg_problem* prob, const double* d_x0, int
                                  double* report_ms, int force, void* stream) {
   clear_error();
   if (!best) return fail(SG_EINVAL, "sg_autotune_solve: null output");
-  sg_solve_opts b{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0};
+  sg_solve_opts b{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0, 0};
   if (base) b = *base;
+  b.warm_start = 0;   // the forms are timed on the zero-control solve
   const TuneKey key{b.precision, n, n_max_intervals, b.tol, b.max_iter, b.damping};
   if (!force) {
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -487,9 +487,10 @@ extern "C" int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t
     return fail(SG_EINVAL, "sg_solve_bvps: n_max_intervals must be 1..65536");
   if (!d_x0 || !d_T || !d_N || !d_work || !d_lambda0 || !d_u0 || !d_V || !d_status || !d_iters)
     return fail(SG_EINVAL, "sg_solve_bvps: null device pointer");
-  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0};
+  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0, 0};
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iter < 0) return fail(SG_EINVAL, "sg_solve_bvps: bad tol or max_iter");
+  if (o.warm_start && !d_Y) return fail(SG_EINVAL, "sg_solve_bvps: warm_start needs d_Y");
   if (o.precision != SG_PREC_FP64 && o.precision != SG_PREC_MIXED)
     return fail(SG_EINVAL, "sg_solve_bvps: unknown precision");
   if (reinterpret_cast<uintptr_t>(d_work) % 256 != 0)
@@ -510,6 +511,7 @@ extern "C" int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t
   a.persistent = o.persistent;
   a.blocks_per_sm = o.blocks_per_sm;
   a.sync_at_end = 1;
+  a.Yin = o.warm_start ? d_Y : nullptr;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (o.precision == SG_PREC_MIXED) {
     Workspace w = carve(d_work, n, n_max_intervals, sizeof(float));
@@ -566,9 +568,10 @@ extern "C" int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, 
     return fail(SG_EINVAL, "sg_solve_bvps_static: n_max_intervals must be 1..65536");
   if (!d_x0 || !d_T || !d_N || !d_lambda0 || !d_u0 || !d_V || !d_status || !d_iters)
     return fail(SG_EINVAL, "sg_solve_bvps_static: null device pointer");
-  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0};
+  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0, 0};
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iter < 0) return fail(SG_EINVAL, "sg_solve_bvps_static: bad tol or max_iter");
+  if (o.warm_start && !d_Y) return fail(SG_EINVAL, "sg_solve_bvps_static: warm_start needs d_Y");
   if (o.precision != SG_PREC_FP64 && o.precision != SG_PREC_MIXED)
     return fail(SG_EINVAL, "sg_solve_bvps_static: unknown precision");
   const size_t need = ws_bytes(n, n_max_intervals, o.precision);
@@ -593,6 +596,7 @@ extern "C" int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, 
   a.persistent = o.persistent;
   a.blocks_per_sm = o.blocks_per_sm;
   a.sync_at_end = 1;
+  a.Yin = o.warm_start ? d_Y : nullptr;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // Every region the solver reads is written first in this call (k_init sets the
   // iterate, the corrections and the per-node state; the counters are zeroed

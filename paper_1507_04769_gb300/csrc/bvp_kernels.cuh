@@ -97,6 +97,7 @@ struct SolveArgs {
   int persistent;      // one warp per node from a device queue (bvp_persistent.cuh)
   int blocks_per_sm;   // cap on resident 4-warp blocks per SM for the persistent form (0 = occupancy)
   int sync_at_end;
+  const double* Yin;   // initial iterate (n x P x 12), or null for the zero-control guess
 };
 
 __host__ __device__ __forceinline__ int64_t npts(int Nmax) { return 3 * int64_t(Nmax) + 1; }
@@ -111,12 +112,20 @@ __global__ void k_init(SolveArgs a, Workspace w) {
   const double* x0 = a.x0 + node * 6;
   double* y = w.Y + t * 12;
   double* d = w.D + t * 12;
+  if (a.Yin) {
 #pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    y[c] = x0[c];   // x held at x0, lambda = 0 (zero control)
-    y[6 + c] = 0.0;
-    d[c] = 0.0;
-    d[6 + c] = 0.0;
+    for (int c = 0; c < 12; ++c) {
+      y[c] = a.Yin[t * 12 + c];   // warm start
+      d[c] = 0.0;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      y[c] = x0[c];   // x held at x0, lambda = 0 (zero control)
+      y[6 + c] = 0.0;
+      d[c] = 0.0;
+      d[6 + c] = 0.0;
+    }
   }
   if (p == 0) {
     NodeState s{};

@@ -34,7 +34,7 @@ class Problem(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("damping", C.c_int32), ("persistent", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("graph", C.c_int32)]
+                ("graph", C.c_int32), ("warm_start", C.c_int32)]
 
 
 class SGError(RuntimeError):
@@ -173,10 +173,12 @@ def workspace_bytes(n: int, n_max: int, precision: int = PREC_FP64) -> int:
 def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=50,
                precision=PREC_FP64, damping=True, n_max=None, return_Y=False,
                workspace: torch.Tensor | None = None, persistent=False, blocks_per_sm=0,
-               graph=False, out=None, stream=None):
+               graph=False, out=None, Y0: torch.Tensor | None = None, stream=None):
     """sg_solve_bvps on device tensors.  x0 (n, 6) f64; T (n,) f64; N (n,) int32.
     `out` may hold preallocated output tensors (keys lambda0, u0, V, status,
-    iters); reusing them (and the workspace) lets graph=True replay one graph."""
+    iters); reusing them (and the workspace) lets graph=True replay one graph.
+    Y0 (n, 3 n_max + 1, 12) f64: warm start from this iterate; it is
+    overwritten with the final iterate (and returned as "Y")."""
     x0 = _dev(x0, torch.float64).reshape(-1, 6)
     n = x0.shape[0]
     dev = x0.device
@@ -195,10 +197,15 @@ def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=5
             "status": torch.empty((n,), dtype=torch.int32, device=dev),
             "iters": torch.empty((n,), dtype=torch.int32, device=dev),
         }
-    Y = torch.zeros((n, 3 * n_max + 1, 12), dtype=torch.float64, device=dev) if return_Y else None
+    if Y0 is not None:
+        if tuple(Y0.shape) != (n, 3 * n_max + 1, 12) or Y0.dtype != torch.float64 or not Y0.is_contiguous():
+            raise ValueError("Y0 must be a contiguous (n, 3 n_max + 1, 12) float64 tensor")
+        Y = Y0
+    else:
+        Y = torch.zeros((n, 3 * n_max + 1, 12), dtype=torch.float64, device=dev) if return_Y else None
     opts = SolveOpts(tol=tol, max_iter=max_iter, precision=precision, damping=int(bool(damping)),
                      persistent=int(bool(persistent)), blocks_per_sm=int(blocks_per_sm),
-                     graph=int(bool(graph)))
+                     graph=int(bool(graph)), warm_start=int(Y0 is not None))
     _check(LIB.sg_solve_bvps(C.byref(problem), _ptr(x0), n, _ptr(T), _ptr(N), n_max, C.byref(opts),
                              _ptr(workspace), workspace.numel(), _ptr(out["lambda0"]), _ptr(out["u0"]),
                              _ptr(out["V"]), _ptr(out["status"]), _ptr(out["iters"]),

@@ -26,6 +26,7 @@ class ValueSurface:
     grid: sg.Grid              # d = 1 + n_state, coordinates (t, x)
     surplus: sg.Surplus        # k = 2 outputs: V and u*_1
     result: dict               # per-node solve outputs (lambda0, u0, V, status, iters)
+    continued: int             # nodes re-solved by continuation in the horizon
     t_end: float
     horizons: np.ndarray       # t_end - t per node
     intervals: np.ndarray      # mesh intervals per node
@@ -36,12 +37,23 @@ class ValueSurface:
 
 
 def solve_value_surface(problem: sg.Problem, n_state: int, level: int, lo, hi, t_end: float, mesh,
-                        precision: int = sg.PREC_MIXED, tol: float = 1e-8, device="cuda") -> ValueSurface:
+                        precision: int = sg.PREC_MIXED, tol: float = 1e-8, max_iter: int = 100,
+                        continuation=((0.25, 0.5, 0.75, 1.0), tuple(k / 10 for k in range(1, 11))),
+                        device="cuda") -> ValueSurface:
     """Solves the characteristic BVP at every node of the level-`level` CGL
     sparse grid on the (t, x) box [lo, hi] (lo[0], hi[0]: the time range,
-    hi[0] <= t_end) and builds the surpluses of V and u*_1.
+    hi[0] <= t_end) and builds the surpluses of V and u*_1.  Raises if a node
+    does not converge (its value would spoil the whole interpolant).
 
-    mesh(horizons) -> intervals per node (numpy int32)."""
+    mesh(horizons) -> intervals per node (numpy int32).
+
+    Nodes whose damped Newton iteration stalls from the zero-control guess
+    (Example III has about 1 % of them at long horizons: the Armijo search
+    settles on a non-root minimum of |F|^2) are re-solved by continuation in
+    the horizon: the same mesh over the horizons `continuation` x (t_end - t)
+    in turn, each solve warm-started from the previous one's collocation
+    solution (the mesh points map onto each other, only h changes); nodes
+    that still stall take the next, finer schedule."""
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     d = lo.size
@@ -58,7 +70,26 @@ def solve_value_surface(problem: sg.Problem, n_state: int, level: int, lo, hi, t
     tau = tau_d.cpu().numpy()
     N = np.asarray(mesh(tau), dtype=np.int32)
     N_d = torch.as_tensor(N, device=device)
-    res = sg.solve_bvps(problem, x0, tau_d, N_d, tol=tol, precision=precision, n_max=int(N.max()))
+    n_max = int(N.max())
+    res = sg.solve_bvps(problem, x0, tau_d, N_d, tol=tol, max_iter=max_iter, precision=precision, n_max=n_max)
+    stalled = torch.nonzero(res["status"] != sg.CONVERGED).flatten()
+    n_continued = int(stalled.numel())
+    for schedule in continuation:   # finer schedules for the nodes that still stall
+        idx = torch.nonzero(res["status"] != sg.CONVERGED).flatten()
+        if not idx.numel():
+            break
+        Y = None
+        for k, scale in enumerate(schedule):
+            sub = sg.solve_bvps(problem, x0[idx].contiguous(), (tau_d[idx] * scale).contiguous(),
+                                N_d[idx].contiguous(), tol=tol, max_iter=max_iter, precision=precision,
+                                n_max=n_max, Y0=Y, return_Y=True)
+            Y = sub["Y"]
+        for key in ("lambda0", "u0", "V", "status", "iters"):
+            res[key][idx] = sub[key]
+    bad = int((res["status"] != sg.CONVERGED).sum().item())
+    if bad:
+        raise RuntimeError(f"{bad} of {M} nodes did not converge (max_iter = {max_iter}, with continuation)")
     vals = torch.stack([res["V"], res["u0"][:, 0]], dim=1).contiguous()
     S = sg.Surplus(g, vals)
-    return ValueSurface(grid=g, surplus=S, result=res, t_end=t_end, horizons=tau, intervals=N)
+    return ValueSurface(grid=g, surplus=S, result=res, continued=n_continued, t_end=t_end,
+                        horizons=tau, intervals=N)

@@ -57,9 +57,11 @@ class LQParams:
 class Example3Params:
     """Example III of Section 5 (three states, one control, no parameters).
     The value function is interpolated on a (t, x) grid over
-    t in [0, t_end], x in [-2, 2]^3; the horizon of a node at time t is
-    t_end - t."""
-    t_end: float = 5.0
+    t in [0, 5], x in [-2, 2]^3; the horizon of a node at time t is
+    t_end - t.  The final time is not printed; t_end = 10 is the reading
+    (with any t_end >= 7 the interpolation error of the exact V on the q = 12
+    grid matches the printed mean 8.5e-4 and variance 2.8e-6)."""
+    t_end: float = 10.0
     kind: int = field(default=EXAMPLE3, init=False)
 
 
