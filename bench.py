@@ -41,6 +41,14 @@ LEVEL, D = 4, 6
 N_QUERIES = 1_000_000
 TOL = 1e-8
 SEG_LEN = 16   # intervals per segment of the library's segmented staircase
+
+# dram__bytes_read.sum + dram__bytes_write.sum per unit from the ncu capture
+# summarised in profiles/solver_kernels_attitude6d_600nodes.md (first Newton
+# iteration of 600 level-4 nodes, 88,064 intervals: 298.8 + 483.1 MB).  Set an
+# entry to None when its kernel changes until it is captured again.
+DRAM_BYTES_PER_UNIT = {
+    "k_condense_reg_fp32": ((298.843392e6 + 483.104768e6) / 88064, "interval"),
+}
 WORKLOAD = ("attitude6d_L4_1457nodes_T{10,20,40}_N{64,128,256}_mixedprec"
             "+surplus+1e6queries")
 
@@ -291,7 +299,7 @@ def gpu_arm(args):
     tune_ms = None
     if args.only_steps:
         args.form = "phase"
-        args.skip_cpu = args.skip_fp64 = args.skip_serving = True
+        args.skip_cpu = args.skip_fp64 = args.skip_serving = args.skip_extensions = True
     if args.form == "auto":
         form, tune_ms = sg.autotune_solve(prob, x0_d, T_d, N_d, tol=TOL, precision=prec, n_max=n_max,
                                           workspace=ws)
@@ -485,6 +493,39 @@ def gpu_arm(args):
             eval_modes[name] = {"ms_per_1e6": ms * 1e6 / N_QUERIES, "evals_per_s": N_QUERIES / (ms / 1e3),
                                 "max_rel_err_vs_fp64": err}
 
+    # ---------------- Example III: value function on the q = 12 grid in (t, x)
+    # (18,945 nodes), against the printed closed form; and the Monte-Carlo
+    # error amplification of Section 4.2 at q = 13, d = 6 (44,689 nodes)
+    extensions = None
+    if rank == 0 and not args.skip_extensions:
+        from paper_1507_04769_gb300 import timegrid
+        lo3, hi3 = synth.example3_box()
+        prm3 = synth.example3_params()
+        torch.cuda.synchronize()
+        a3, b3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a3.record(stream)
+        vs = timegrid.solve_value_surface(sg.problem_from(prm3), 3, 8, lo3, hi3, prm3.t_end, synth.example3_mesh,
+                                          precision=prec, tol=TOL)
+        b3.record(stream)
+        torch.cuda.synchronize()
+        tx = synth.uniform_queries(1200, lo3, hi3, seed=5)
+        out3 = vs.evaluate(torch.as_tensor(tx, device=dev)).cpu().numpy()
+        tau3, x3 = prm3.t_end - tx[:, 0], tx[:, 1:].T
+        g3 = 1.0 + x3[0] ** 2 + x3[1] ** 2
+        e3 = out3[:, 0] - 0.5 * x3[2] ** 2 / g3 ** 2 * np.tanh(tau3)
+        extensions = {
+            "example3_q12": {"nodes": vs.grid.M, "t_end": prm3.t_end, "solve_and_surplus_ms": a3.elapsed_time(b3),
+                             "newton_iters_hist": np.bincount(vs.result["iters"].cpu().numpy()).tolist(),
+                             "continued_nodes": vs.continued, "points": 1200,
+                             "mae_V": float(np.abs(e3).mean()), "var_V": float(np.var(e3)),
+                             "paper": {"mae_V": 8.5e-4, "var_V": 2.8e-6}},
+            "error_amplification_q13_d6": {
+                "theorem1_bound": sg.theorem1_bound(6, 13),
+                "monte_carlo_uniform_0_1": sg.mc_error_amplification(6, 7, 2000, seed=0),
+                "monte_carlo_uniform_m1_1": sg.mc_error_amplification(6, 7, 2000, seed=0, symmetric=True),
+                "points": 2000, "paper": {"theorem1_bound": 3.66e4, "monte_carlo": 66.60}},
+        }
+
     # ---------------- serving: Poisson-arriving mixed requests, continuous batching
     serving_rep = None
     if not args.skip_serving and rank == 0:
@@ -564,6 +605,7 @@ def gpu_arm(args):
         "eval_modes": eval_modes,
         "pipe_peaks_probe": probe,
         "serving": serving_rep,
+        "extensions": extensions,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
@@ -655,8 +697,15 @@ def roofline(kt, iters, N_h, M, prec):
     roof = None
     if dom:
         e = kernels[dom]
+        traffic = None
+        if dom in DRAM_BYTES_PER_UNIT and e["launches"] > 0:
+            # DRAM bytes per unit from one ncu capture of the same kernel on a
+            # smaller case, times the units of an average timed launch
+            per_unit, unit_kind = DRAM_BYTES_PER_UNIT[dom]
+            units = {"interval": int_units}[unit_kind] * (steps_timed or 1)
+            traffic = per_unit * units / e["launches"]
         roof = {"kernel": dom, "bound": e["bound"], "achieved": e["achieved"], "peak": e["peak"],
-                "unit": e["unit"], "frac": e["frac"], "traffic": None,
+                "unit": e["unit"], "frac": e["frac"], "traffic": traffic,
                 "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if e["unit"] == "TFLOP/s"
                                 and e["peak"] == PEAK_FP32_TFLOPS else
                                 "nominal GB300 FP64 1.25 TFLOP/s" if e["unit"] == "TFLOP/s" else
@@ -679,6 +728,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--skip-extensions", action="store_true",
+                    help="skip the Example III value surface and the error-amplification estimates")
     ap.add_argument("--only-steps", action="store_true",
                     help="warm-up and timed steps only, one launch per phase (for kernel launch lists)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
