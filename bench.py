@@ -513,7 +513,22 @@ def gpu_arm(args):
         tau3, x3 = prm3.t_end - tx[:, 0], tx[:, 1:].T
         g3 = 1.0 + x3[0] ** 2 + x3[1] ** 2
         e3 = out3[:, 0] - 0.5 * x3[2] ** 2 / g3 ** 2 * np.tanh(tau3)
+        # Section 4.1: e_interp + e_bvp of the level-4 feedback at one horizon
+        # (T = 20, N = 128), against error-controlled solves at 1,280 random states
+        from paper_1507_04769_gb300 import validation as val
+        gv = sg.Grid(D, LEVEL, lo, hi)
+        rv = sg.solve_bvps(prob, gv.coords, torch.full((gv.M,), 20.0, dtype=torch.float64, device=dev),
+                           torch.full((gv.M,), 128, dtype=torch.int32, device=dev), tol=1e-10, precision=prec)
+        pts = torch.as_tensor(synth.uniform_queries(1280, lo, hi, seed=31), device=dev)
+        a4, b4 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a4.record(stream)
+        vres = val.validate_feedback(prob, sg.Surplus(gv, rv["u0"]), pts, 20.0, tol=1e-9)
+        b4.record(stream)
+        torch.cuda.synchronize()
         extensions = {
+            "validation_attitude_L4_T20": dict(vres.stats(0), reference_tol=1e-9, component="u1",
+                                               ms=a4.elapsed_time(b4),
+                                               all_components_mae=[vres.stats(c)["mae"] for c in range(3)]),
             "example3_q12": {"nodes": vs.grid.M, "t_end": prm3.t_end, "solve_and_surplus_ms": a3.elapsed_time(b3),
                              "newton_iters_hist": np.bincount(vs.result["iters"].cpu().numpy()).tolist(),
                              "continued_nodes": vs.continued, "points": 1200,
