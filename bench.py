@@ -5,7 +5,8 @@ One step = one pass of the whole path on the level-4 6-D attitude workload:
   Step I    sparse grid, d = 6, level 4 (1457 CGL nodes) on [-pi/4, pi/4]^6
   Step II   one characteristic BVP per node, T in {10, 20, 40} with N = 64 / 128
             / 256 Lobatto intervals, Newton to |F|_inf <= 1e-8 (mixed precision:
-            FP32 Jacobian / elimination / direction, FP64 residual and update)
+            FP32 Jacobian / elimination / direction, pair-of-floats residual,
+            FP64 update)
   Step III  surpluses of u*(x) at the nodes
   on-line   u*(x) at 1e6 query states (half uniform, half N(0, 0.2^2) clipped)
 The headline value is converged BVP solves per second of whole-step time.

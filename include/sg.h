@@ -48,9 +48,11 @@ enum { SG_PROBLEM_ATTITUDE = 0, SG_PROBLEM_LQ = 1, SG_PROBLEM_EXAMPLE3 = 2 };
 /* Precision of the Newton solve.
  * FP64:  everything in FP64.
  * MIXED: Jacobian, stage condensation, block elimination and the search
- *        direction in FP32; collocation residual, line search, update,
- *        terminal costate condition and outputs in FP64.  Newton then converges
- *        to the same FP64 root (the FP32 direction only slows the final rate). */
+ *        direction in FP32; the right-hand side and the stage rows of the
+ *        collocation residual in pair-of-floats arithmetic (about 48 bits, on
+ *        the FP32 pipe); the iterate, boundary rows, line search, update and
+ *        outputs in FP64.  Newton then converges to the same discrete root to
+ *        about 1e-13 (the FP32 direction only slows the final rate). */
 enum { SG_PREC_FP64 = 0, SG_PREC_MIXED = 1 };
 
 /* Per-node Newton status written to d_status.  SG_BADINPUT: N outside

@@ -57,6 +57,11 @@ static bool invert3(const double* R, double* Ri) {
   return true;
 }
 
+static float2 split_pair(double x) {
+  const float hi = static_cast<float>(x);
+  return make_float2(hi, static_cast<float>(x - static_cast<double>(hi)));
+}
+
 bool make_dev_problem(const sg_problem& in, DevProblem* out) {
   DevProblem p{};
   p.kind = in.kind;
@@ -110,6 +115,18 @@ bool make_dev_problem(const sg_problem& in, DevProblem* out) {
       }
   } else if (in.kind != SG_PROBLEM_EXAMPLE3) {
     return false;
+  }
+  for (int i = 0; i < 3; ++i) {
+    p.Jinv_f[i] = split_pair(p.Jinv[i]);
+    p.hm_f[i] = split_pair(p.hm[i]);
+  }
+  for (int i = 0; i < 9; ++i) p.Kw_f[i] = split_pair(p.Kw[i]);
+  p.wv_f = split_pair(p.wv);
+  p.ww_f = split_pair(p.ww);
+  for (int i = 0; i < 36; ++i) {
+    p.A_f[i] = split_pair(p.A[i]);
+    p.K_f[i] = split_pair(p.K[i]);
+    p.Q_f[i] = split_pair(p.Q[i]);
   }
   *out = p;
   return true;

@@ -12,12 +12,13 @@
 //               for the mesh-point corrections, segmented so that the serial
 //               chain per node is short (parallel over nodes and segments)
 //   k_recover   interior-stage corrections from the stored pivot rows
-//   k_trial     FP64 residual at Y + alpha D, per interval; it also stores the
+//   k_trial     residual at Y + alpha D, per interval; it also stores the
 //               stage residual rows (the right-hand side of the next
 //               condensation); k_ls_reduce takes the Armijo decision per node
 //               in a fixed reduction order
 // T = double gives the FP64 form, T = float the mixed form (FP32 Jacobian,
-// elimination and direction; FP64 residual, line search and update).
+// elimination and direction; pair-of-floats residual, FP64 line search and
+// update).
 #pragma once
 
 #include <cmath>
@@ -142,7 +143,7 @@ __global__ void k_init(SolveArgs a, Workspace w) {
 }
 
 // ---------------------------------------------------------------- residual
-// FP64 residual at Y + alpha D.  A block takes kTrialIv consecutive intervals
+// Residual at Y + alpha D.  A block takes kTrialIv consecutive intervals
 // of one node: first every thread evaluates F at one collocation point of the
 // chunk (3 kTrialIv + 1 <= 128 points, so the shared end points are evaluated
 // once), then the stage rows 2..4 of each interval are formed from the
@@ -156,7 +157,11 @@ __host__ __device__ __forceinline__ int trial_chunks(int Nmax) { return (Nmax + 
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
-  __shared__ double ys[kTrialPts][12];
+  // FP64 form: points and rows in FP64.  Mixed form: the right-hand side and
+  // the stage rows in pair-of-floats arithmetic (about 48 bits, on the FP32
+  // pipe); the boundary rows and the iterate Y + alpha D stay FP64.
+  constexpr bool kPair = sizeof(T) == sizeof(float);
+  __shared__ double ys[kTrialPts][12];   // dfnum in the mixed form (same size)
   __shared__ double fs[kTrialPts][12];
   __shared__ double part_s[3 * kTrialIv][2];
   const int tid = threadIdx.x;
@@ -171,15 +176,30 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
   const int niv = N - i0 < kTrialIv ? N - i0 : kTrialIv;
   const double alpha = s.alpha;
   const int64_t base = node * npts(a.Nmax) + 3 * int64_t(i0);
+  auto ypoint = [&](int64_t pt, int c) { return __fma_rn(alpha, w.D[pt * 12 + c], w.Y[pt * 12 + c]); };
   if (tid <= 3 * niv) {
-    double y[12], F[12];
+    if constexpr (kPair) {
+      dfnum y[12], F[12];
 #pragma unroll
-    for (int c = 0; c < 12; ++c) y[c] = __fma_rn(alpha, w.D[(base + tid) * 12 + c], w.Y[(base + tid) * 12 + c]);
-    char_rhs(a.P, y, F);
+      for (int c = 0; c < 12; ++c) y[c] = dfnum(ypoint(base + tid, c));
+      char_rhs_t<dfnum>(a.P, y, F);
+      dfnum* yp = reinterpret_cast<dfnum*>(ys[tid]);
+      dfnum* fp = reinterpret_cast<dfnum*>(fs[tid]);
 #pragma unroll
-    for (int c = 0; c < 12; ++c) {
-      ys[tid][c] = y[c];
-      fs[tid][c] = F[c];
+      for (int c = 0; c < 12; ++c) {
+        yp[c] = y[c];
+        fp[c] = F[c];
+      }
+    } else {
+      double y[12], F[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) y[c] = ypoint(base + tid, c);
+      char_rhs(a.P, y, F);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        ys[tid][c] = y[c];
+        fs[tid][c] = F[c];
+      }
     }
   }
   __syncthreads();
@@ -191,28 +211,53 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
     T* res = static_cast<T*>(w.Res) + (node * a.Nmax + i0 + j) * kResRows + 12 * (k - 1);
     double ss = 0.0, mx = 0.0;
     bool bad = false;
+    if constexpr (kPair) {
+      const dfnum c0(h * kLobA[k][0]), c1(h * kLobA[k][1]), c2(h * kLobA[k][2]), c3(h * kLobA[k][3]);
+      const dfnum* y0 = reinterpret_cast<const dfnum*>(ys[p0]);
+      const dfnum* yk = reinterpret_cast<const dfnum*>(ys[p0 + k]);
+      const dfnum* f0 = reinterpret_cast<const dfnum*>(fs[p0]);
+      const dfnum* f1 = reinterpret_cast<const dfnum*>(fs[p0 + 1]);
+      const dfnum* f2 = reinterpret_cast<const dfnum*>(fs[p0 + 2]);
+      const dfnum* f3 = reinterpret_cast<const dfnum*>(fs[p0 + 3]);
+      dfnum ssd(0.0);
+      float mxf = 0.0f;
 #pragma unroll
-    for (int c = 0; c < 12; ++c) {
-      const double r = ys[p0 + k][c] - ys[p0][c] -
-                       h * (kLobA[k][0] * fs[p0][c] + kLobA[k][1] * fs[p0 + 1][c] + kLobA[k][2] * fs[p0 + 2][c] +
-                            kLobA[k][3] * fs[p0 + 3][c]);
-      res[c] = static_cast<T>(r);
-      bad = bad || !isfinite(r);
-      ss += r * r;
-      mx = fmax(mx, fabs(r));
+      for (int c = 0; c < 12; ++c) {
+        const dfnum r = (yk[c] - y0[c]) - (((c0 * f0[c] + c1 * f1[c]) + c2 * f2[c]) + c3 * f3[c]);
+        res[c] = r.hi;
+        bad = bad || !isfinite(r.hi);
+        ssd = ssd + r * r;
+        mxf = fmaxf(mxf, fabsf(r.hi));
+      }
+      ss = ssd.to_double();
+      mx = mxf;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        const double r = ys[p0 + k][c] - ys[p0][c] -
+                         h * (kLobA[k][0] * fs[p0][c] + kLobA[k][1] * fs[p0 + 1][c] + kLobA[k][2] * fs[p0 + 2][c] +
+                              kLobA[k][3] * fs[p0 + 3][c]);
+        res[c] = static_cast<T>(r);
+        bad = bad || !isfinite(r);
+        ss += r * r;
+        mx = fmax(mx, fabs(r));
+      }
     }
+    // boundary rows in FP64 from the iterate itself
     if (k == 1 && i0 + j == 0) {
       const double* x0 = a.x0 + node * 6;
       for (int c = 0; c < 6; ++c) {
-        const double r = ys[0][c] - x0[c];
+        const double r = ypoint(base, c) - x0[c];
         bad = bad || !isfinite(r);
         ss += r * r;
         mx = fmax(mx, fabs(r));
       }
     }
     if (k == 3 && i0 + j == N - 1) {
+      double yN[12];
+      for (int c = 0; c < 12; ++c) yN[c] = ypoint(base + p0 + 3, c);
       for (int c = 0; c < 6; ++c) {
-        const double r = ys[p0 + 3][6 + c] - terminal_grad(a.P, ys[p0 + 3], c);
+        const double r = yN[6 + c] - terminal_grad(a.P, yN, c);
         bad = bad || !isfinite(r);
         ss += r * r;
         mx = fmax(mx, fabs(r));

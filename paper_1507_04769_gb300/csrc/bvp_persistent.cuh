@@ -7,7 +7,7 @@
 // their warp longer; no host round trip or grid-wide barrier is involved.
 //
 // The arithmetic is the same as the one-launch-per-phase form: the same
-// kernels' per-warp device functions, the same FP64 residual and Armijo rule.
+// kernels' per-warp device functions, the same residual and Armijo rule.
 #pragma once
 
 #include "bvp_kernels.cuh"
@@ -21,7 +21,7 @@ __host__ __device__ constexpr int persist_smem_per_warp() {
   return sizeof(T) == sizeof(double) ? 36 * kCols * 8 : kCondSmemFloats * 4;
 }
 
-// FP64 residual at Y + alpha D for the whole node, by one warp.  The
+// Residual at Y + alpha D for the whole node, by one warp.  The
 // right-hand side F at every point goes to `Fs` (the node's Jacobian slot,
 // free during the line search); each lane then forms the stage rows of the
 // intervals lane, lane+32, ..., stores them (precision T) for the next
@@ -32,14 +32,28 @@ __device__ __forceinline__ void residual_node(const SolveArgs& a, const Workspac
   const int64_t pb = node * npts(a.Nmax);
   const double* Y = w.Y + pb * 12;
   const double* D = w.D + pb * 12;
+  // F at every point (the node's Jacobian slot is free during the line
+  // search); in the mixed form F and the stage rows are pairs of floats, as in
+  // the launch-per-phase residual
+  constexpr bool kPair = sizeof(T) == sizeof(float);
   double* Fs = reinterpret_cast<double*>(static_cast<T*>(w.Jm) + pb * 144);
   for (int p = lane; p <= 3 * N; p += 32) {
-    double y[12], F[12];
+    if constexpr (kPair) {
+      dfnum y[12], F[12];
 #pragma unroll
-    for (int c = 0; c < 12; ++c) y[c] = __fma_rn(alpha, D[12 * p + c], Y[12 * p + c]);
-    char_rhs(a.P, y, F);
+      for (int c = 0; c < 12; ++c) y[c] = dfnum(__fma_rn(alpha, D[12 * p + c], Y[12 * p + c]));
+      char_rhs_t<dfnum>(a.P, y, F);
+      dfnum* fp = reinterpret_cast<dfnum*>(Fs + 12 * p);
 #pragma unroll
-    for (int c = 0; c < 12; ++c) Fs[12 * p + c] = F[c];
+      for (int c = 0; c < 12; ++c) fp[c] = F[c];
+    } else {
+      double y[12], F[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) y[c] = __fma_rn(alpha, D[12 * p + c], Y[12 * p + c]);
+      char_rhs(a.P, y, F);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) Fs[12 * p + c] = F[c];
+    }
   }
   __syncwarp();
   const double h = a.T[node] / N;
@@ -48,19 +62,42 @@ __device__ __forceinline__ void residual_node(const SolveArgs& a, const Workspac
   for (int i = lane; i < N; i += 32) {
     T* res = static_cast<T*>(w.Res) + (node * a.Nmax + i) * kResRows;
     const int p0 = 3 * i;
-#pragma unroll
-    for (int c = 0; c < 12; ++c) {
-      const double y0 = __fma_rn(alpha, D[12 * p0 + c], Y[12 * p0 + c]);
-      const double f0 = Fs[12 * p0 + c], f1 = Fs[12 * (p0 + 1) + c], f2 = Fs[12 * (p0 + 2) + c],
-                   f3 = Fs[12 * (p0 + 3) + c];
+    if constexpr (kPair) {
+      const dfnum* Fd = reinterpret_cast<const dfnum*>(Fs);
 #pragma unroll
       for (int k = 1; k < 4; ++k) {
-        const double yk = __fma_rn(alpha, D[12 * (p0 + k) + c], Y[12 * (p0 + k) + c]);
-        const double r = yk - y0 - h * (kLobA[k][0] * f0 + kLobA[k][1] * f1 + kLobA[k][2] * f2 + kLobA[k][3] * f3);
-        res[12 * (k - 1) + c] = static_cast<T>(r);
-        bad = bad || !isfinite(r);
-        ss += r * r;
-        mx = fmax(mx, fabs(r));
+        const dfnum c0(h * kLobA[k][0]), c1(h * kLobA[k][1]), c2(h * kLobA[k][2]), c3(h * kLobA[k][3]);
+        dfnum ssd(0.0);
+        float mxf = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          const dfnum y0(__fma_rn(alpha, D[12 * p0 + c], Y[12 * p0 + c]));
+          const dfnum yk(__fma_rn(alpha, D[12 * (p0 + k) + c], Y[12 * (p0 + k) + c]));
+          const dfnum r = (yk - y0) - (((c0 * Fd[12 * p0 + c] + c1 * Fd[12 * (p0 + 1) + c]) +
+                                        c2 * Fd[12 * (p0 + 2) + c]) + c3 * Fd[12 * (p0 + 3) + c]);
+          res[12 * (k - 1) + c] = r.hi;
+          bad = bad || !isfinite(r.hi);
+          ssd = ssd + r * r;
+          mxf = fmaxf(mxf, fabsf(r.hi));
+        }
+        ss += ssd.to_double();
+        mx = fmax(mx, double(mxf));
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        const double y0 = __fma_rn(alpha, D[12 * p0 + c], Y[12 * p0 + c]);
+        const double f0 = Fs[12 * p0 + c], f1 = Fs[12 * (p0 + 1) + c], f2 = Fs[12 * (p0 + 2) + c],
+                     f3 = Fs[12 * (p0 + 3) + c];
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+          const double yk = __fma_rn(alpha, D[12 * (p0 + k) + c], Y[12 * (p0 + k) + c]);
+          const double r = yk - y0 - h * (kLobA[k][0] * f0 + kLobA[k][1] * f1 + kLobA[k][2] * f2 + kLobA[k][3] * f3);
+          res[12 * (k - 1) + c] = static_cast<T>(r);
+          bad = bad || !isfinite(r);
+          ss += r * r;
+          mx = fmax(mx, fabs(r));
+        }
       }
     }
     if (i == 0) {

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "dfnum.cuh"
 
 namespace sg {
 
@@ -34,7 +35,22 @@ struct DevProblem {
   double G[18];   // R^-1 B' (3 x 6)
   double R[9];
   double Bu[18];  // plant input matrix: attitude J^-1 B (rows 3..5 of a 6 x 3), LQ B (6 x 3)
+  // the constants of the right-hand side as (hi, lo) float pairs, for the
+  // pair-of-floats residual of the mixed form (filled on the host)
+  float2 Jinv_f[3], hm_f[3], Kw_f[9], wv_f, ww_f;
+  float2 A_f[36], K_f[36], Q_f[36];
 };
+
+// A problem constant in the number type S of templated code: the double, its
+// float pair, or its float rounding (FP32 Jacobian).
+template <typename S>
+__device__ __forceinline__ S pconst(double d, float2 f);
+template <>
+__device__ __forceinline__ double pconst<double>(double d, float2) { return d; }
+template <>
+__device__ __forceinline__ float pconst<float>(double d, float2) { return static_cast<float>(d); }
+template <>
+__device__ __forceinline__ dfnum pconst<dfnum>(double, float2 f) { return dfnum(f.x, f.y, 0); }
 
 // ------------------------------------------------------------------ duals
 // FP64 sine and cosine.  On |a| <= pi/4 (where the Euler angles of the
@@ -207,7 +223,7 @@ __device__ __forceinline__ void attitude_f0_grad(const DevProblem& P, const S* x
   f0[1] = b;
   f0[2] = sec * a;
   // g = Rx Ry Rz h
-  const T h0 = T(P.hm[0]), h1 = T(P.hm[1]), h2 = T(P.hm[2]);
+  const T h0 = pconst<T>(P.hm[0], P.hm_f[0]), h1 = pconst<T>(P.hm[1], P.hm_f[1]), h2 = pconst<T>(P.hm[2], P.hm_f[2]);
   S az0 = cs * h0 + ss * h1;
   S az1 = cs * h1 - ss * h0;
   // Ry applied to (az0, az1, h2)
@@ -217,7 +233,8 @@ __device__ __forceinline__ void attitude_f0_grad(const DevProblem& P, const S* x
   S g0 = ay0;
   S g1 = cp * az1 + sp * ay2;
   S g2 = cp * ay2 - sp * az1;
-  const T j0 = T(P.Jinv[0]), j1 = T(P.Jinv[1]), j2 = T(P.Jinv[2]);
+  const T j0 = pconst<T>(P.Jinv[0], P.Jinv_f[0]), j1 = pconst<T>(P.Jinv[1], P.Jinv_f[1]),
+          j2 = pconst<T>(P.Jinv[2], P.Jinv_f[2]);
   // g x w
   f0[3] = (g1 * w3 - g2 * w2) * j0;
   f0[4] = (g2 * w1 - g0 * w3) * j1;
@@ -307,47 +324,56 @@ __device__ __forceinline__ void ex3_char(const S* x, const S* lam, S* dx, S* dl)
 }
 
 // ------------------------------------------------------------------ RHS and Jacobian
-// F(y) for y = (x, lambda) in FP64.
-__device__ __forceinline__ void char_rhs(const DevProblem& P, const double* y, double* F) {
+// F(y) for y = (x, lambda) in the number type S: double (FP64) or dfnum
+// (pair of floats, the residual of the mixed form).
+template <typename S>
+__device__ __forceinline__ void char_rhs_t(const DevProblem& P, const S* y, S* F) {
   if (P.kind == SG_PROBLEM_EXAMPLE3) {
-    double dx[3], dl[3];
-    ex3_char<double>(y, y + 6, dx, dl);
+    S dx[3], dl[3];
+    ex3_char<S>(y, y + 6, dx, dl);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       F[i] = dx[i];
-      F[3 + i] = 0.0;
+      F[3 + i] = S(0.0);
       F[6 + i] = dl[i];
-      F[9 + i] = 0.0;
+      F[9 + i] = S(0.0);
     }
     return;
   }
   if (P.kind == SG_PROBLEM_ATTITUDE) {
-    double f0[6], g[6];
-    attitude_f0_grad<double, double>(P, y, y + 6, f0, g);
+    S f0[6], g[6];
+    attitude_f0_grad<S, S>(P, y, y + 6, f0, g);
 #pragma unroll
     for (int i = 0; i < 3; ++i) F[i] = f0[i];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      F[3 + i] = f0[3 + i] - (P.Kw[3 * i] * y[9] + P.Kw[3 * i + 1] * y[10] + P.Kw[3 * i + 2] * y[11]);
+      F[3 + i] = f0[3 + i] - (pconst<S>(P.Kw[3 * i], P.Kw_f[3 * i]) * y[9] +
+                              pconst<S>(P.Kw[3 * i + 1], P.Kw_f[3 * i + 1]) * y[10] +
+                              pconst<S>(P.Kw[3 * i + 2], P.Kw_f[3 * i + 2]) * y[11]);
+    const S wv = pconst<S>(P.wv, P.wv_f), ww = pconst<S>(P.ww, P.ww_f);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) F[6 + i] = -P.wv * y[i] - g[i];
+    for (int i = 0; i < 3; ++i) F[6 + i] = -(wv * y[i]) - g[i];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) F[9 + i] = -P.ww * y[3 + i] - g[3 + i];
+    for (int i = 0; i < 3; ++i) F[9 + i] = -(ww * y[3 + i]) - g[3 + i];
   } else {
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      double ax = 0.0, kl = 0.0, qx = 0.0, atl = 0.0;
+      S ax(0.0), kl(0.0), qx(0.0), atl(0.0);
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
-        ax += P.A[6 * i + j] * y[j];
-        kl += P.K[6 * i + j] * y[6 + j];
-        qx += P.Q[6 * i + j] * y[j];
-        atl += P.A[6 * j + i] * y[6 + j];
+        ax = ax + pconst<S>(P.A[6 * i + j], P.A_f[6 * i + j]) * y[j];
+        kl = kl + pconst<S>(P.K[6 * i + j], P.K_f[6 * i + j]) * y[6 + j];
+        qx = qx + pconst<S>(P.Q[6 * i + j], P.Q_f[6 * i + j]) * y[j];
+        atl = atl + pconst<S>(P.A[6 * j + i], P.A_f[6 * j + i]) * y[6 + j];
       }
       F[i] = ax - kl;
       F[6 + i] = -qx - atl;
     }
   }
+}
+
+__device__ __forceinline__ void char_rhs(const DevProblem& P, const double* y, double* F) {
+  char_rhs_t<double>(P, y, F);
 }
 
 // Jacobian dF/dy (12 x 12, row-major) in precision T, from one dual pass over
