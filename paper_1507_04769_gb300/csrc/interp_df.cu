@@ -52,46 +52,53 @@ __device__ __forceinline__ void df_group(const unsigned char* __restrict__ tab_q
                                          const float2* __restrict__ w_s, int n0, int n1, int stream,
                                          DfAcc (&acc)[K], int& since_fold) {
   int nn = n0 + ((stream - n0) % NS + NS) % NS;
-#pragma unroll 2
-  for (; nn < n1; nn += NS) {
-    df phi = {1.0f, 0.0f};
-    if constexpr (A > 0) {
-      uint32_t o[A];
-      if constexpr (A <= 4) {
-        const uint4 v = *reinterpret_cast<const uint4*>(off_s + nn * kMaxDim);
-        const uint32_t t[4] = {v.x, v.y, v.z, v.w};
+  int left = nn < n1 ? (n1 - nn + NS - 1) / NS : 0;
+  while (left > 0) {
+    // a run of nodes up to the next fold, with no per-node fold test
+    const int run = left < kFoldBlock - since_fold ? left : kFoldBlock - since_fold;
+#pragma unroll 4
+    for (int r = 0; r < run; ++r, nn += NS) {
+      df phi = {1.0f, 0.0f};
+      if constexpr (A > 0) {
+        uint32_t o[A];
+        if constexpr (A <= 4) {
+          const uint4 v = *reinterpret_cast<const uint4*>(off_s + nn * kMaxDim);
+          const uint32_t t[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int a = 0; a < A; ++a) o[a] = t[a];
-      } else {
-        const uint4 v0 = *reinterpret_cast<const uint4*>(off_s + nn * kMaxDim);
-        const uint4 v1 = *reinterpret_cast<const uint4*>(off_s + nn * kMaxDim + 4);
-        const uint32_t t[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+          for (int a = 0; a < A; ++a) o[a] = t[a];
+        } else {
+          const uint4 v0 = *reinterpret_cast<const uint4*>(off_s + nn * kMaxDim);
+          const uint4 v1 = *reinterpret_cast<const uint4*>(off_s + nn * kMaxDim + 4);
+          const uint32_t t[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-        for (int a = 0; a < A; ++a) o[a] = t[a];
+          for (int a = 0; a < A; ++a) o[a] = t[a];
+        }
+        const float2 f0 = *reinterpret_cast<const float2*>(tab_q + o[0]);
+        phi = {f0.x, f0.y};
+#pragma unroll
+        for (int a = 1; a < A; ++a) {
+          const float2 f = *reinterpret_cast<const float2*>(tab_q + o[a]);
+          phi = df_mul_raw(phi, {f.x, f.y});
+        }
       }
-      const float2 f0 = *reinterpret_cast<const float2*>(tab_q + o[0]);
-      phi = {f0.x, f0.y};
 #pragma unroll
-      for (int a = 1; a < A; ++a) {
-        const float2 f = *reinterpret_cast<const float2*>(tab_q + o[a]);
-        phi = df_mul_raw(phi, {f.x, f.y});
+      for (int c = 0; c < K; ++c) {
+        const float2 wc = w_s[nn * K + c];
+        // exact product phi.hi * w.hi = p + pe; cross terms to t
+        const float p = __fmul_rn(phi.hi, wc.x);
+        const float pe = __fmaf_rn(phi.hi, wc.x, -p);
+        const float t = __fadd_rn(__fmaf_rn(phi.hi, wc.y, __fmul_rn(phi.lo, wc.x)), pe);
+        // Knuth's two_sum of the running sum and p
+        const float s = __fadd_rn(acc[c].ah, p);
+        const float bb = __fsub_rn(s, acc[c].ah);
+        const float se = __fadd_rn(__fsub_rn(acc[c].ah, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+        acc[c].ah = s;
+        acc[c].al = __fadd_rn(acc[c].al, __fadd_rn(se, t));
       }
     }
-#pragma unroll
-    for (int c = 0; c < K; ++c) {
-      const float2 wc = w_s[nn * K + c];
-      // exact product phi.hi * w.hi = p + pe; cross terms to t
-      const float p = __fmul_rn(phi.hi, wc.x);
-      const float pe = __fmaf_rn(phi.hi, wc.x, -p);
-      const float t = __fadd_rn(__fmaf_rn(phi.hi, wc.y, __fmul_rn(phi.lo, wc.x)), pe);
-      // Knuth's two_sum of the running sum and p
-      const float s = __fadd_rn(acc[c].ah, p);
-      const float bb = __fsub_rn(s, acc[c].ah);
-      const float se = __fadd_rn(__fsub_rn(acc[c].ah, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-      acc[c].ah = s;
-      acc[c].al = __fadd_rn(acc[c].al, __fadd_rn(se, t));
-    }
-    if (++since_fold == kFoldBlock) {
+    left -= run;
+    since_fold += run;
+    if (since_fold == kFoldBlock) {
       since_fold = 0;
 #pragma unroll
       for (int c = 0; c < K; ++c) {
