@@ -100,15 +100,20 @@ def _col(vec, like):
 
 
 class Attitude:
-    """All state arrays are (12, ...) or (6, ...): component first, points after."""
-    n = 12
-    m = 3
+    """All state arrays are (12, ...) or (6, ...): component first, points after.
 
-    def __init__(self, p: synth.AttitudeParams):
+    B is 3 x m (m = 3: Example I; m = 2: Example II).  The running cost
+    penalises v - v_e for a target attitude v_e (0 unless given; Example II
+    takes v_e from target_attitude)."""
+    n = 12
+
+    def __init__(self, p: synth.AttitudeParams, target=None):
         self.p = p
         self.Jinv = 1.0 / np.asarray(p.J, dtype=np.float64)
         self.B = np.asarray(p.B, dtype=np.float64)
+        self.m = self.B.shape[1]
         self.hmom = np.asarray(p.hmom, dtype=np.float64)
+        self.target = np.zeros(3) if target is None else np.asarray(target, dtype=np.float64)
         JB = self.Jinv[:, None] * self.B               # J^{-1} B
         self.Kw = JB @ JB.T / p.r                      # K restricted to the w block
 
@@ -156,7 +161,7 @@ class Attitude:
         return np.concatenate([gv, gw])
 
     def grad_l(self, x):
-        return np.concatenate([self.p.wv * x[:3], self.p.ww * x[3:6]])
+        return np.concatenate([self.p.wv * (x[:3] - _col(self.target, x[:3])), self.p.ww * x[3:6]])
 
     def rhs(self, y):
         """Characteristic right-hand side F(y), y = (x, lambda), shape (12, ...)."""
@@ -168,7 +173,8 @@ class Attitude:
     def running_cost(self, y):
         x, lam = y[:6], y[6:]
         u = self.ustar(x, lam)
-        return 0.5 * (self.p.wv * (x[:3] ** 2).sum(0) + self.p.ww * (x[3:6] ** 2).sum(0)
+        dv = x[:3] - _col(self.target, x[:3])
+        return 0.5 * (self.p.wv * (dv ** 2).sum(0) + self.p.ww * (x[3:6] ** 2).sum(0)
                       + self.p.r * (u ** 2).sum(0))
 
     def terminal(self, x):
@@ -184,7 +190,8 @@ class Attitude:
         """H*(x, lambda) = L(x, u*) + lambda' f(x, u*)."""
         x, lam = y[:6], y[6:]
         u = self.ustar(x, lam)
-        f = self.f0(x) + np.concatenate([np.zeros_like(u), _col(self.Jinv, u) * _mv(self.B, u)])
+        Bu = _mv(self.B, u)
+        f = self.f0(x) + np.concatenate([np.zeros_like(Bu), _col(self.Jinv, Bu) * Bu])
         return self.running_cost(y) + (lam * f).sum(0)
 
 
@@ -332,9 +339,38 @@ class Example3:
         return -x[2] / g * np.tanh(tau)
 
 
-def make(params):
+def reachable_normal(B):
+    """C with C' B = 0 (Example II: the momentum direction the wheels cannot
+    change), unit length; for m = 2 the cross product of B's columns."""
+    B = np.asarray(B, dtype=np.float64)
+    c = np.cross(B[:, 0], B[:, 1])
+    return c / np.linalg.norm(c)
+
+
+def target_attitude(params, x0, guesses=None):
+    """Eq. optim_attitude: v_e = argmax tr R(v) subject to
+    -C' R(v) H = C' (J w0 - R(v0) H), by SLSQP from several starts (the
+    largest trace wins).  x0 = (v0, w0)."""
+    from scipy.optimize import minimize
+    B = np.asarray(params.B, dtype=np.float64)
+    J = np.asarray(params.J, dtype=np.float64)
+    H = np.asarray(params.hmom, dtype=np.float64)
+    C = reachable_normal(B)
+    v0, w0 = np.asarray(x0[:3], dtype=np.float64), np.asarray(x0[3:6], dtype=np.float64)
+    rhs = C @ (J * w0 - rot(v0) @ H)
+    cons = {"type": "eq", "fun": lambda v: -C @ rot(v) @ H - rhs}
+    best = None
+    for g in (guesses if guesses is not None else (v0, np.zeros(3))):
+        r = minimize(lambda v: -np.trace(rot(v)), np.asarray(g, dtype=np.float64), constraints=[cons],
+                     method="SLSQP", tol=1e-15, options={"maxiter": 500})
+        if r.success and abs(cons["fun"](r.x)) < 1e-12 and (best is None or r.fun < best.fun):
+            best = r
+    return best.x
+
+
+def make(params, target=None):
     if params.kind == synth.ATTITUDE:
-        return Attitude(params)
+        return Attitude(params, target)
     if params.kind == synth.EXAMPLE3:
         return Example3(params)
     return LinearQuadratic(params)

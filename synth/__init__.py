@@ -40,6 +40,8 @@ class AttitudeParams:
     tv: float = 1.0
     tw: float = 1.0
     kind: int = field(default=ATTITUDE, init=False)
+    # B may be 3 x m (m = 2: Example II's two pairs of wheels); the running cost
+    # then penalises v - v_e with a per-state target v_e (Example II)
 
 
 @dataclass
@@ -102,6 +104,24 @@ def example1_params() -> AttitudeParams:
                   [1.0 / 10.0, 1.0 / 15.0, 1.0]])
     return AttitudeParams(J=np.array([2.0, 3.0, 4.0]), hmom=np.ones(3), B=B,
                           wv=1.0, ww=1.0, r=0.5, tv=2.0, tw=2.0)
+
+
+def example2_params() -> AttitudeParams:
+    """The printed parameters of Example II (Section 5): two pairs of momentum
+    wheels, B = [[1, 1/10], [0, 1], [1/12, 0]], J = diag(2, 3, 4),
+    H = (12, 12, 6), L = W1/2 |v - v_e|^2 + W2/2 |w|^2 + W3/2 |u|^2 with
+    W1 = 1, W2 = 2, W3 = 0.5, no terminal cost, T = 30."""
+    B = np.array([[1.0, 0.1], [0.0, 1.0], [1.0 / 12.0, 0.0]])
+    return AttitudeParams(J=np.array([2.0, 3.0, 4.0]), hmom=np.array([12.0, 12.0, 6.0]), B=B,
+                          wv=1.0, ww=2.0, r=0.5, tv=0.0, tw=0.0)
+
+
+EXAMPLE2_T = 30.0
+
+
+def example2_box():
+    """The domain D of Example II: v in [-pi/6, pi/6]^3, w in [-pi/8, pi/8]^3."""
+    return (np.array([-np.pi / 6] * 3 + [-np.pi / 8] * 3), np.array([np.pi / 6] * 3 + [np.pi / 8] * 3))
 
 
 def lq_params(seed: int = 0) -> LQParams:
