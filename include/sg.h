@@ -76,8 +76,10 @@ enum { SG_EVAL_FP64 = 0, SG_EVAL_TF32X3 = 1, SG_EVAL_DF32 = 2 };
  * SG_PROBLEM_ATTITUDE (Section 5, Eq. sat_model): x = (phi, theta, psi, w1, w2, w3),
  *   v' = E(v) w,  J w' = S(w) R(v) hmom + B u   with 3-2-1 Euler angles,
  *   E the Euler-rate matrix, R = Rx(phi) Ry(theta) Rz(psi) (inertial -> body),
- *   S(w) a = a x w.  Running cost 0.5 (wv |v|^2 + ww |w|^2 + r |u|^2),
- *   terminal cost 0.5 (tv |v(T)|^2 + tw |w(T)|^2).
+ *   S(w) a = a x w.  Running cost 0.5 (wv |v - v_e|^2 + ww |w|^2 + r |u|^2)
+ *   (v_e = 0 unless d_target is given), terminal cost 0.5 (tv |v(T)|^2 + tw |w(T)|^2).
+ *   m = 3 is Example I's three pairs of wheels; m = 2 with tv = tw = 0 and the
+ *   targets of sg_attitude_targets is Example II (two pairs, uncontrollable).
  * SG_PROBLEM_LQ: x' = A x + Blq u, running cost 0.5 (x'Qx + u'Ru),
  *   terminal 0.5 x'QT x; R must be symmetric positive definite.
  * SG_PROBLEM_EXAMPLE3 (Section 5, Example III): three states in x[0..2]
@@ -89,11 +91,11 @@ enum { SG_EVAL_FP64 = 0, SG_EVAL_TF32X3 = 1, SG_EVAL_DF32 = 2 };
  * Unused fields of the other families are ignored. */
 typedef struct sg_problem {
   int32_t kind;
-  int32_t _pad;
+  int32_t m;         /* attitude: number of controls, 2 or 3 (0 means 3)      */
   /* attitude */
   double J[3];       /* diagonal inertia                       */
   double hmom[3];    /* total angular momentum, inertial frame */
-  double B[9];       /* 3x3 control matrix, row-major          */
+  double B[9];       /* 3x3 control matrix, row-major; columns >= m ignored    */
   double wv, ww, r, tv, tw;
   /* LQ */
   double A[36];      /* 6x6 */
@@ -101,6 +103,10 @@ typedef struct sg_problem {
   double Q[36];      /* 6x6 */
   double R[9];       /* 3x3 */
   double QT[36];     /* 6x6 */
+  /* attitude: device array of per-node target attitudes v_e (n x 3 doubles,
+     row i for x0 row i of the solve), or NULL for v_e = 0.  The running cost
+     penalises wv |v - v_e|^2 (Example II; sg_attitude_targets computes them). */
+  const double* d_target;
 } sg_problem;
 
 typedef struct sg_solve_opts {
@@ -238,6 +244,21 @@ int sg_autotune_solve(const sg_problem* prob, const double* d_x0, int64_t n, con
                       void* d_work, size_t work_bytes, double* d_lambda0, double* d_u0,
                       double* d_V, int32_t* d_status, int32_t* d_iters, sg_solve_opts* best,
                       double* report_ms, int force, void* stream);
+
+/* sg_attitude_targets - Example II (Section 5, Eq. optim_attitude): for each
+ * initial state x0 = (v, w) the target attitude
+ *     v_e = argmax tr R(vt)  subject to  -C' R(vt) H = C' (J w - R(v) H),
+ * C the unit normal of B's two columns (C' B = 0; m = 2).  The constraint is
+ * the momentum component the wheels cannot change, so v_e is constant along
+ * every controlled trajectory from x0.  Newton's method on the optimality
+ * conditions from vt = v (then from vt = 0 if that does not reach a maximum).
+ *   d_x0      n x 6 doubles (device); d_target n x 3 doubles (device, output)
+ *   d_status  n int32 (device, output, may be NULL): 0 found, 1 no maximum found
+ *             (the target row is then NaN)
+ * Asynchronous on `stream`.  Errors: SG_EINVAL (not an attitude problem with
+ * m = 2, parallel columns of B, sizes, pointers), SG_ECUDA. */
+int sg_attitude_targets(const sg_problem* prob, const double* d_x0, int64_t n, double* d_target,
+                        int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------- Step III
  * sg_build_surpluses - hierarchical surpluses of values at the grid nodes,

@@ -363,9 +363,38 @@ def target_attitude(params, x0, guesses=None):
     for g in (guesses if guesses is not None else (v0, np.zeros(3))):
         r = minimize(lambda v: -np.trace(rot(v)), np.asarray(g, dtype=np.float64), constraints=[cons],
                      method="SLSQP", tol=1e-15, options={"maxiter": 500})
-        if r.success and abs(cons["fun"](r.x)) < 1e-12 and (best is None or r.fun < best.fun):
+        if r.success and abs(cons["fun"](r.x)) < 1e-10 and (best is None or r.fun < best.fun):
             best = r
-    return best.x
+    # SLSQP stops on the flat top of tr R about 1e-8 from the maximiser; a few
+    # Newton steps on the optimality conditions (complex-step gradients,
+    # Hessians by central differences of them) finish it
+    def grad(fun, v):
+        g = np.empty(3)
+        for i in range(3):
+            vc = v.astype(np.complex128)
+            vc[i] += 1e-30j
+            g[i] = fun(vc).imag / 1e-30
+        return g
+
+    ftr = lambda v: rot(v)[0, 0] + rot(v)[1, 1] + rot(v)[2, 2]
+    fc = lambda v: -C @ rot(v) @ H - rhs
+    v = best.x.copy()
+    gc = grad(fc, v)
+    mu = -grad(ftr, v) @ gc / (gc @ gc)
+    for _ in range(8):
+        res = np.concatenate([grad(ftr, v) + mu * grad(fc, v), [fc(v).real]])
+        K = np.zeros((4, 4))
+        for j in range(3):
+            e = np.zeros(3)
+            e[j] = 1e-6
+            K[:3, j] = ((grad(ftr, v + e) + mu * grad(fc, v + e)) - (grad(ftr, v - e) + mu * grad(fc, v - e))) / 2e-6
+        gc = grad(fc, v)
+        K[:3, 3] = gc
+        K[3, :3] = gc
+        step = np.linalg.solve(K, -res)
+        v = v + step[:3]
+        mu = mu + step[3]
+    return v
 
 
 def make(params, target=None):

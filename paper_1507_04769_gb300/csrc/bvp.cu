@@ -72,15 +72,22 @@ bool make_dev_problem(const sg_problem& in, DevProblem* out) {
       p.Jinv[i] = 1.0 / in.J[i];
       p.hm[i] = in.hmom[i];
     }
+    const int m = in.m == 0 ? 3 : in.m;
+    if (m != 2 && m != 3) return false;
+    p.m = m;
+    p.target = in.d_target;
+    double Bm[9];   // B with the columns beyond m zeroed
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Bm[3 * i + j] = j < m ? in.B[3 * i + j] : 0.0;
     double JB[9];
     for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) JB[3 * i + j] = p.Jinv[i] * in.B[3 * i + j];
+      for (int j = 0; j < 3; ++j) JB[3 * i + j] = p.Jinv[i] * Bm[3 * i + j];
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) {
         double s = 0.0;
         for (int m = 0; m < 3; ++m) s += JB[3 * i + m] * JB[3 * j + m];
         p.Kw[3 * i + j] = s / in.r;
-        p.Gw[3 * i + j] = in.B[3 * j + i] * p.Jinv[j] / in.r;
+        p.Gw[3 * i + j] = Bm[3 * j + i] * p.Jinv[j] / in.r;
       }
     // plant input matrix J^-1 B in rows 3..5 of a 6 x 3 (rows 0..2 zero)
     for (int i = 0; i < 3; ++i)

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
       dfnum y[12], F[12];
 #pragma unroll
       for (int c = 0; c < 12; ++c) y[c] = dfnum(ypoint(base + tid, c));
-      char_rhs_t<dfnum>(a.P, y, F);
+      char_rhs_t<dfnum>(a.P, y, F, node_target(a.P, node));
       dfnum* yp = reinterpret_cast<dfnum*>(ys[tid]);
       dfnum* fp = reinterpret_cast<dfnum*>(fs[tid]);
 #pragma unroll
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
       double y[12], F[12];
 #pragma unroll
       for (int c = 0; c < 12; ++c) y[c] = ypoint(base + tid, c);
-      char_rhs(a.P, y, F);
+      char_rhs(a.P, y, F, node_target(a.P, node));
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
         ys[tid][c] = y[c];
@@ -1237,8 +1237,9 @@ __global__ void k_outputs(SolveArgs a, Workspace w, double* lambda0, double* u0,
   double z = 0.0;
   for (int i = lane; i < N; i += 32) {
     const double* yi = Y + 3 * int64_t(i) * 12;
-    z += h * (kLobB[0] * running_cost(a.P, yi) + kLobB[1] * running_cost(a.P, yi + 12) +
-              kLobB[2] * running_cost(a.P, yi + 24) + kLobB[3] * running_cost(a.P, yi + 36));
+    const double* ve = node_target(a.P, node);
+    z += h * (kLobB[0] * running_cost(a.P, yi, ve) + kLobB[1] * running_cost(a.P, yi + 12, ve) +
+              kLobB[2] * running_cost(a.P, yi + 24, ve) + kLobB[3] * running_cost(a.P, yi + 36, ve));
   }
   z = warp_sum(z);
   if (lane == 0) {

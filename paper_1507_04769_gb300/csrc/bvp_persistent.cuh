@@ -42,7 +42,7 @@ __device__ __forceinline__ void residual_node(const SolveArgs& a, const Workspac
       dfnum y[12], F[12];
 #pragma unroll
       for (int c = 0; c < 12; ++c) y[c] = dfnum(__fma_rn(alpha, D[12 * p + c], Y[12 * p + c]));
-      char_rhs_t<dfnum>(a.P, y, F);
+      char_rhs_t<dfnum>(a.P, y, F, node_target(a.P, node));
       dfnum* fp = reinterpret_cast<dfnum*>(Fs + 12 * p);
 #pragma unroll
       for (int c = 0; c < 12; ++c) fp[c] = F[c];
@@ -50,7 +50,7 @@ __device__ __forceinline__ void residual_node(const SolveArgs& a, const Workspac
       double y[12], F[12];
 #pragma unroll
       for (int c = 0; c < 12; ++c) y[c] = __fma_rn(alpha, D[12 * p + c], Y[12 * p + c]);
-      char_rhs(a.P, y, F);
+      char_rhs(a.P, y, F, node_target(a.P, node));
 #pragma unroll
       for (int c = 0; c < 12; ++c) Fs[12 * p + c] = F[c];
     }

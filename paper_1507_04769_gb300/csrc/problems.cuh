@@ -21,6 +21,8 @@ namespace sg {
 // Problem data with the derived matrices precomputed on the host.
 struct DevProblem {
   int kind;
+  int m;                 // attitude: number of controls (2 or 3)
+  const double* target;  // attitude: per-node target attitudes v_e (n x 3) or null
   // attitude (Section 5, Eq. sat_model)
   double Jinv[3];
   double hm[3];
@@ -327,7 +329,7 @@ __device__ __forceinline__ void ex3_char(const S* x, const S* lam, S* dx, S* dl)
 // F(y) for y = (x, lambda) in the number type S: double (FP64) or dfnum
 // (pair of floats, the residual of the mixed form).
 template <typename S>
-__device__ __forceinline__ void char_rhs_t(const DevProblem& P, const S* y, S* F) {
+__device__ __forceinline__ void char_rhs_t(const DevProblem& P, const S* y, S* F, const double* ve = nullptr) {
   if (P.kind == SG_PROBLEM_EXAMPLE3) {
     S dx[3], dl[3];
     ex3_char<S>(y, y + 6, dx, dl);
@@ -351,8 +353,13 @@ __device__ __forceinline__ void char_rhs_t(const DevProblem& P, const S* y, S* F
                               pconst<S>(P.Kw[3 * i + 1], P.Kw_f[3 * i + 1]) * y[10] +
                               pconst<S>(P.Kw[3 * i + 2], P.Kw_f[3 * i + 2]) * y[11]);
     const S wv = pconst<S>(P.wv, P.wv_f), ww = pconst<S>(P.ww, P.ww_f);
+    if (ve) {   // running cost on v - v_e
 #pragma unroll
-    for (int i = 0; i < 3; ++i) F[6 + i] = -(wv * y[i]) - g[i];
+      for (int i = 0; i < 3; ++i) F[6 + i] = -(wv * (y[i] - S(ve[i]))) - g[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) F[6 + i] = -(wv * y[i]) - g[i];
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) F[9 + i] = -(ww * y[3 + i]) - g[3 + i];
   } else {
@@ -372,8 +379,14 @@ __device__ __forceinline__ void char_rhs_t(const DevProblem& P, const S* y, S* F
   }
 }
 
-__device__ __forceinline__ void char_rhs(const DevProblem& P, const double* y, double* F) {
-  char_rhs_t<double>(P, y, F);
+__device__ __forceinline__ void char_rhs(const DevProblem& P, const double* y, double* F,
+                                         const double* ve = nullptr) {
+  char_rhs_t<double>(P, y, F, ve);
+}
+
+// The target attitude row of a node (attitude family), or null.
+__device__ __forceinline__ const double* node_target(const DevProblem& P, int64_t node) {
+  return (P.kind == SG_PROBLEM_ATTITUDE && P.target) ? P.target + node * 3 : nullptr;
 }
 
 // Jacobian dF/dy (12 x 12, row-major) in precision T, from one dual pass over
@@ -480,7 +493,7 @@ __device__ __forceinline__ void char_jacobian(const DevProblem& P, const double*
 }
 
 // Running cost L(x, u*(x, lambda)) (Section 2) at y = (x, lambda).
-__device__ __forceinline__ double running_cost(const DevProblem& P, const double* y) {
+__device__ __forceinline__ double running_cost(const DevProblem& P, const double* y, const double* ve = nullptr) {
   if (P.kind == SG_PROBLEM_EXAMPLE3) {
     const double g = 1.0 + y[0] * y[0] + y[1] * y[1];
     const double u = -g * y[8];
@@ -492,7 +505,8 @@ __device__ __forceinline__ double running_cost(const DevProblem& P, const double
     for (int i = 0; i < 3; ++i) {
       u[i] = -(P.Gw[3 * i] * y[9] + P.Gw[3 * i + 1] * y[10] + P.Gw[3 * i + 2] * y[11]);
       su += u[i] * u[i];
-      sv += y[i] * y[i];
+      const double dv = ve ? y[i] - ve[i] : y[i];
+      sv += dv * dv;
       sw += y[3 + i] * y[3 + i];
     }
     return 0.5 * (P.wv * sv + P.ww * sw + P.r * su);

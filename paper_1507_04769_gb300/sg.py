@@ -23,12 +23,12 @@ EVAL_FP64, EVAL_TF32X3, EVAL_DF32 = 0, 1, 2
 
 
 class Problem(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("_pad", C.c_int32),
+    _fields_ = [("kind", C.c_int32), ("m", C.c_int32),
                 ("J", C.c_double * 3), ("hmom", C.c_double * 3), ("B", C.c_double * 9),
                 ("wv", C.c_double), ("ww", C.c_double), ("r", C.c_double),
                 ("tv", C.c_double), ("tw", C.c_double),
                 ("A", C.c_double * 36), ("Blq", C.c_double * 18), ("Q", C.c_double * 36),
-                ("R", C.c_double * 9), ("QT", C.c_double * 36)]
+                ("R", C.c_double * 9), ("QT", C.c_double * 36), ("d_target", C.c_void_p)]
 
 
 class SolveOpts(C.Structure):
@@ -71,6 +71,8 @@ def _load():
     lib.sg_surplus_free.restype = None
     lib.sg_eval_feedback.argtypes = [P, P, I64, I32, P, P]
     lib.sg_sincos_probe.argtypes = [P, I64, P, P, P]
+    lib.sg_attitude_targets.argtypes = [C.POINTER(Problem), P, I64, P, P, P]
+    lib.sg_attitude_targets.restype = C.c_int
     lib.sg_theorem1_bound.argtypes = [I32, I32, C.POINTER(D)]
     lib.sg_theorem1_bound.restype = C.c_int
     for name in ("sg_build_grid", "sg_grid_info", "sg_solve_bvps", "sg_build_surpluses",
@@ -110,9 +112,10 @@ class _DevView:
 
 
 # --------------------------------------------------------------- problems
-def problem_from(params) -> Problem:
+def problem_from(params, target: torch.Tensor | None = None) -> Problem:
     """Builds the ABI struct from synthetic parameters (AttitudeParams /
-    LQParams / Example3Params)."""
+    LQParams / Example3Params).  target: per-node target attitudes (n, 3) on the
+    device for the attitude family (kept alive by the caller while in use)."""
     p = Problem()
     if params.kind == PROBLEM_EXAMPLE3:
         p.kind = PROBLEM_EXAMPLE3
@@ -120,7 +123,15 @@ def problem_from(params) -> Problem:
         p.kind = PROBLEM_ATTITUDE
         p.J[:] = [float(v) for v in np.asarray(params.J).ravel()]
         p.hmom[:] = [float(v) for v in np.asarray(params.hmom).ravel()]
-        p.B[:] = [float(v) for v in np.asarray(params.B).ravel()]
+        B = np.asarray(params.B, dtype=np.float64).reshape(3, -1)
+        p.m = B.shape[1]
+        B3 = np.zeros((3, 3))
+        B3[:, :p.m] = B
+        p.B[:] = [float(v) for v in B3.ravel()]
+        if target is not None:
+            if target.dtype != torch.float64 or not target.is_cuda or not target.is_contiguous():
+                raise ValueError("target must be a contiguous float64 CUDA tensor (n, 3)")
+            p.d_target = target.data_ptr()
         p.wv, p.ww, p.r, p.tv, p.tw = params.wv, params.ww, params.r, params.tv, params.tw
     else:
         p.kind = PROBLEM_LQ
@@ -303,6 +314,16 @@ def mc_error_amplification(d: int, level: int, n_points: int, seed: int = 0, sym
     S = Surplus(g, eps.to(device))
     e = eval_feedback(S, xq.to(device), mode=mode)
     return float(e.abs().max().item())
+
+
+def attitude_targets(problem: Problem, x0: torch.Tensor, stream=None):
+    """sg_attitude_targets: Example II target attitudes (n, 3) and status (n,)."""
+    x0 = _dev(x0, torch.float64).reshape(-1, 6)
+    n = x0.shape[0]
+    tgt = torch.empty((n, 3), dtype=torch.float64, device=x0.device)
+    st = torch.empty((n,), dtype=torch.int32, device=x0.device)
+    _check(LIB.sg_attitude_targets(C.byref(problem), _ptr(x0), n, _ptr(tgt), _ptr(st), _stream(stream)))
+    return tgt, st
 
 
 def sincos_probe(x: torch.Tensor, stream=None):
