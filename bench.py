@@ -526,7 +526,24 @@ def gpu_arm(args):
         vres = val.validate_feedback(prob, sg.Surplus(gv, rv["u0"]), pts, 20.0, tol=1e-9)
         b4.record(stream)
         torch.cuda.synchronize()
+        # Example II: the two-wheel attitude problem at q = 13 (44,689 nodes,
+        # per-node target attitudes), V validated at 1,280 random states
+        from paper_1507_04769_gb300 import surfaces
+        prm2 = synth.example2_params()
+        lo2, hi2 = synth.example2_box()
+        a5, b5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a5.record(stream)
+        srf2 = surfaces.two_wheel_surface(prm2, 7, lo2, hi2, synth.EXAMPLE2_T, precision=prec, tol=TOL)
+        b5.record(stream)
+        torch.cuda.synchronize()
+        pts2 = torch.as_tensor(synth.uniform_queries(1280, lo2, hi2, seed=51), device=dev)
+        tgt2, _ = sg.attitude_targets(sg.problem_from(prm2), pts2)
+        v2 = val.validate_value(sg.problem_from(prm2), srf2.surplus, pts2, synth.EXAMPLE2_T, 1e-9, value_col=2,
+                                target=tgt2)
         extensions = {
+            "example2_q13": dict(v2.stats(0), nodes=srf2.grid.M, continued_nodes=srf2.continued,
+                                 targets_solves_surplus_ms=a5.elapsed_time(b5), reference_tol=1e-9,
+                                 paper={"relative_mae_V": 8.5e-3}),
             "validation_attitude_L4_T20": dict(vres.stats(0), reference_tol=1e-9, component="u1",
                                                ms=a4.elapsed_time(b4),
                                                all_components_mae=[vres.stats(c)["mae"] for c in range(3)]),

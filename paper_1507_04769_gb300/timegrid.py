@@ -18,7 +18,7 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from . import sg
+from . import sg, surfaces
 
 
 @dataclass
@@ -70,22 +70,8 @@ def solve_value_surface(problem: sg.Problem, n_state: int, level: int, lo, hi, t
     tau = tau_d.cpu().numpy()
     N = np.asarray(mesh(tau), dtype=np.int32)
     N_d = torch.as_tensor(N, device=device)
-    n_max = int(N.max())
-    res = sg.solve_bvps(problem, x0, tau_d, N_d, tol=tol, max_iter=max_iter, precision=precision, n_max=n_max)
-    stalled = torch.nonzero(res["status"] != sg.CONVERGED).flatten()
-    n_continued = int(stalled.numel())
-    for schedule in continuation:   # finer schedules for the nodes that still stall
-        idx = torch.nonzero(res["status"] != sg.CONVERGED).flatten()
-        if not idx.numel():
-            break
-        Y = None
-        for k, scale in enumerate(schedule):
-            sub = sg.solve_bvps(problem, x0[idx].contiguous(), (tau_d[idx] * scale).contiguous(),
-                                N_d[idx].contiguous(), tol=tol, max_iter=max_iter, precision=precision,
-                                n_max=n_max, Y0=Y, return_Y=True)
-            Y = sub["Y"]
-        for key in ("lambda0", "u0", "V", "status", "iters"):
-            res[key][idx] = sub[key]
+    res, n_continued = surfaces.solve_nodes(problem, x0, tau_d, N_d, precision=precision, tol=tol,
+                                            max_iter=max_iter, schedules=continuation)
     bad = int((res["status"] != sg.CONVERGED).sum().item())
     if bad:
         raise RuntimeError(f"{bad} of {M} nodes did not converge (max_iter = {max_iter}, with continuation)")

@@ -20,7 +20,7 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from . import sg
+from . import sg, surfaces
 
 ORDER = 6   # superconvergence order of four-stage Lobatto IIIA at the mesh points
 
@@ -37,8 +37,10 @@ class Controlled:
 
 def solve_error_controlled(problem: sg.Problem, x0: torch.Tensor, T: torch.Tensor, tol: float,
                            h0: float = 5.0 / 32.0, max_doublings: int = 5, precision: int = sg.PREC_FP64,
-                           newton_tol: float = 1e-12, max_iter: int = 100) -> Controlled:
-    """Solves every node to an estimated error of V and lambda(0) below `tol`."""
+                           newton_tol: float = 1e-12, max_iter: int = 100,
+                           target: torch.Tensor | None = None) -> Controlled:
+    """Solves every node to an estimated error of V and lambda(0) below `tol`.
+    target: per-node target attitudes (n, 3) for the attitude family, or None."""
     x0 = x0.to(torch.float64).contiguous()
     T = T.to(torch.float64).contiguous()
     n = x0.shape[0]
@@ -48,7 +50,9 @@ def solve_error_controlled(problem: sg.Problem, x0: torch.Tensor, T: torch.Tenso
 
     def solve(idx, Nsub):
         Nd = torch.as_tensor(Nsub.astype(np.int32), device=dev)
-        return sg.solve_bvps(problem, x0[idx].contiguous(), T[idx].contiguous(), Nd, tol=newton_tol,
+        tg = target[idx].contiguous() if target is not None else None
+        prob = surfaces._with_target(problem, tg) if target is not None else problem
+        return sg.solve_bvps(prob, x0[idx].contiguous(), T[idx].contiguous(), Nd, tol=newton_tol,
                              max_iter=max_iter, precision=precision, n_max=int(Nsub.max()))
 
     out = {"lambda0": torch.full((n, 6), float("nan"), dtype=torch.float64, device=dev),
@@ -96,8 +100,11 @@ class Validation:
 
     def stats(self, col: int = 0) -> dict:
         e = self.interp[self.ok, col] - self.reference[self.ok, col]
+        ref = np.abs(self.reference[self.ok, col])
+        rel = np.abs(e) / np.where(ref > 0, ref, np.inf)
         return {"points": int(self.ok.sum()), "mae": float(np.abs(e).mean()), "max": float(np.abs(e).max()),
-                "var": float(np.var(e)), "reference_err_est_max": float(self.err_est[self.ok].max())}
+                "var": float(np.var(e)), "relative_mae": float(rel.mean()),
+                "reference_err_est_max": float(self.err_est[self.ok].max())}
 
 
 def validate_feedback(problem: sg.Problem, surplus: sg.Surplus, points: torch.Tensor, T: float, tol: float,
@@ -109,4 +116,18 @@ def validate_feedback(problem: sg.Problem, surplus: sg.Surplus, points: torch.Te
     ref = solve_error_controlled(problem, pts, Tq, tol, **kw)
     interp = sg.eval_feedback(surplus, pts, mode=mode).cpu().numpy()
     return Validation(points=pts.cpu().numpy(), interp=interp, reference=ref.u0.cpu().numpy()[:, :interp.shape[1]],
+                      err_est=ref.err_est, ok=ref.ok)
+
+
+def validate_value(problem: sg.Problem, surplus: sg.Surplus, points: torch.Tensor, T: float, tol: float,
+                   value_col: int, mode: int = sg.EVAL_DF32, target: torch.Tensor | None = None,
+                   **kw) -> Validation:
+    """Section 4.1 for the value function: I^q(V)(x) (output `value_col` of the
+    surplus handle) against V(x) from error-controlled solves at the points
+    (state space, horizon T; per-point target attitudes for Example II)."""
+    pts = points.to(torch.float64).contiguous()
+    Tq = torch.full((pts.shape[0],), float(T), dtype=torch.float64, device=pts.device)
+    ref = solve_error_controlled(problem, pts, Tq, tol, target=target, **kw)
+    interp = sg.eval_feedback(surplus, pts, mode=mode).cpu().numpy()[:, value_col:value_col + 1]
+    return Validation(points=pts.cpu().numpy(), interp=interp, reference=ref.V.cpu().numpy()[:, None],
                       err_est=ref.err_est, ok=ref.ok)

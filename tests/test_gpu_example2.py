@@ -89,3 +89,25 @@ def test_printed_trajectory_on_gpu():
         y = sum(np.prod([(tau - c[j]) / (c[k] - c[j]) for j in range(4) if j != k]) * Y[3 * i + k] for k in range(4))
         u = -B.T @ (y[9:12] / np.asarray(PRM.J)) / PRM.r
         assert np.abs(np.concatenate([y[:6], u]) - ref).max() < 1e-6, t
+
+
+def test_two_wheel_surface_and_value_validation():
+    """Level 3 of Example II: every node gets a target and converges, the
+    interpolant reproduces the solved values at the nodes, and the pointwise
+    validation of V runs against error-controlled solves with their own
+    target attitudes."""
+    sg = _sg()
+    from paper_1507_04769_gb300 import surfaces, validation
+    lo, hi = synth.example2_box()
+    srf = surfaces.two_wheel_surface(PRM, 3, lo, hi, synth.EXAMPLE2_T)
+    vals = torch.stack([srf.result["u0"][:, 0], srf.result["u0"][:, 1], srf.result["V"]], dim=1)
+    at_nodes = srf.evaluate(srf.grid.coords)
+    assert float((at_nodes - vals).abs().max()) <= 1e-10 * max(1.0, float(vals.abs().max()))
+    pts = torch.as_tensor(_states(32, 43), device="cuda")
+    tgt, st = sg.attitude_targets(sg.problem_from(PRM), pts)
+    assert bool((st == 0).all())
+    val = validation.validate_value(sg.problem_from(PRM), srf.surplus, pts, synth.EXAMPLE2_T, 1e-9,
+                                    value_col=2, target=tgt)
+    s = val.stats(0)
+    assert s["points"] == 32 and s["reference_err_est_max"] <= 1e-9
+    assert 0.0 < s["relative_mae"] < 1.0
