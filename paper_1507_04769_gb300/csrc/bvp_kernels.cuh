@@ -1113,12 +1113,16 @@ __device__ __forceinline__ void recover_interval(const SolveArgs& a, const Works
   double* D = w.D + (node * npts(a.Nmax) + 3 * int64_t(i)) * 12;
   const T dyl = lane < 12 ? T(D[lane]) : T(0);
   const T dyr = lane < 12 ? T(D[36 + lane]) : T(0);
+  // the part of row k left of its diagonal is never read (and never stored)
   T row[kRecLd];
+#pragma unroll
+  for (int c = 0; c < kRecLd; ++c) row[c] = T(0);
   if (lane < 24) {
     if constexpr (sizeof(T) == 4) {
       const float4* s4 = reinterpret_cast<const float4*>(rec + lane * kRecLd);
 #pragma unroll
       for (int q = 0; q < kRecLd / 4; ++q) {
+        if (4 * q + 3 < lane) continue;
         const float4 v = s4[q];
         row[4 * q] = v.x; row[4 * q + 1] = v.y; row[4 * q + 2] = v.z; row[4 * q + 3] = v.w;
       }
@@ -1126,13 +1130,11 @@ __device__ __forceinline__ void recover_interval(const SolveArgs& a, const Works
       const double2* s2 = reinterpret_cast<const double2*>(rec + lane * kRecLd);
 #pragma unroll
       for (int q = 0; q < kRecLd / 2; ++q) {
+        if (2 * q + 1 < lane) continue;
         const double2 v = s2[q];
         row[2 * q] = v.x; row[2 * q + 1] = v.y;
       }
     }
-  } else {
-#pragma unroll
-    for (int c = 0; c < kRecLd; ++c) row[c] = T(0);
   }
   T acc = row[48];
 #pragma unroll

@@ -22,7 +22,7 @@ namespace sg {
 constexpr int kFoldBlock = 64;     // nodes per FP64 fold of the compensated sums (per thread)
 constexpr int kDfWarps = 4;        // warps per block
 constexpr int kDfThreads = 32 * kDfWarps;
-constexpr int kDfChunk = 128;      // nodes staged in shared memory at a time
+constexpr int kDfChunk = 256;      // nodes staged in shared memory at a time
 
 // Product of a pair with a pair, left unnormalised: the result (p, e) has
 // p = fl(a.hi b.hi) and e = the exact rounding error of p plus the cross
