@@ -513,36 +513,30 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
   // interior part to act[24], passive part to P_s[r]
   auto build = [&](int r, float (&act)[24]) {
     const int k = r / 12 + 1, comp = r % 12;
-    float v[48];
+    float4* dst = reinterpret_cast<float4*>(P_s + r * kCondLd);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float cf = -hf * kLobAf[k][j];
       const float4* src = reinterpret_cast<const float4*>(J + j * 144 + comp * 12);
-      const int c0 = j == 0 ? 24 : (j == 3 ? 36 : 12 * (j - 1));
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const float4 x = src[q];
-        v[c0 + 4 * q + 0] = cf * x.x;
-        v[c0 + 4 * q + 1] = cf * x.y;
-        v[c0 + 4 * q + 2] = cf * x.z;
-        v[c0 + 4 * q + 3] = cf * x.w;
+        float v[4] = {cf * x.x, cf * x.y, cf * x.z, cf * x.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const bool diag = 4 * q + t == comp;
+          if (j == 0) v[t] -= diag ? 1.0f : 0.0f;          // -I on y_i
+          if (j == k && k < 3) v[t] += diag ? 1.0f : 0.0f;  // +I on the stage's own point
+          if (j == 3 && k == 3) v[t] += diag ? 1.0f : 0.0f;
+        }
+        if (j == 1 || j == 2) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) act[12 * (j - 1) + 4 * q + t] = v[t];
+        } else {
+          dst[(j == 0 ? 0 : 3) + q] = make_float4(v[0], v[1], v[2], v[3]);
+        }
       }
     }
-    // +I on the stage's own point, -I on y_i
-#pragma unroll
-    for (int t = 0; t < 12; ++t) {
-      if (t == comp) {
-        if (k == 1) v[t] += 1.0f;
-        if (k == 2) v[12 + t] += 1.0f;
-        if (k == 3) v[36 + t] += 1.0f;
-        v[24 + t] -= 1.0f;
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 24; ++c) act[c] = v[c];
-    float4* dst = reinterpret_cast<float4*>(P_s + r * kCondLd);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) dst[q] = make_float4(v[24 + 4 * q], v[25 + 4 * q], v[26 + 4 * q], v[27 + 4 * q]);
     P_s[r * kCondLd + 24] = -res[r];
   };
 
@@ -602,10 +596,18 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
         }
       }
     }
-    L_s[lane * kCondLd + k] = la;
+    // column k is done: row `lane` keeps its multiplier there (rows 32..35
+    // store theirs at once)
+    ra[k] = la;
     if (hasb) L_s[(8 + lane) * kCondLd + k] = lb;
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) w.ns[node].singular = 1;
+  // multipliers to L (a pivot row's entries from its own step on are never read)
+  {
+    float4* d4 = reinterpret_cast<float4*>(L_s + lane * kCondLd);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) d4[q] = make_float4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
+  }
   __syncwarp();
 
   // ---- phase B: passive columns
