@@ -540,14 +540,29 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     P_s[r * kCondLd + 24] = -res[r];
   };
 
-  const bool hasb = lane >= 24 && lane < 28;
-  float ra[24], rb[24];
+  float ra[24];
   build(lane, ra);
-  if (hasb) {
-    build(8 + lane, rb);   // rows 32..35
-  } else {
+  // rows 32..35 (stage 4, components 8..11) are spread over the warp: lane
+  // group g = lane / 8 holds row 32 + g, lane sub = lane % 8 holds columns
+  // sub, sub + 8 and sub + 16 of its interior part and of its passive part
+  const int g = lane >> 3, sub = lane & 7;
+  const int r2 = 32 + g, comp2 = 8 + g;
+  float rb[3];
+  {
+    const float cf0 = -hf * kLobAf[3][0], cf1 = -hf * kLobAf[3][1];
+    const float cf2 = -hf * kLobAf[3][2], cf3 = -hf * kLobAf[3][3];
 #pragma unroll
-    for (int c = 0; c < 24; ++c) rb[c] = 0.0f;
+    for (int m = 0; m < 3; ++m) {
+      const int c = sub + 8 * m;
+      const int j = c < 12 ? 1 : 2;                 // interior column c: point j, component c % 12
+      rb[m] = (j == 1 ? cf1 : cf2) * J[j * 144 + comp2 * 12 + (c < 12 ? c : c - 12)];
+      // passive column c: y_i (point 0) below 12, y_{i+1} (point 3) from 12
+      float pv = c < 12 ? cf0 * J[comp2 * 12 + c] : cf3 * J[3 * 144 + comp2 * 12 + c - 12];
+      if (c == comp2) pv -= 1.0f;
+      if (c - 12 == comp2) pv += 1.0f;
+      P_s[r2 * kCondLd + c] = pv;
+    }
+    if (sub == 0) P_s[r2 * kCondLd + 24] = -res[r2];
   }
 
   // ---- phase A: interior columns
@@ -582,7 +597,6 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     const float4* src = reinterpret_cast<const float4*>(U_s + k * kCondLd);
     const float inv = src[6].x;
     const float la = ra[k] * (inv * live);
-    const float lb = hasb ? rb[k] * inv : 0.0f;
 #pragma unroll
     for (int q = q0; q < 6; ++q) {
       const float4 u4 = src[q];
@@ -590,16 +604,21 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int c = 4 * q + t;
-        if (c > k) {
-          ra[c] = fmaf(-la, u[t], ra[c]);
-          rb[c] = fmaf(-lb, u[t], rb[c]);
-        }
+        if (c > k) ra[c] = fmaf(-la, u[t], ra[c]);
       }
     }
-    // column k is done: row `lane` keeps its multiplier there (rows 32..35
-    // store theirs at once)
+    // column k is done: row `lane` keeps its multiplier there
     ra[k] = la;
-    if (hasb) L_s[(8 + lane) * kCondLd + k] = lb;
+    // rows 32..35: column k sits on lane k % 8 of each group, register k / 8
+    const float lb = __shfl_sync(0xffffffffu, rb[k >> 3], k & 7, 8) * inv;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      if (8 * m + 7 > k) {
+        const int c = sub + 8 * m;
+        if (c > k) rb[m] = fmaf(-lb, U_s[k * kCondLd + c], rb[m]);
+      }
+    }
+    if (sub == 0) L_s[r2 * kCondLd + k] = lb;
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) w.ns[node].singular = 1;
   // multipliers to L (a pivot row's entries from its own step on are never read)
