@@ -495,7 +495,7 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
 // Rows never move.  The stored recovery rows are [U_k | Q_k] in pivot order
 // (raw pivot on the diagonal), the condensed block row is [S | T | rhs].
 constexpr int kCondLd = 28;                          // row stride of P, L and U (floats)
-constexpr int kCondSmemFloats = 36 * kCondLd * 2 + 24 * kCondLd + 32;   // P, L, U, pivot order
+constexpr int kCondSmemFloats = 36 * kCondLd * 2 + 8 * kCondLd + 32;    // P, L, U (ring of 8 rows), pivot order
 
 __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const Workspace& w, int64_t node,
                                                       int i, int N, int lane, float* __restrict__ sm) {
@@ -506,14 +506,18 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
   const float* res = static_cast<const float*>(w.Res) + wid * kResRows;
   float* P_s = sm;                         // [36][kCondLd] passive columns, original
   float* L_s = sm + 36 * kCondLd;          // [36][kCondLd] multipliers l(r, k)
-  float* U_s = sm + 72 * kCondLd;          // [24][kCondLd] pivot rows (interior part), 1/pivot at 24
-  int* perm_s = reinterpret_cast<int*>(sm + 96 * kCondLd);   // [24] pivot row of step k
+  float* U_s = sm + 72 * kCondLd;          // [8][kCondLd] pivot row of step k at k % 8, 1/pivot at 24
+  int* perm_s = reinterpret_cast<int*>(sm + 80 * kCondLd);   // [24] pivot row of step k
+  const int64_t blk = node * a.Nmax + i;
+  float* rec = static_cast<float*>(w.Rec) + blk * kRec;
 
   // row r = 12 (k - 1) + comp for stage k = 1, 2, 3 (Lobatto stages 2, 3, 4):
-  // interior part to act[24], passive part to P_s[r]
+  // passive part to P_s[r], interior part through L_s[r] (free until the end
+  // of phase A) to act[24]; the identity terms are added in shared memory
   auto build = [&](int r, float (&act)[24]) {
     const int k = r / 12 + 1, comp = r % 12;
-    float4* dst = reinterpret_cast<float4*>(P_s + r * kCondLd);
+    float4* dP = reinterpret_cast<float4*>(P_s + r * kCondLd);
+    float4* dA = reinterpret_cast<float4*>(L_s + r * kCondLd);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float cf = -hf * kLobAf[k][j];
@@ -521,23 +525,22 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const float4 x = src[q];
-        float v[4] = {cf * x.x, cf * x.y, cf * x.z, cf * x.w};
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const bool diag = 4 * q + t == comp;
-          if (j == 0) v[t] -= diag ? 1.0f : 0.0f;          // -I on y_i
-          if (j == k && k < 3) v[t] += diag ? 1.0f : 0.0f;  // +I on the stage's own point
-          if (j == 3 && k == 3) v[t] += diag ? 1.0f : 0.0f;
-        }
-        if (j == 1 || j == 2) {
-#pragma unroll
-          for (int t = 0; t < 4; ++t) act[12 * (j - 1) + 4 * q + t] = v[t];
-        } else {
-          dst[(j == 0 ? 0 : 3) + q] = make_float4(v[0], v[1], v[2], v[3]);
-        }
+        const float4 v = make_float4(cf * x.x, cf * x.y, cf * x.z, cf * x.w);
+        if (j == 0) dP[q] = v;            // y_i
+        if (j == 1) dA[q] = v;            // stage 2
+        if (j == 2) dA[3 + q] = v;        // stage 3
+        if (j == 3) dP[3 + q] = v;        // y_{i+1}
       }
     }
     P_s[r * kCondLd + 24] = -res[r];
+    P_s[r * kCondLd + comp] -= 1.0f;                     // -I on y_i
+    if (k == 3) P_s[r * kCondLd + 12 + comp] += 1.0f;    // +I on the stage's own point
+    else L_s[r * kCondLd + r] += 1.0f;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const float4 v = dA[q];
+      act[4 * q] = v.x; act[4 * q + 1] = v.y; act[4 * q + 2] = v.z; act[4 * q + 3] = v.w;
+    }
   };
 
   float ra[24];
@@ -584,7 +587,7 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
       const float pv = ra[k];
       const float inv = (pv != 0.0f && isfinite(pv)) ? __frcp_rn(pv) : 0.0f;
       bad = inv == 0.0f;
-      float4* dst = reinterpret_cast<float4*>(U_s + k * kCondLd);
+      float4* dst = reinterpret_cast<float4*>(U_s + (k & 7) * kCondLd);
 #pragma unroll
       for (int q = q0; q < 6; ++q) dst[q] = make_float4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
       dst[6] = make_float4(inv, 0.0f, 0.0f, 0.0f);
@@ -594,7 +597,7 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
       live = 0.0f;
     }
     __syncwarp();
-    const float4* src = reinterpret_cast<const float4*>(U_s + k * kCondLd);
+    const float4* src = reinterpret_cast<const float4*>(U_s + (k & 7) * kCondLd);
     const float inv = src[6].x;
     const float la = ra[k] * (inv * live);
 #pragma unroll
@@ -615,10 +618,22 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     for (int m = 0; m < 3; ++m) {
       if (8 * m + 7 > k) {
         const int c = sub + 8 * m;
-        if (c > k) rb[m] = fmaf(-lb, U_s[k * kCondLd + c], rb[m]);
+        if (c > k) rb[m] = fmaf(-lb, U_s[(k & 7) * kCondLd + c], rb[m]);
       }
     }
     if (sub == 0) L_s[r2 * kCondLd + k] = lb;
+    if ((k & 7) == 7) {
+      // the ring is full: rows k - 7 .. k to the recovery rows (at and right
+      // of the diagonal chunk) with 1/pivot
+      const int k0 = k - 7;
+      for (int e = lane; e < 48; e += 32) {
+        const int kk = k0 + e / 6, q = e % 6;
+        if (q >= kk / 4)
+          reinterpret_cast<float4*>(rec + kk * kRecLd)[q] = reinterpret_cast<const float4*>(U_s + (kk & 7) * kCondLd)[q];
+      }
+      if (lane < 8) rec[(k0 + lane) * kRecLd + kRecInv] = U_s[lane * kCondLd + 24];
+      __syncwarp();
+    }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) w.ns[node].singular = 1;
   // multipliers to L (a pivot row's entries from its own step on are never read)
@@ -630,8 +645,6 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
   __syncwarp();
 
   // ---- phase B: passive columns
-  const int64_t blk = node * a.Nmax + i;
-  float* rec = static_cast<float*>(w.Rec) + blk * kRec;
   float* cond = static_cast<float*>(w.Cond) + blk * kBlk;
   const bool col = lane < 25;
   const int cl = col ? lane : 0;
@@ -672,20 +685,12 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     }
     if (col) cond[(r - 24) * kBlkLd + lane] = f;
   }
-  // interior part of the recovery rows: U_k (at and right of the diagonal)
-  // and 1/pivot
-  for (int e = lane; e < 24 * 6; e += 32) {
-    const int k = e / 6, q = e % 6;
-    if (q >= k / 4)
-      reinterpret_cast<float4*>(rec + k * kRecLd)[q] = reinterpret_cast<const float4*>(U_s + k * kCondLd)[q];
-  }
-  if (lane < 24) rec[lane * kRecLd + kRecInv] = U_s[lane * kCondLd + 24];
   __syncwarp();   // the tables are reused by the warp's next interval
 }
 
 constexpr int kCondRegWarps = 4;
 
-__global__ void __launch_bounds__(32 * kCondRegWarps, 5) k_condense_reg(SolveArgs a, Workspace w) {
+__global__ void __launch_bounds__(32 * kCondRegWarps, 6) k_condense_reg(SolveArgs a, Workspace w) {
   __shared__ __align__(16) float sm[kCondRegWarps][kCondSmemFloats];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
