@@ -176,6 +176,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
   const unsigned gwarp_int = static_cast<unsigned>(ceil_div(nint, 4));
   const unsigned gwarp_node = static_cast<unsigned>(ceil_div(a.n, 4));
   const unsigned gwarp_seg = static_cast<unsigned>(ceil_div(a.n * seg_count(a.Nmax), 4));
+  const unsigned gseg_blk = static_cast<unsigned>(ceil_div(a.n * seg_count(a.Nmax), seg_warps<T>()));
   const size_t cond_smem = sizeof(double) * kCondWarps * 36 * kCols;
   if constexpr (sizeof(T) == sizeof(double)) {
     SG_CUDA_TRY(cudaFuncSetAttribute(k_condense_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -228,7 +229,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
                (k_condense_smem<<<static_cast<unsigned>(ceil_div(nint, kCondWarps)), 32 * kCondWarps, cond_smem,
                                   st>>>(a, w)));
     }
-    SG_TIMED(kname<T>("k_abd_seg"), st, (k_abd_seg<T><<<gwarp_seg, 128, 0, st>>>(a, w)));
+    SG_TIMED(kname<T>("k_abd_seg"), st, (k_abd_seg<T><<<gseg_blk, 32 * seg_warps<T>(), 0, st>>>(a, w)));
     SG_TIMED(kname<T>("k_abd_red"), st, (k_abd_red<T><<<gwarp_node, 128, 0, st>>>(a, w)));
     SG_TIMED(kname<T>("k_abd_segback"), st, (k_abd_segback<T><<<gwarp_seg, 128, 0, st>>>(a, w)));
     SG_TIMED(kname<T>("k_recover"), st, (k_recover<T><<<gwarp_int, 128, 0, st>>>(a, w)));
@@ -360,7 +361,8 @@ static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, dou
   } else {
     nb.kernel(k_condense_smem, static_cast<unsigned>(ceil_div(nint, kCondWarps)), 32 * kCondWarps, cond_smem, a, w);
   }
-  nb.kernel(k_abd_seg<T>, gws, 128, 0, a, w);
+  nb.kernel(k_abd_seg<T>, static_cast<unsigned>(ceil_div(a.n * seg_count(a.Nmax), seg_warps<T>())),
+            32 * seg_warps<T>(), 0, a, w);
   nb.kernel(k_abd_red<T>, gwn, 128, 0, a, w);
   nb.kernel(k_abd_segback<T>, gws, 128, 0, a, w);
   nb.kernel(k_recover<T>, gwi, 128, 0, a, w);

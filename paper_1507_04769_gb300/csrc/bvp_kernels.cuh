@@ -938,13 +938,95 @@ __device__ __forceinline__ bool abd_node_reg(const SolveArgs& a, const Workspace
 // rows of a segment, the structured pairwise reduction of block rows of
 // Wright (SIAM J. Sci. Stat. Comput. 13, 1992) taken sequentially inside a
 // segment; the chain becomes kSegLen + N / kSegLen panels.
+//
+// Each panel runs in two phases, like the condensation:
+//   phase A (rows on lanes): lane r < 24 holds the 12 y_i entries of panel
+//   row r in registers.  Partial pivoting over the 24 rows; at step k the
+//   pivot lane writes its row (1/pivot on the diagonal) to the table U and
+//   every row keeps its multiplier l(r, k) in the eliminated column, stored
+//   to L at the end.
+//   phase B (columns on lanes): lane c < 25 owns passive column c of
+//   [F | Z | rhs].  With the pivot order p_k the passive part of pivot row k
+//   is Q_k = P(p_k) - sum_{j<k} l(p_k, j) Q_j, and a carry row r leaves as
+//   P(r) - sum_k l(r, k) Q_k.
+// The panel rows live in shared memory between panels: their passive parts
+// in P and their y_i parts in Y.  Carry rows move Z into Y; the slots of the
+// pivot rows take block row i + 1.
 template <typename T>
-__global__ void __launch_bounds__(128) k_abd_seg(SolveArgs a, Workspace w) {
-  constexpr int kStage = 12 * kBlkLd;
-  __shared__ __align__(16) T sm[4][2 * kSegLd + kStage];
+__host__ __device__ constexpr int seg_warps() { return sizeof(T) == 4 ? 4 : 2; }   // warps per block
+constexpr int kSegP = 25;   // row stride of the passive table P
+// P, Y, L, U and the staged block row (elements), then 32 ints (pivot slots, carry slots)
+constexpr int kSegSmem = 24 * kSegP + 24 * 12 + 24 * 12 + 12 * 12 + 12 * kBlkLd;
+template <typename T>
+__host__ __device__ constexpr int seg_smem_elems() { return kSegSmem + 32 * 4 / int(sizeof(T)); }
+
+template <typename T>
+__device__ __forceinline__ void load_row12(const T* __restrict__ src, T (&r)[12]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 v = s4[q];
+      r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+    }
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const double2 v = s2[q];
+      r[2 * q] = v.x; r[2 * q + 1] = v.y;
+    }
+  }
+}
+
+// 16-byte vectors q < nq of a 12-entry row (the rest left unset)
+template <typename T>
+__device__ __forceinline__ void load_row12_upto(const T* __restrict__ src, T (&r)[12], int nq) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (q < nq) {
+        const float4 v = s4[q];
+        r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+      }
+    }
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      if (q < nq) {
+        const double2 v = s2[q];
+        r[2 * q] = v.x; r[2 * q + 1] = v.y;
+      }
+    }
+  }
+}
+
+// 16-byte vectors q >= q0 of a 12-entry row
+template <typename T>
+__device__ __forceinline__ void store_row12_from(T* __restrict__ dst, const T (&r)[12], int q0) {
+  if constexpr (sizeof(T) == 4) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (q >= q0) d4[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+  } else {
+    double2* d2 = reinterpret_cast<double2*>(dst);
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      if (q >= q0) d2[q] = make_double2(r[2 * q], r[2 * q + 1]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * seg_warps<T>()) k_abd_seg(SolveArgs a, Workspace w) {
+  constexpr int W = seg_warps<T>();
+  constexpr int V = 16 / int(sizeof(T));   // entries per 16-byte vector
+  __shared__ __align__(16) T sm[W][seg_smem_elems<T>()];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int smax = seg_count(a.Nmax);
-  const int64_t wid = blockIdx.x * int64_t(4) + warp;
+  const int64_t wid = blockIdx.x * int64_t(W) + warp;
   const int64_t node = wid / smax;
   const int s = static_cast<int>(wid % smax);
   if (node >= a.n) return;
@@ -953,109 +1035,166 @@ __global__ void __launch_bounds__(128) k_abd_seg(SolveArgs a, Workspace w) {
   if (s >= seg_count(N)) return;
   const int i0 = s * kSegLen;
   const int i1 = i0 + kSegLen < N ? i0 + kSegLen : N;
-  T* pivbuf = sm[warp];
-  T* stage = sm[warp] + 2 * kSegLd;
+  T* P_s = sm[warp];                  // [24][kSegP] passive parts [F | Z | rhs] of the panel rows
+  T* Y_s = P_s + 24 * kSegP;          // [24][12] y_i parts
+  T* L_s = Y_s + 24 * 12;             // [24][12] multipliers l(r, k)
+  T* U_s = L_s + 24 * 12;             // [12][12] pivot rows (y_i part), 1/pivot on the diagonal
+  T* stage = U_s + 12 * 12;           // [12][kBlkLd] block row i + 1
+  int* perm_s = reinterpret_cast<int*>(stage + 12 * kBlkLd);   // [12] slot of the pivot row of step k
+  int* cslot_s = perm_s + 16;                                   // [12] carry slots in lane order
   const T* cond = static_cast<const T*>(w.Cond) + node * a.Nmax * int64_t(kBlk);
   T* seg = static_cast<T*>(w.Seg) + node * a.Nmax * int64_t(kSegBlk);
+  T* red = static_cast<T*>(w.Red) + (node * smax + s) * int64_t(kBlk);
   const unsigned lt_mask = (1u << lane) - 1u;
+  const bool col = lane < 25;               // phase B: passive column c = F (0..11), Z (12..23), rhs (24)
+  const int c = col ? lane : 0;
+  const int segc = c < 12 ? c : c + 12;     // its column in a stored pivot row [F | U | V | rhs]
 
-  // r = [F (y_a) 0..11 | Y (y_i) 12..23 | Z (y_{i+1}) 24..35 | rhs 36]
-  T r[37];
-#pragma unroll
-  for (int c = 0; c < 37; ++c) r[c] = T(0);
-  {
-    T row[25];
-    if (lane < 12) {   // carry = block row i0 on (y_a, y_{a+1})
-      load_row25<T>(cond + int64_t(i0) * kBlk + lane * kBlkLd, row);
-#pragma unroll
-      for (int c = 0; c < 24; ++c) r[c] = row[c];
-      r[36] = row[24];
-    } else if (lane < 24 && i0 + 1 < i1) {   // block row i0 + 1 on (y_{a+1}, y_{a+2})
-      load_row25<T>(cond + int64_t(i0 + 1) * kBlk + (lane - 12) * kBlkLd, row);
-#pragma unroll
-      for (int c = 0; c < 24; ++c) r[12 + c] = row[c];
-      r[36] = row[24];
+  const T* b0 = cond + int64_t(i0) * kBlk;
+  if (i0 + 1 >= i1) {   // a one-interval segment: its block row is the reduced row
+    for (int e = lane; e < kBlk; e += 32) red[e] = b0[e];
+    return;
+  }
+  // panel rows: slots 0..11 = block row i0 = [F = S | Y = T | Z = 0 | r],
+  // slots 12..23 = block row i0 + 1 = [F = 0 | Y = S | Z = T | r]
+  const T* b1 = b0 + kBlk;
+  if (col) {
+#pragma unroll 4
+    for (int r = 0; r < 12; ++r) {
+      P_s[r * kSegP + c] = c < 12 ? b0[r * kBlkLd + c] : (c < 24 ? T(0) : b0[r * kBlkLd + 24]);
+      P_s[(12 + r) * kSegP + c] = c < 12 ? T(0) : b1[r * kBlkLd + c];
     }
   }
-  const bool cand = lane < 24;
+  if (lane < 24) {
+    T y[12];
+    load_row12<T>(lane < 12 ? b0 + lane * kBlkLd + 12 : b1 + (lane - 12) * kBlkLd, y);
+    store_row12_from<T>(Y_s + lane * 12, y, 0);
+  }
+  __syncwarp();
+
   const unsigned itag = 31u - unsigned(lane);
-  bool carry = lane < 12;
   bool bad = false;
   for (int i = i0 + 1; i < i1; ++i) {
-    if (i + 1 < i1) {   // stage block row i + 1 for the lanes that become free (asynchronous copy)
+    const bool more = i + 1 < i1;
+    if (more) {   // block row i + 1 to the stage (asynchronous copy)
       const char* src = reinterpret_cast<const char*>(cond + int64_t(i + 1) * kBlk);
-      for (int e = lane; e < kStage * int(sizeof(T)) / 16; e += 32)
+      for (int e = lane; e < 12 * kBlkLd * int(sizeof(T)) / 16; e += 32)
         cp_async16(reinterpret_cast<char*>(stage) + 16 * e, src + 16 * e);
       cp_async_commit();
     }
-    // candidates: the 24 panel rows; mask and tag as in the condensation
-    unsigned kmask = cand ? ~31u : 0u;
-    unsigned ktag = cand ? itag : 0u;
-    T live = cand ? T(1) : T(0);
-    int my_step = -1;
+    // ---- phase A
+    T ya[12];
+    if (lane < 24) {
+      load_row12<T>(Y_s + lane * 12, ya);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 12; ++t) ya[t] = T(0);
+    }
+    // pivot key: magnitude with the low 5 bits replaced by a lane tag (ties
+    // to the lower lane); rows that are no candidates have zero mask and tag
+    unsigned kmask = lane < 24 ? ~31u : 0u;
+    unsigned ktag = lane < 24 ? itag : 0u;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      const unsigned key = (mag_key(r[12 + k]) & kmask) | ktag;
+      const int q0 = k / V;
+      const unsigned key = (mag_key(ya[k]) & kmask) | ktag;
       const unsigned best = __reduce_max_sync(0xffffffffu, key);
-      const bool is_p = (best & 31u) == itag && ktag != 0u;
-      T* pb = pivbuf + (k & 1) * kSegLd;
-      if (is_p) {
-        store_row40<T>(pb, r);
-        my_step = k;
+      if ((best & 31u) == itag && ktag != 0u) {
+        const T piv = ya[k];
+        const bool good = piv != T(0) && isfinite(piv);
+        bad = bad || !good;
+        ya[k] = good ? recip_rn(piv) : T(0);
+        store_row12_from<T>(U_s + k * 12, ya, q0);
+        perm_s[k] = lane;
         kmask = 0u;
         ktag = 0u;
-        live = T(0);
       }
       __syncwarp();
-      T prow[40];
-      load_row40<T>(pb, prow);
-      const T piv = prow[12 + k];
-      const bool good = piv != T(0) && isfinite(piv);
-      bad = bad || !good;
-      const T inv = good ? recip_rn(piv) : T(0);
-      const T la = r[12 + k] * (inv * live);
+      const T* u = U_s + k * 12;
+      const T la = ktag != 0u ? ya[k] * u[k] : T(0);
 #pragma unroll
-      for (int c = 0; c < 37; ++c)
-        if (c < 12 || c > 12 + k) r[c] = fma(-la, prow[c], r[c]);
-      if (is_p) r[12 + k] = inv;
-    }
-    const bool done = my_step >= 0;
-    if (done) store_row40<T>(seg + (int64_t(i) * 12 + my_step) * kSegLd, r);
-    cp_async_wait_all();   // this lane's part of the stage has landed
-    __syncwarp();          // ... and every lane's
-    // next panel: the carry rows move y_{i+1} into the y_i slot; the pivot
-    // lanes take block row i + 1 from the stage, in lane order
-    const int rank = __popc(__ballot_sync(0xffffffffu, done) & lt_mask);
-    carry = cand && !done;
-    if (carry) {
+      for (int q = q0; q < 12 / V; ++q) {
+        T uv[V];
+        if constexpr (sizeof(T) == 4) {
+          const float4 v4 = reinterpret_cast<const float4*>(u)[q];
+          uv[0] = v4.x; uv[1] = v4.y; uv[2] = v4.z; uv[3] = v4.w;
+        } else {
+          const double2 v2 = reinterpret_cast<const double2*>(u)[q];
+          uv[0] = v2.x; uv[1] = v2.y;
+        }
 #pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        r[12 + c] = r[24 + c];
-        r[24 + c] = T(0);
+        for (int t = 0; t < V; ++t) {
+          const int cc = V * q + t;
+          if (cc > k) ya[cc] = fma(-la, uv[t], ya[cc]);
+        }
       }
-    } else if (done && i + 1 < i1) {
-      const T* src = stage + rank * kBlkLd;
-#pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        r[c] = T(0);
-        r[12 + c] = src[c];
-        r[24 + c] = src[12 + c];
-      }
-      r[36] = src[24];
+      ya[k] = la;   // column k is done: the row keeps its multiplier there
     }
-    __syncwarp();   // stage and pivot buffer reads done before the next panel writes
+    if (lane < 24) store_row12_from<T>(L_s + lane * 12, ya, 0);   // a pivot row's entries from its step on are never read
+    const unsigned cmask = __ballot_sync(0xffffffffu, ktag != 0u);   // the 12 rows that were no pivot
+    if (ktag != 0u) cslot_s[__popc(cmask & lt_mask)] = lane;
+    __syncwarp();
+
+    // ---- phase B
+    T* segp = seg + int64_t(i) * 12 * kSegLd;
+    T Q[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const int pk = perm_s[k];
+      T x = P_s[pk * kSegP + c], y = T(0);
+      T l[12];
+      load_row12_upto<T>(L_s + pk * 12, l, (k + V - 1) / V);
+#pragma unroll
+      for (int j = 0; j < k; ++j) {
+        if (j & 1) y = fma(-l[j], Q[j], y);
+        else x = fma(-l[j], Q[j], x);
+      }
+      x += y;
+      Q[k] = x;
+      if (col) segp[k * kSegLd + segc] = x;
+    }
+    // y_i part of the pivot rows (1/pivot on the diagonal; left of it unread)
+    for (int e = lane; e < 12 * (12 / V); e += 32) {
+      const int k = e / (12 / V), q = e % (12 / V);
+      if (q >= k / V)
+        reinterpret_cast<float4*>(segp + k * kSegLd + 12)[q] = reinterpret_cast<const float4*>(U_s + k * 12)[q];
+    }
+#pragma unroll 3
+    for (int m = 0; m < 12; ++m) {
+      const int r = cslot_s[m];
+      T f = P_s[r * kSegP + c], g = T(0);
+      T l[12];
+      load_row12<T>(L_s + r * 12, l);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        if (k & 1) g = fma(-l[k], Q[k], g);
+        else f = fma(-l[k], Q[k], f);
+      }
+      f += g;
+      if (col) {
+        if (!more) {
+          red[m * kBlkLd + c] = f;   // last panel: the carry rows are the reduced row [F | Y | rhs]
+        } else if (c >= 12 && c < 24) {
+          Y_s[r * 12 + c - 12] = f;   // Z moves into the y_i slot
+          P_s[r * kSegP + c] = T(0);
+        } else {
+          P_s[r * kSegP + c] = f;
+        }
+      }
+    }
+    if (more) {   // the pivot slots take block row i + 1 = [0 | S | T | r]
+      cp_async_wait_all();   // this lane's part of the stage has landed
+      __syncwarp();          // ... and every lane's
+#pragma unroll 4
+      for (int k = 0; k < 12; ++k) {
+        const int slot = perm_s[k];
+        if (col) P_s[slot * kSegP + c] = c < 12 ? T(0) : stage[k * kBlkLd + c];
+        if (lane < 12) Y_s[slot * 12 + lane] = stage[k * kBlkLd + lane];
+      }
+    }
+    __syncwarp();   // tables written before the next panel reads them
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) w.ns[node].singular = 1;
-  // reduced block row of the segment: the carry rows [F | Y | rhs]
-  const int rank = __popc(__ballot_sync(0xffffffffu, carry) & lt_mask);
-  if (carry) {
-    T row[25];
-#pragma unroll
-    for (int c = 0; c < 24; ++c) row[c] = r[c];
-    row[24] = r[36];
-    T* red = static_cast<T*>(w.Red) + (node * smax + s) * int64_t(kBlk);
-    store_row25<T>(red + rank * kBlkLd, row);
-  }
 }
 
 template <typename T>
