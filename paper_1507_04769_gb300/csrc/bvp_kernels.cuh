@@ -328,21 +328,55 @@ __global__ void k_ls_reduce(SolveArgs a, Workspace w, int mode) {
 }
 
 // ---------------------------------------------------------------- Jacobian
+constexpr int kPtWarps = 4;    // warps per block of k_point
+constexpr int kPtLd = 76;      // staged row stride of a point: six rows (72) + 4, 16-byte aligned
+
 template <typename T>
-__global__ void k_point(SolveArgs a, Workspace w) {
+__global__ void __launch_bounds__(32 * kPtWarps) k_point(SolveArgs a, Workspace w) {
   const int64_t P = npts(a.Nmax);
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= a.n * P) return;
-  const int64_t node = t / P;
-  const int64_t p = t % P;
-  if (!w.ns[node].active) return;
-  if (p > 3 * int64_t(a.N[node])) return;
+  bool valid = t < a.n * P;
+  if (valid) {
+    const int64_t node = t / P, p = t % P;
+    valid = w.ns[node].active && p <= 3 * int64_t(a.N[node]);
+  }
   double y[12];
 #pragma unroll
-  for (int c = 0; c < 12; ++c) y[c] = w.Y[t * 12 + c];
-  char_jacobian<T>(a.P, y, static_cast<T*>(w.Jm) + t * 144, nullptr);
+  for (int c = 0; c < 12; ++c) y[c] = valid ? w.Y[t * 12 + c] : 0.0;
+  if constexpr (sizeof(T) == 8) {
+    if (valid) char_jacobian<T>(a.P, y, static_cast<T*>(w.Jm) + t * 144, nullptr);
+  } else {
+    // The 32 points of a warp are consecutive in Jm.  Rows are staged in
+    // shared memory six at a time and the warp writes them as contiguous
+    // 288-byte runs (one per point) instead of 48-byte rows 576 bytes apart.
+    __shared__ __align__(16) float stage[kPtWarps][32 * kPtLd];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    if (vmask == 0u) return;   // the whole warp
+    float* mine = stage[warp] + lane * kPtLd;
+    float* Jw = static_cast<float*>(w.Jm) + (t - lane) * 144;   // the warp's first point
+    char_jacobian_rows<float>(
+        a.P, y,
+        [&](int r, const float (&row)[12]) {
+          float4* dst = reinterpret_cast<float4*>(mine + 12 * (r % 6));
+#pragma unroll
+          for (int q4 = 0; q4 < 3; ++q4)
+            dst[q4] = make_float4(row[4 * q4], row[4 * q4 + 1], row[4 * q4 + 2], row[4 * q4 + 3]);
+          if (r % 6 == 5) {
+            __syncwarp();
+            const int h = r / 6;
+            for (int e = lane; e < 32 * 18; e += 32) {
+              const int pt = e / 18, q = e % 18;
+              if ((vmask >> pt) & 1u)
+                reinterpret_cast<float4*>(Jw + pt * 144 + 72 * h)[q] =
+                    reinterpret_cast<const float4*>(stage[warp] + pt * kPtLd)[q];
+            }
+            __syncwarp();
+          }
+        },
+        nullptr);
+  }
 }
-
 
 // ---------------------------------------------------------------- helpers
 // Pivot search of the register-resident kernels: the largest |v| over the

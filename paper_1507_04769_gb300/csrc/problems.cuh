@@ -389,12 +389,14 @@ __device__ __forceinline__ const double* node_target(const DevProblem& P, int64_
   return (P.kind == SG_PROBLEM_ATTITUDE && P.target) ? P.target + node * 3 : nullptr;
 }
 
-// Jacobian dF/dy (12 x 12, row-major) in precision T, from one dual pass over
-// the six state directions.  If Fout is non-null and T is double, the FP64
-// right-hand side from the value parts is written there as well.
-template <typename T>
-__device__ __forceinline__ void char_jacobian(const DevProblem& P, const double* y, T* Jm,
-                                              double* Fout) {
+// Jacobian dF/dy (12 x 12) in precision T, from one dual pass over the six
+// state directions.  Row r goes to put_row(r, row[12]), in the order r = 0..11
+// (every thread of a warp makes the same calls, so the sink may work across
+// the warp).  If Fout is non-null and T is double, the FP64 right-hand side
+// from the value parts is written there as well.
+template <typename T, typename Sink>
+__device__ __forceinline__ void char_jacobian_rows(const DevProblem& P, const double* y, Sink&& put_row,
+                                                   double* Fout) {
   if (P.kind == SG_PROBLEM_EXAMPLE3) {
     using D = Dual<T, 6>;
     D x[3], lam[3], dx[3], dl[3];
@@ -420,8 +422,7 @@ __device__ __forceinline__ void char_jacobian(const DevProblem& P, const double*
           row[6 + c] = f.d[3 + c];
         }
       }
-#pragma unroll
-      for (int c = 0; c < 12; ++c) Jm[12 * r + c] = row[c];
+      put_row(r, row);
     }
     if (Fout) char_rhs(P, y, Fout);
     return;
@@ -454,16 +455,7 @@ __device__ __forceinline__ void char_jacobian(const DevProblem& P, const double*
           row[6 + c] = -f0[c].d[r - 6];                                    // -f0_x'
         }
       }
-      if constexpr (sizeof(T) == 4) {
-        float4* dst = reinterpret_cast<float4*>(Jm + 12 * r);
-#pragma unroll
-        for (int q4 = 0; q4 < 3; ++q4)
-          dst[q4] = make_float4(row[4 * q4], row[4 * q4 + 1], row[4 * q4 + 2], row[4 * q4 + 3]);
-      } else {
-        double2* dst = reinterpret_cast<double2*>(Jm + 12 * r);
-#pragma unroll
-        for (int q2 = 0; q2 < 6; ++q2) dst[q2] = make_double2(row[2 * q2], row[2 * q2 + 1]);
-      }
+      put_row(r, row);
     }
     if (Fout) {
 #pragma unroll
@@ -479,17 +471,42 @@ __device__ __forceinline__ void char_jacobian(const DevProblem& P, const double*
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < 6; ++r) {
+    for (int r = 0; r < 12; ++r) {
+      T row[12];
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
-        Jm[12 * r + c] = T(P.A[6 * r + c]);
-        Jm[12 * r + 6 + c] = T(-P.K[6 * r + c]);
-        Jm[12 * (6 + r) + c] = T(-P.Q[6 * r + c]);
-        Jm[12 * (6 + r) + 6 + c] = T(-P.A[6 * c + r]);
+        if (r < 6) {
+          row[c] = T(P.A[6 * r + c]);
+          row[6 + c] = T(-P.K[6 * r + c]);
+        } else {
+          row[c] = T(-P.Q[6 * (r - 6) + c]);
+          row[6 + c] = T(-P.A[6 * c + (r - 6)]);
+        }
       }
+      put_row(r, row);
     }
     if (Fout) char_rhs(P, y, Fout);
   }
+}
+
+// The same Jacobian stored row-major at Jm (16-byte rows).
+template <typename T>
+__device__ __forceinline__ void char_jacobian(const DevProblem& P, const double* y, T* Jm, double* Fout) {
+  char_jacobian_rows<T>(
+      P, y,
+      [&](int r, const T (&row)[12]) {
+        if constexpr (sizeof(T) == 4) {
+          float4* dst = reinterpret_cast<float4*>(Jm + 12 * r);
+#pragma unroll
+          for (int q4 = 0; q4 < 3; ++q4)
+            dst[q4] = make_float4(row[4 * q4], row[4 * q4 + 1], row[4 * q4 + 2], row[4 * q4 + 3]);
+        } else {
+          double2* dst = reinterpret_cast<double2*>(Jm + 12 * r);
+#pragma unroll
+          for (int q2 = 0; q2 < 6; ++q2) dst[q2] = make_double2(row[2 * q2], row[2 * q2 + 1]);
+        }
+      },
+      Fout);
 }
 
 // Running cost L(x, u*(x, lambda)) (Section 2) at y = (x, lambda).
