@@ -164,6 +164,8 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
   __shared__ double ys[kTrialPts][12];   // dfnum in the mixed form (same size)
   __shared__ double fs[kTrialPts][12];
   __shared__ double part_s[3 * kTrialIv][2];
+  __shared__ double cA_s[3][4];          // h a_kj as pairs (mixed form), k = 1..3
+  __shared__ double h_s;
   const int tid = threadIdx.x;
   const int nchunk = trial_chunks(a.Nmax);
   const int64_t node = blockIdx.x / nchunk;
@@ -177,6 +179,13 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
   const double alpha = s.alpha;
   const int64_t base = node * npts(a.Nmax) + 3 * int64_t(i0);
   auto ypoint = [&](int64_t pt, int c) { return __fma_rn(alpha, w.D[pt * 12 + c], w.Y[pt * 12 + c]); };
+  // the step and the stage coefficients once per block (the last 12 threads)
+  if (tid >= 128 - 12) {
+    const int e = tid - (128 - 12), k = e / 4 + 1, jj = e % 4;
+    const double h = a.T[node] / N;
+    if (e == 0) h_s = h;
+    if constexpr (kPair) *reinterpret_cast<dfnum*>(&cA_s[k - 1][jj]) = dfnum(h * kLobA[k][jj]);
+  }
   if (tid <= 3 * niv) {
     if constexpr (kPair) {
       dfnum y[12], F[12];
@@ -203,7 +212,7 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
     }
   }
   __syncthreads();
-  const double h = a.T[node] / N;
+  const double h = h_s;
   if (tid < 3 * niv) {
     // interval j = tid / 3 of the chunk, stage row block k = tid % 3 + 1
     const int j = tid / 3, k = tid % 3 + 1;
@@ -212,7 +221,8 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
     double ss = 0.0, mx = 0.0;
     bool bad = false;
     if constexpr (kPair) {
-      const dfnum c0(h * kLobA[k][0]), c1(h * kLobA[k][1]), c2(h * kLobA[k][2]), c3(h * kLobA[k][3]);
+      const dfnum* cA = reinterpret_cast<const dfnum*>(&cA_s[k - 1][0]);
+      const dfnum c0 = cA[0], c1 = cA[1], c2 = cA[2], c3 = cA[3];
       const dfnum* y0 = reinterpret_cast<const dfnum*>(ys[p0]);
       const dfnum* yk = reinterpret_cast<const dfnum*>(ys[p0 + k]);
       const dfnum* f0 = reinterpret_cast<const dfnum*>(fs[p0]);
