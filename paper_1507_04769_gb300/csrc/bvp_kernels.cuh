@@ -1203,7 +1203,8 @@ __global__ void __launch_bounds__(32 * seg_warps<T>()) k_abd_seg(SolveArgs a, Wo
       if (q >= k / V)
         reinterpret_cast<float4*>(segp + k * kSegLd + 12)[q] = reinterpret_cast<const float4*>(U_s + k * 12)[q];
     }
-#pragma unroll 3
+    const bool zcol = c >= 12 && c < 24;
+#pragma unroll
     for (int m = 0; m < 12; ++m) {
       const int r = cslot_s[m];
       T f = P_s[r * kSegP + c], g = T(0);
@@ -1215,21 +1216,18 @@ __global__ void __launch_bounds__(32 * seg_warps<T>()) k_abd_seg(SolveArgs a, Wo
         else f = fma(-l[k], Q[k], f);
       }
       f += g;
-      if (col) {
-        if (!more) {
-          red[m * kBlkLd + c] = f;   // last panel: the carry rows are the reduced row [F | Y | rhs]
-        } else if (c >= 12 && c < 24) {
-          Y_s[r * 12 + c - 12] = f;   // Z moves into the y_i slot
-          P_s[r * kSegP + c] = T(0);
-        } else {
-          P_s[r * kSegP + c] = f;
-        }
+      if (more) {
+        // Z moves into the y_i slot
+        if (col) P_s[r * kSegP + c] = zcol ? T(0) : f;
+        if (zcol) Y_s[r * 12 + c - 12] = f;
+      } else if (col) {
+        red[m * kBlkLd + c] = f;   // last panel: the carry rows are the reduced row [F | Y | rhs]
       }
     }
     if (more) {   // the pivot slots take block row i + 1 = [0 | S | T | r]
       cp_async_wait_all();   // this lane's part of the stage has landed
       __syncwarp();          // ... and every lane's
-#pragma unroll 4
+#pragma unroll
       for (int k = 0; k < 12; ++k) {
         const int slot = perm_s[k];
         if (col) P_s[slot * kSegP + c] = c < 12 ? T(0) : stage[k * kBlkLd + c];
