@@ -170,6 +170,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
   const int64_t npoint = a.n * P;
   const int64_t nint = a.n * a.Nmax;
   const unsigned gp = static_cast<unsigned>(ceil_div(npoint, 128));
+  const unsigned gupd = static_cast<unsigned>(ceil_div(npoint * kUpdPer, 128));
   const unsigned gi = static_cast<unsigned>(a.n * trial_chunks(a.Nmax));
   const unsigned gnode_thr = static_cast<unsigned>(ceil_div(a.n, 128));
   const unsigned gnode_warp = static_cast<unsigned>(ceil_div(a.n * 32, 128));
@@ -244,7 +245,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
       if (h_cnt[0] == 0) break;
     }
     SG_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), st));
-    SG_TIMED("k_update", st, (k_update<<<gp, 128, 0, st>>>(a, w)));
+    SG_TIMED("k_update", st, (k_update<<<gupd, 128, 0, st>>>(a, w)));
     SG_TIMED("k_after_update", st, (k_after_update<<<gnode_thr, 128, 0, st>>>(a, w)));
     SG_LAUNCH_CHECK("update kernels");
     if ((rc = read_counters()) != SG_OK) return rc;
@@ -371,7 +372,7 @@ static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, dou
   cudaGraph_t ls_body;
   nb.loop(hl, &ls_body);
   nb.memset0(w.counters, 2 * sizeof(int));
-  nb.kernel(k_update, gp, 128, 0, a, w);
+  nb.kernel(k_update, static_cast<unsigned>(ceil_div(a.n * npts(a.Nmax) * kUpdPer, 128)), 128, 0, a, w);
   nb.kernel(k_after_update, gnt, 128, 0, a, w);
   nb.kernel(k_set_cond, 1, 1, 0, hn, static_cast<const int*>(w.counters + 1));
   if (nb.err != cudaSuccess) return nb.err;

@@ -1255,6 +1255,9 @@ __global__ void __launch_bounds__(128) k_abd_red(SolveArgs a, Workspace w) {
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_abd_segback(SolveArgs a, Workspace w) {
+  // the pivot rows of panel i - 1 are copied to shared memory (asynchronously)
+  // while panel i is substituted
+  __shared__ __align__(16) T buf_s[4][2][12 * kSegLd];
   const int lane = threadIdx.x & 31;
   const int smax = seg_count(a.Nmax);
   const int64_t wid = blockIdx.x * int64_t(4) + (threadIdx.x >> 5);
@@ -1275,14 +1278,25 @@ __global__ void __launch_bounds__(128) k_abd_segback(SolveArgs a, Workspace w) {
     dya[c] = T(D[3 * int64_t(i0) * 12 + c]);
     dyn[c] = T(D[3 * int64_t(i1) * 12 + c]);
   }
-  for (int i = i1 - 1; i > i0; --i) {
+  T (*buf)[12 * kSegLd] = buf_s[threadIdx.x >> 5];
+  auto fetch = [&](int i, int b) {   // panel i's 12 pivot rows to buf[b]
+    const char* src = reinterpret_cast<const char*>(seg + int64_t(i) * 12 * kSegLd);
+    for (int e = lane; e < 12 * kSegLd * int(sizeof(T)) / 16; e += 32)
+      cp_async16(reinterpret_cast<char*>(buf[b]) + 16 * e, src + 16 * e);
+    cp_async_commit();
+  };
+  fetch(i1 - 1, 0);
+  for (int i = i1 - 1, b = 0; i > i0; --i, b ^= 1) {
+    cp_async_wait_all();   // panel i has landed (this lane's part) ...
+    __syncwarp();          // ... and every lane's; buf[b ^ 1] was read in the last pass
+    if (i - 1 > i0) fetch(i - 1, b ^ 1);
     // lane k holds pivot row k of panel i: [F | U (1/pivot at k) | V | rhs]
     T r[37];
 #pragma unroll
     for (int c = 0; c < 37; ++c) r[c] = T(0);
     if (lane < 12) {
       T row[40];
-      load_row40<T>(seg + (int64_t(i) * 12 + lane) * kSegLd, row);
+      load_row40<T>(buf[b] + lane * kSegLd, row);
 #pragma unroll
       for (int c = 0; c < 37; ++c) r[c] = row[c];
     }
@@ -1389,16 +1403,22 @@ __global__ void k_ls_begin(SolveArgs a, Workspace w) {
   w.ns[node] = s;
 }
 
+// Y += alpha D, a thread per pair of components (consecutive threads touch
+// consecutive 16-byte words).
+constexpr int kUpdPer = 6;   // threads per collocation point
 __global__ void k_update(SolveArgs a, Workspace w) {
   const int64_t P = npts(a.Nmax);
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= a.n * P) return;
+  const int64_t u = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (u >= a.n * P * kUpdPer) return;
+  const int64_t t = u / kUpdPer;
   const int64_t node = t / P;
   if (!w.ns[node].active) return;
   if (t % P > 3 * int64_t(a.N[node])) return;
   const double alpha = w.ns[node].alpha;
-#pragma unroll
-  for (int c = 0; c < 12; ++c) w.Y[t * 12 + c] = __fma_rn(alpha, w.D[t * 12 + c], w.Y[t * 12 + c]);
+  double2* y2 = reinterpret_cast<double2*>(w.Y) + u;
+  const double2 d = reinterpret_cast<const double2*>(w.D)[u];
+  const double2 y = *y2;
+  *y2 = make_double2(__fma_rn(alpha, d.x, y.x), __fma_rn(alpha, d.y, y.y));
 }
 
 __global__ void k_after_update(SolveArgs a, Workspace w) {
