@@ -171,6 +171,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
   const int64_t nint = a.n * a.Nmax;
   const unsigned gp = static_cast<unsigned>(ceil_div(npoint, 128));
   const unsigned gupd = static_cast<unsigned>(ceil_div(npoint * kUpdPer, 128));
+  const unsigned ginit = static_cast<unsigned>(ceil_div(npoint * kInitPer, 128));
   const unsigned gi = static_cast<unsigned>(a.n * trial_chunks(a.Nmax));
   const unsigned gnode_thr = static_cast<unsigned>(ceil_div(a.n, 128));
   const unsigned gnode_warp = static_cast<unsigned>(ceil_div(a.n * 32, 128));
@@ -196,7 +197,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
     const int64_t want = ceil_div(a.n, 4);
     const unsigned grid = static_cast<unsigned>(want < int64_t(sms) * per_sm ? want : int64_t(sms) * per_sm);
     SG_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), st));
-    SG_TIMED("k_init", st, (k_init<<<gp, 128, 0, st>>>(a, w)));
+    SG_TIMED("k_init", st, (k_init<<<ginit, 128, 0, st>>>(a, w)));
     SG_TIMED(kname<T>("k_newton_persistent"), st, (k_newton_persistent<T><<<grid, 128, smem, st>>>(a, w)));
     SG_TIMED("k_outputs", st, (k_outputs<<<gnode_warp, 128, 0, st>>>(a, w, lambda0, u0, V, status, iters)));
     if (Yout) SG_TIMED("k_copy_Y", st, (k_copy_Y<<<gp, 128, 0, st>>>(a, w, Yout)));
@@ -214,7 +215,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
   };
   int rc;
   SG_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), st));
-  SG_TIMED("k_init", st, (k_init<<<gp, 128, 0, st>>>(a, w)));
+  SG_TIMED("k_init", st, (k_init<<<ginit, 128, 0, st>>>(a, w)));
   SG_TIMED("k_trial", st, (k_trial<T><<<gi, 128, 0, st>>>(a, w)));
   SG_TIMED("k_ls_reduce", st, (k_ls_reduce<<<gnode_warp, 128, 0, st>>>(a, w, 0)));
   SG_LAUNCH_CHECK("init kernels");
@@ -344,7 +345,7 @@ static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, dou
   if ((e = cudaGraphConditionalHandleCreate(&hl, root, 0, 0)) != cudaSuccess) return e;
   GraphBuilder rb{root, {}};
   rb.memset0(w.counters, 4 * sizeof(int));
-  rb.kernel(k_init, gp, 128, 0, a, w);
+  rb.kernel(k_init, static_cast<unsigned>(ceil_div(a.n * P * kInitPer, 128)), 128, 0, a, w);
   rb.kernel(k_trial<T>, gi, 128, 0, a, w);
   rb.kernel(k_ls_reduce, gnw, 128, 0, a, w, 0);
   rb.kernel(k_set_cond, 1, 1, 0, hn, static_cast<const int*>(w.counters + 1));
@@ -398,7 +399,7 @@ static cudaError_t build_persistent_graph(const SolveArgs& a, const Workspace& w
   if (e != cudaSuccess) return e;
   GraphBuilder rb{root, {}};
   rb.memset0(w.counters, 4 * sizeof(int));
-  rb.kernel(k_init, static_cast<unsigned>(ceil_div(a.n * P, 128)), 128, 0, a, w);
+  rb.kernel(k_init, static_cast<unsigned>(ceil_div(a.n * P * kInitPer, 128)), 128, 0, a, w);
   rb.kernel(k_newton_persistent<T>, grid, 128, static_cast<size_t>(smem), a, w);
   rb.kernel(k_outputs, static_cast<unsigned>(ceil_div(a.n * 32, 128)), 128, 0, a, w, lambda0, u0, V, status, iters);
   if (Yout) rb.kernel(k_copy_Y, static_cast<unsigned>(ceil_div(a.n * P, 128)), 128, 0, a, w, Yout);

@@ -104,31 +104,31 @@ struct SolveArgs {
 __host__ __device__ __forceinline__ int64_t npts(int Nmax) { return 3 * int64_t(Nmax) + 1; }
 
 // ---------------------------------------------------------------- setup
+// A thread per pair of components of a collocation point (consecutive
+// threads write consecutive 16-byte words); the node's first thread also
+// sets up its state.
+constexpr int kInitPer = 6;   // threads per collocation point
 __global__ void k_init(SolveArgs a, Workspace w) {
   const int64_t P = npts(a.Nmax);
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= a.n * P) return;
+  const int64_t u = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (u >= a.n * P * kInitPer) return;
+  const int64_t t = u / kInitPer;
+  const int q = static_cast<int>(u % kInitPer);   // components 2q, 2q + 1
   const int64_t node = t / P;
   const int64_t p = t % P;
   const double* x0 = a.x0 + node * 6;
-  double* y = w.Y + t * 12;
-  double* d = w.D + t * 12;
+  double2 y;
   if (a.Yin) {
-#pragma unroll
-    for (int c = 0; c < 12; ++c) {
-      y[c] = a.Yin[t * 12 + c];   // warm start
-      d[c] = 0.0;
-    }
+    // warm start (the caller's array may be only 8-byte aligned)
+    y = (reinterpret_cast<uintptr_t>(a.Yin) & 15u) ? make_double2(a.Yin[2 * u], a.Yin[2 * u + 1])
+                                                   : reinterpret_cast<const double2*>(a.Yin)[u];
   } else {
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      y[c] = x0[c];   // x held at x0, lambda = 0 (zero control)
-      y[6 + c] = 0.0;
-      d[c] = 0.0;
-      d[6 + c] = 0.0;
-    }
+    // x held at x0, lambda = 0 (zero control)
+    y = q < 3 ? make_double2(x0[2 * q], x0[2 * q + 1]) : make_double2(0.0, 0.0);
   }
-  if (p == 0) {
+  reinterpret_cast<double2*>(w.Y)[u] = y;
+  reinterpret_cast<double2*>(w.D)[u] = make_double2(0.0, 0.0);
+  if (p == 0 && q == 0) {
     NodeState s{};
     const int N = a.N[node];
     const double T = a.T[node];

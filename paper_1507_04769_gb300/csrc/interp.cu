@@ -66,25 +66,45 @@ __global__ void k_fine_table(int level, const double* xf, double* tab1) {
 }
 
 // One level of Eq. interpo: for the nodes n in [n0, n1) (all with |i| = s),
-// w_n = f_n - sum over coarser nodes m < n0 of phi_m(x_n) w_m.
-__global__ void k_surplus_level(int64_t n0, int64_t n1, int d, int k, int fine_n,
-                                const uint16_t* __restrict__ fid, const int16_t* __restrict__ fpt,
-                                const double* __restrict__ tab1, const double* __restrict__ f,
-                                double* __restrict__ W) {
-  const int64_t n = n0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+// w_n = f_n - sum over coarser nodes m < n0 of phi_m(x_n) w_m.  A warp per
+// node n: lane l takes the coarser nodes m = l (mod 32), then the 32 partial
+// sums are added by a fixed shuffle tree (the result does not depend on the
+// launch).
+constexpr int kSurpWarps = 4;
+template <int KM>   // compile-time bound on the outputs k (so the sums stay in registers)
+__global__ void __launch_bounds__(32 * kSurpWarps)
+    k_surplus_level(int64_t n0, int64_t n1, int d, int k, int fine_n, const uint16_t* __restrict__ fid,
+                    const int16_t* __restrict__ fpt, const double* __restrict__ tab1,
+                    const double* __restrict__ f, double* __restrict__ W) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = n0 + blockIdx.x * int64_t(kSurpWarps) + (threadIdx.x >> 5);
   if (n >= n1) return;
-  double acc[kMaxOut];
-  for (int c = 0; c < k; ++c) acc[c] = f[n * k + c];
+  double acc[KM];
+#pragma unroll
+  for (int c = 0; c < KM; ++c) acc[c] = 0.0;
   int pts[kMaxDim];
-  for (int dim = 0; dim < d; ++dim) pts[dim] = fpt[n * d + dim];
-  for (int64_t m = 0; m < n0; ++m) {
+#pragma unroll
+  for (int dim = 0; dim < kMaxDim; ++dim) pts[dim] = dim < d ? fpt[n * d + dim] : 0;
+  for (int64_t m = lane; m < n0; m += 32) {
     double phi = 1.0;
-    for (int dim = 0; dim < d && phi != 0.0; ++dim)
-      phi *= tab1[int(fid[m * d + dim]) * (fine_n + 1) + pts[dim]];
-    if (phi != 0.0)
-      for (int c = 0; c < k; ++c) acc[c] -= phi * W[m * k + c];
+#pragma unroll
+    for (int dim = 0; dim < kMaxDim; ++dim)
+      if (dim < d && phi != 0.0) phi *= tab1[int(fid[m * d + dim]) * (fine_n + 1) + pts[dim]];
+    if (phi != 0.0) {
+#pragma unroll
+      for (int c = 0; c < KM; ++c)
+        if (c < k) acc[c] = fma(phi, W[m * k + c], acc[c]);
+    }
   }
-  for (int c = 0; c < k; ++c) W[n * k + c] = acc[c];
+#pragma unroll
+  for (int c = 0; c < KM; ++c) {
+    if (c < k) {
+      double v = acc[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) W[n * k + c] = f[n * k + c] - v;
+    }
+  }
 }
 
 // Gather rows of W into the evaluation order.
@@ -338,8 +358,10 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   SG_TRY_CLEAN(cudaGetLastError());
   for (size_t lv = 0; lv + 1 < level_start.size(); ++lv) {
     const int64_t n0 = level_start[lv], n1 = level_start[lv + 1];
-    SG_TIMED("k_surplus_level", st, (k_surplus_level<<<static_cast<unsigned>(ceil_div(n1 - n0, 128)), 128, 0, st>>>(
-        n0, n1, d, k, fine_n, d_fid, d_fpt, d_tab1, d_values, s->W)));
+    auto* kern = k <= 4 ? k_surplus_level<4> : k_surplus_level<kMaxOut>;
+    SG_TIMED("k_surplus_level", st,
+             (kern<<<static_cast<unsigned>(ceil_div(n1 - n0, kSurpWarps)), 32 * kSurpWarps, 0, st>>>(
+                 n0, n1, d, k, fine_n, d_fid, d_fpt, d_tab1, d_values, s->W)));
     SG_TRY_CLEAN(cudaGetLastError());
   }
   SG_TIMED("k_gather_rows", st, (k_gather_rows<<<static_cast<unsigned>(ceil_div(M * k, 256)), 256, 0, st>>>(M, k, d_order, s->W, s->Ws)));
