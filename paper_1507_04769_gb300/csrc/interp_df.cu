@@ -23,6 +23,10 @@ constexpr int kFoldBlock = 64;     // nodes per FP64 fold of the compensated sum
 constexpr int kDfWarps = 4;        // warps per block
 constexpr int kDfThreads = 32 * kDfWarps;
 constexpr int kDfChunk = 256;      // nodes staged in shared memory at a time
+// surplus pairs per staged node: K rounded up to even, so a node's pairs are
+// read as 16-byte words
+template <int K>
+constexpr int df_kp() { return (K + 1) & ~1; }
 
 // Product of a pair with a pair, left unnormalised: the result (p, e) has
 // p = fl(a.hi b.hi) and e = the exact rounding error of p plus the cross
@@ -56,7 +60,7 @@ __device__ __forceinline__ void df_group(const unsigned char* __restrict__ tab_q
   while (left > 0) {
     // a run of nodes up to the next fold, with no per-node fold test
     const int run = left < kFoldBlock - since_fold ? left : kFoldBlock - since_fold;
-#pragma unroll 4
+#pragma unroll 2
     for (int r = 0; r < run; ++r, nn += NS) {
       df phi = {1.0f, 0.0f};
       if constexpr (A > 0) {
@@ -81,13 +85,22 @@ __device__ __forceinline__ void df_group(const unsigned char* __restrict__ tab_q
           phi = df_mul_raw(phi, {f.x, f.y});
         }
       }
+      float2 wv[df_kp<K>()];
+#pragma unroll
+      for (int h = 0; h < df_kp<K>() / 2; ++h) {
+        const float4 v = reinterpret_cast<const float4*>(w_s + nn * df_kp<K>())[h];
+        wv[2 * h] = make_float2(v.x, v.y);
+        wv[2 * h + 1] = make_float2(v.z, v.w);
+      }
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        const float2 wc = w_s[nn * K + c];
-        // exact product phi.hi * w.hi = p + pe; cross terms to t
+        const float2 wc = wv[c];
+        // p = fl(phi.hi w.hi); t = its exact rounding error plus the cross
+        // terms (the unnormalised product of df_mul_raw)
         const float p = __fmul_rn(phi.hi, wc.x);
-        const float pe = __fmaf_rn(phi.hi, wc.x, -p);
-        const float t = __fadd_rn(__fmaf_rn(phi.hi, wc.y, __fmul_rn(phi.lo, wc.x)), pe);
+        float t = __fmaf_rn(phi.hi, wc.x, -p);
+        t = __fmaf_rn(phi.hi, wc.y, t);
+        t = __fmaf_rn(phi.lo, wc.x, t);
         // Knuth's two_sum of the running sum and p
         const float s = __fadd_rn(acc[c].ah, p);
         const float bb = __fsub_rn(s, acc[c].ah);
@@ -126,7 +139,7 @@ __global__ void __launch_bounds__(kDfThreads) k_eval_df32(EvalArgs e, int d) {
   const int tab_bytes = d * nf * QB * static_cast<int>(sizeof(float2));
   float2* tab = reinterpret_cast<float2*>(smem_raw);                                  // [d*nf][QB]
   uint32_t* off_s = reinterpret_cast<uint32_t*>(smem_raw + tab_bytes);                 // [kDfChunk][kMaxDim]
-  float2* w_s = reinterpret_cast<float2*>(off_s + kDfChunk * kMaxDim);                 // [kDfChunk][K]
+  float2* w_s = reinterpret_cast<float2*>(off_s + kDfChunk * kMaxDim);                 // [kDfChunk][df_kp<K>]
   const int tid = threadIdx.x;
   const int ql = tid % QB, stream = tid / QB;
   const int64_t qbase = blockIdx.x * int64_t(QB);
@@ -152,7 +165,7 @@ __global__ void __launch_bounds__(kDfThreads) k_eval_df32(EvalArgs e, int d) {
       // table row (dim * nf + id) -> byte offset within the query column
       off_s[x] = static_cast<uint32_t>(e.ops[(m0 + nn) * kMaxDim + j]) * (QB * sizeof(float2));
     }
-    for (int x = tid; x < cn * K; x += kDfThreads) w_s[x] = e.Wdf[m0 * K + x];
+    for (int x = tid; x < cn * K; x += kDfThreads) w_s[(x / K) * df_kp<K>() + x % K] = e.Wdf[m0 * K + x];
     __syncthreads();
     // groups of equal active-dimension count that meet this chunk
     for (int a = 0; a <= kMaxDim; ++a) {
@@ -197,7 +210,7 @@ template <int K, int QB>
 static size_t df32_smem(const EvalArgs& e, int d) {
   const size_t tab = sizeof(float2) * d * e.nf * QB;
   const size_t red = sizeof(double) * kDfThreads * K;
-  return (tab > red ? tab : red) + sizeof(uint32_t) * kDfChunk * kMaxDim + sizeof(float2) * kDfChunk * K;
+  return (tab > red ? tab : red) + sizeof(uint32_t) * kDfChunk * kMaxDim + sizeof(float2) * kDfChunk * df_kp<K>();
 }
 
 template <int K, int QB>
