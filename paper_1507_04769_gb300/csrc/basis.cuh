@@ -106,7 +106,70 @@ __device__ __forceinline__ df df_recip(df a) {
 
 // All 1-D basis values at u (FP64 in [0,1]) for levels 1..L+1, as pairs, in
 // barycentric form on the finest set (see basis_row in interp.cu).
+// The same for a level fixed at compile time: every loop unrolls, so the
+// reciprocals stay in registers (the general form indexes them at run time,
+// which puts them in local memory).
+template <int L>
+__device__ __forceinline__ void basis_row_df_t(double u, const float2* __restrict__ xf, float2* tab, int stride) {
+  constexpr int fine_n = 1 << L;
+  tab[0] = make_float2(1.0f, 0.0f);
+  const df uu = df_from(u);
+  df rinv[fine_n + 1];
+  int hit = -1;
+#pragma unroll
+  for (int p = 0; p <= fine_n; ++p) {
+    const df d = df_sub(uu, {xf[p].x, xf[p].y});
+    if (d.hi == 0.0f && d.lo == 0.0f) {
+      hit = p;
+      rinv[p] = {0.0f, 0.0f};
+    } else {
+      rinv[p] = df_recip(d);
+    }
+  }
+  int id = 1;
+#pragma unroll
+  for (int l = 2; l <= L + 1; ++l) {
+    const int n = 1 << (l - 1);
+    const int sf = fine_n / n;
+    const bool exact = hit >= 0 && (hit % sf) == 0;
+    df inv_denom = {0.0f, 0.0f};
+    if (!exact) {
+      df den = {0.0f, 0.0f};
+#pragma unroll
+      for (int m = 0; m <= n; ++m) {
+        float wm = (m & 1) ? -1.0f : 1.0f;
+        if (m == 0 || m == n) wm *= 0.5f;
+        den = df_add(den, df_scale(rinv[m * sf], wm));
+      }
+      inv_denom = df_recip(den);
+    }
+    const int cnt = l == 2 ? 2 : (n >> 1);
+#pragma unroll
+    for (int j = 0; j < cnt; ++j) {
+      const int m = l == 2 ? j * n : 2 * j + 1;
+      df v;
+      if (exact) {
+        v = {(m * sf == hit) ? 1.0f : 0.0f, 0.0f};
+      } else {
+        float wm = (m & 1) ? -1.0f : 1.0f;
+        if (m == 0 || m == n) wm *= 0.5f;
+        v = df_mul(df_scale(rinv[m * sf], wm), inv_denom);
+      }
+      tab[(id + j) * stride] = make_float2(v.hi, v.lo);
+    }
+    id += cnt;
+  }
+}
+
 __device__ inline void basis_row_df(double u, int level, const float2* __restrict__ xf, float2* tab, int stride) {
+  switch (level) {
+    case 1: return basis_row_df_t<1>(u, xf, tab, stride);
+    case 2: return basis_row_df_t<2>(u, xf, tab, stride);
+    case 3: return basis_row_df_t<3>(u, xf, tab, stride);
+    case 4: return basis_row_df_t<4>(u, xf, tab, stride);
+    case 5: return basis_row_df_t<5>(u, xf, tab, stride);
+    default: break;
+  }
   tab[0] = make_float2(1.0f, 0.0f);
   if (level == 0) return;
   const int fine_n = 1 << level;

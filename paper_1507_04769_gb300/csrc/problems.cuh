@@ -50,7 +50,7 @@ __device__ __forceinline__ S pconst(double d, float2 f);
 template <>
 __device__ __forceinline__ double pconst<double>(double d, float2) { return d; }
 template <>
-__device__ __forceinline__ float pconst<float>(double d, float2) { return static_cast<float>(d); }
+__device__ __forceinline__ float pconst<float>(double, float2 f) { return f.x; }   // the nearest float, stored
 template <>
 __device__ __forceinline__ dfnum pconst<dfnum>(double, float2 f) { return dfnum(f.x, f.y, 0); }
 
@@ -438,7 +438,8 @@ __device__ __forceinline__ void char_jacobian_rows(const DevProblem& P, const do
       lam[i] = T(y[6 + i]);
     }
     attitude_f0_grad<D, T>(P, x, lam, f0, g);
-    const T wdiag[6] = {T(P.wv), T(P.wv), T(P.wv), T(P.ww), T(P.ww), T(P.ww)};
+    const T wv = pconst<T>(P.wv, P.wv_f), ww = pconst<T>(P.ww, P.ww_f);
+    const T wdiag[6] = {wv, wv, wv, ww, ww, ww};
     // rows are assembled in registers and written as 16-byte vectors
 #pragma unroll
     for (int r = 0; r < 12; ++r) {
@@ -448,7 +449,7 @@ __device__ __forceinline__ void char_jacobian_rows(const DevProblem& P, const do
         if (r < 6) {
           row[c] = f0[r].d[c];                                             // f0_x
           T k = T(0);
-          if (r >= 3 && c >= 3) k = T(P.Kw[3 * (r - 3) + (c - 3)]);
+          if (r >= 3 && c >= 3) k = pconst<T>(P.Kw[3 * (r - 3) + (c - 3)], P.Kw_f[3 * (r - 3) + (c - 3)]);
           row[6 + c] = -k;                                                 // -K
         } else {
           row[c] = -g[r - 6].d[c] - (r - 6 == c ? wdiag[r - 6] : T(0));    // -(l_xx + phi_xx)
