@@ -47,8 +47,10 @@ SEG_LEN = 16   # intervals per segment of the library's segmented staircase
 # summarised in profiles/solver_kernels_attitude6d_600nodes.md (first Newton
 # iteration of 600 level-4 nodes, 88,064 intervals: 298.8 + 483.1 MB).  Set an
 # entry to None when its kernel changes until it is captured again.
-# (filled from an ncu capture of the kernel as it stands; empty while none is taken)
+# DRAM bytes per unit of work from an ncu capture of the kernel as it stands
+# (the 600-node solve case: 88,064 intervals in one launch)
 DRAM_BYTES_PER_UNIT = {
+    "k_condense_reg_fp32": ((295.942400e6 + 464.498432e6) / 88064, "interval"),
 }
 WORKLOAD = ("attitude6d_L4_1457nodes_T{10,20,40}_N{64,128,256}_mixedprec"
             "+surplus+1e6queries")
