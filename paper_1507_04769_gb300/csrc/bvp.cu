@@ -318,6 +318,7 @@ struct GraphBuilder {
     p.conditional.size = 1;
     cudaGraphNode_t n;
     err = cudaGraphAddNode(&n, g, last.data(), nullptr, last.size(), &p);
+    if (err != cudaSuccess) return;   // no body graph was made
     last.assign(1, n);
     *body = p.conditional.phGraph_out[0];
   }
