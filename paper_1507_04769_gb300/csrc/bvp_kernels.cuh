@@ -1334,7 +1334,8 @@ __device__ __forceinline__ void recover_interval(const SolveArgs& a, const Works
   double* D = w.D + (node * npts(a.Nmax) + 3 * int64_t(i)) * 12;
   const T dyl = lane < 12 ? T(D[lane]) : T(0);
   const T dyr = lane < 12 ? T(D[36 + lane]) : T(0);
-  // the part of row k left of its diagonal is never read (and never stored)
+  // the part of row k left of its diagonal is never read (the FP32
+  // condensation does not store it)
   T row[kRecLd];
 #pragma unroll
   for (int c = 0; c < kRecLd; ++c) row[c] = T(0);
