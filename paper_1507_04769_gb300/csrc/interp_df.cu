@@ -20,7 +20,7 @@
 namespace sg {
 
 constexpr int kFoldBlock = 64;     // nodes per FP64 fold of the compensated sums (per thread)
-constexpr int kDfWarps = 4;        // warps per block
+constexpr int kDfWarps = 6;        // warps per block
 constexpr int kDfThreads = 32 * kDfWarps;
 constexpr int kDfChunk = 256;      // nodes staged in shared memory at a time
 // surplus pairs per staged node: K rounded up to even, so a node's pairs are
