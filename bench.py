@@ -5,8 +5,8 @@ One step = one pass of the whole path on the level-4 6-D attitude workload:
   Step I    sparse grid, d = 6, level 4 (1457 CGL nodes) on [-pi/4, pi/4]^6
   Step II   one characteristic BVP per node, T in {10, 20, 40} with N = 64 / 128
             / 256 Lobatto intervals, Newton to |F|_inf <= 1e-8 (mixed precision:
-            FP32 Jacobian / elimination / direction, pair-of-floats residual,
-            FP64 update)
+            FP32 Jacobian / elimination / direction; FP64 residual, boundary
+            rows, line search and update)
   Step III  surpluses of u*(x) at the nodes
   on-line   u*(x) at 1e6 query states (half uniform, half N(0, 0.2^2) clipped)
 The headline value is converged BVP solves per second of whole-step time.
@@ -277,7 +277,7 @@ def gpu_arm(args):
     dev = torch.device("cuda", local)
     from paper_1507_04769_gb300 import sg
 
-    prec = sg.PREC_MIXED if args.precision == "mixed" else sg.PREC_FP64
+    prec = {"mixed": sg.PREC_MIXED, "mixed-pair": sg.PREC_MIXED_PAIR, "fp64": sg.PREC_FP64}[args.precision]
     eval_mode = {"fp64": sg.EVAL_FP64, "df32": sg.EVAL_DF32, "tf32x3": sg.EVAL_TF32X3}[args.eval]
     lo, hi = synth.box(D)
     params = synth.attitude_params(0)
@@ -443,7 +443,7 @@ def gpu_arm(args):
 
     # ---------------- FP64 form on the same GPU (speedup of the mixed form)
     fp64 = None
-    if prec == sg.PREC_MIXED and not args.skip_fp64:
+    if prec != sg.PREC_FP64 and not args.skip_fp64:
         ws64 = torch.empty(sg.workspace_bytes(M, n_max, sg.PREC_FP64), dtype=torch.uint8, device=dev)
         g = sg.Grid(D, LEVEL, lo, hi)
         r64 = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=sg.PREC_FP64, workspace=ws64,
@@ -474,6 +474,26 @@ def gpu_arm(args):
                 "max_rel_diff_lambda0_mixed_vs_fp64": dl,
                 "newton_iters_hist_fp64": np.bincount(r64["iters"].cpu().numpy()).tolist(),
                 "kernels": dict(list(kern64.items())[:5])}
+        # the other FP32-direction form (residual in FP64, or in pairs of
+        # floats), in the timed form's execution form, on its workspace
+        other = sg.PREC_MIXED_PAIR if prec == sg.PREC_MIXED else sg.PREC_MIXED
+        rr = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=other, workspace=ws,
+                           n_max=n_max, **form)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            rr = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=other, workspace=ws,
+                               n_max=n_max, **form)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tr = a.elapsed_time(b) / 1e3 / args.steps
+        cr = int((rr["status"] == sg.CONVERGED).sum().item())
+        dr = (r64["lambda0"] - rr["lambda0"]).abs().max().item() / r64["lambda0"].abs().max().item()
+        fp64["mixed_pair_residual" if other == sg.PREC_MIXED_PAIR else "mixed_fp64_residual"] = {
+            "solves_per_s": cr / tr, "solve_ms": 1e3 * tr, "speedup_over_fp64": t64 / tr,
+            "max_rel_diff_lambda0_vs_fp64": dr,
+            "newton_iters_hist": np.bincount(rr["iters"].cpu().numpy()).tolist()}
         del ws64
 
     # ---------------- interpolant modes on the 1e6 queries (FP64, DF32, 3xTF32)
@@ -618,11 +638,15 @@ def gpu_arm(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32" if prec == sg.PREC_MIXED else "f64",
+        "dtype": "f64+f32" if prec != sg.PREC_FP64 else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "nodes": M, "grid_level": LEVEL, "d": D,
                    "horizons": "T in {10,20,40}, N = 6.4 T", "queries": N_QUERIES, "tol": TOL,
-                   "precision": args.precision, "eval": args.eval,
+                   "precision": {"mixed": "FP32 Jacobian, elimination and direction; FP64 residual, "
+                                           "boundary rows, line search and update",
+                                 "mixed-pair": "FP32 direction; pair-of-floats residual; FP64 line search and update",
+                                 "fp64": "FP64 throughout"}[args.precision],
+                   "eval": args.eval,
                    "solve_form": form, "autotune_ms": tune_ms,
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"{world} independent instance(s), no collective"},
@@ -675,9 +699,10 @@ def collect_kernel_times(sg):
 def roofline(kt, iters, N_h, M, prec):
     """Per-kernel algorithmic work / measured time; the dominant kernel's entry
     is the roofline object."""
-    suffix = "_fp32" if prec == 1 else "_fp64"
-    tsize = 4 if prec == 1 else 8
-    peak_lin = PEAK_FP32_TFLOPS if prec == 1 else PEAK_FP64_TFLOPS
+    fp32 = prec != 0   # any form but SG_PREC_FP64 runs the direction in FP32
+    suffix = "_fp32" if fp32 else "_fp64"
+    tsize = 4 if fp32 else 8
+    peak_lin = PEAK_FP32_TFLOPS if fp32 else PEAK_FP64_TFLOPS
     int_units = float(np.sum(iters * N_h))           # interval-iterations per solve
     pt_units = float(np.sum(iters * (3 * N_h + 1)))  # point-iterations per solve
     seg = -(-N_h // SEG_LEN)                            # segments per node
@@ -755,7 +780,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "mixed-pair", "fp64"], default="mixed",
+                    help="mixed: FP32 direction, FP64 residual; mixed-pair: the residual in pairs of floats")
     ap.add_argument("--eval", choices=["df32", "fp64", "tf32x3"], default="df32")
     ap.add_argument("--form", choices=["auto", "phase", "phase-graph", "persistent"], default="auto",
                     help="execution form of the solve (auto: the library's autotuner picks)")

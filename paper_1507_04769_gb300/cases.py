@@ -28,7 +28,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["solve", "eval"])
     ap.add_argument("--nodes", type=int, default=1457)
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "mixed-pair"], default="mixed")
     ap.add_argument("--queries", type=int, default=200_000)
     ap.add_argument("--mode", choices=sorted(MODES), default="fp64")
     ap.add_argument("--level", type=int, default=4)
@@ -42,7 +42,7 @@ def main(argv=None):
     x0 = g.coords[:n]
     Td = torch.as_tensor(T[:n], device="cuda")
     Nd = torch.as_tensor(N[:n], dtype=torch.int32, device="cuda")
-    prec = sg.PREC_MIXED if a.precision == "mixed" else sg.PREC_FP64
+    prec = {"mixed": sg.PREC_MIXED, "mixed-pair": sg.PREC_MIXED_PAIR, "fp64": sg.PREC_FP64}[a.precision]
     if a.what == "solve":
         for _ in range(a.repeat):
             res = sg.solve_bvps(prob, x0, Td, Nd, precision=prec, n_max=int(N[:n].max()))

@@ -150,8 +150,13 @@ static const char* intern(const std::string& s) {
   return names.back()->c_str();
 }
 
+// The forms with an FP32 direction (their workspace holds floats).
+static bool fp32_direction(int precision) {
+  return precision == SG_PREC_MIXED || precision == SG_PREC_MIXED_PAIR;
+}
+
 static size_t ws_bytes(int64_t n, int Nmax, int precision) {
-  const size_t tsize = precision == SG_PREC_MIXED ? sizeof(float) : sizeof(double);
+  const size_t tsize = fp32_direction(precision) ? sizeof(float) : sizeof(double);
   return carve(nullptr, n, Nmax, tsize).bytes;
 }
 
@@ -216,7 +221,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
   int rc;
   SG_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), st));
   SG_TIMED("k_init", st, (k_init<<<ginit, 128, 0, st>>>(a, w)));
-  SG_TIMED("k_trial", st, (k_trial<T><<<gi, 128, 0, st>>>(a, w)));
+  SG_TIMED("k_trial", st, (trial_kernel<T>(a)<<<gi, 128, 0, st>>>(a, w)));
   SG_TIMED("k_ls_reduce", st, (k_ls_reduce<<<gnode_warp, 128, 0, st>>>(a, w, 0)));
   SG_LAUNCH_CHECK("init kernels");
   if ((rc = read_counters()) != SG_OK) return rc;
@@ -239,7 +244,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
     SG_LAUNCH_CHECK("newton kernels");
     for (int trial = 0; trial < 12; ++trial) {
       SG_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(int), st));
-      SG_TIMED("k_trial", st, (k_trial<T><<<gi, 128, 0, st>>>(a, w)));
+      SG_TIMED("k_trial", st, (trial_kernel<T>(a)<<<gi, 128, 0, st>>>(a, w)));
       SG_TIMED("k_ls_reduce", st, (k_ls_reduce<<<gnode_warp, 128, 0, st>>>(a, w, 1)));
       SG_LAUNCH_CHECK("line search kernels");
       if ((rc = read_counters()) != SG_OK) return rc;
@@ -347,7 +352,7 @@ static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, dou
   GraphBuilder rb{root, {}};
   rb.memset0(w.counters, 4 * sizeof(int));
   rb.kernel(k_init, static_cast<unsigned>(ceil_div(a.n * P * kInitPer, 128)), 128, 0, a, w);
-  rb.kernel(k_trial<T>, gi, 128, 0, a, w);
+  rb.kernel(trial_kernel<T>(a), gi, 128, 0, a, w);
   rb.kernel(k_ls_reduce, gnw, 128, 0, a, w, 0);
   rb.kernel(k_set_cond, 1, 1, 0, hn, static_cast<const int*>(w.counters + 1));
   cudaGraph_t newton_body;
@@ -381,7 +386,7 @@ static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, dou
 
   GraphBuilder lb{ls_body, {}};
   lb.memset0(w.counters, sizeof(int));
-  lb.kernel(k_trial<T>, gi, 128, 0, a, w);
+  lb.kernel(trial_kernel<T>(a), gi, 128, 0, a, w);
   lb.kernel(k_ls_reduce, gnw, 128, 0, a, w, 1);
   lb.kernel(k_set_cond, 1, 1, 0, hl, static_cast<const int*>(w.counters));
   if (lb.err != cudaSuccess) return lb.err;
@@ -520,7 +525,7 @@ extern "C" int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iter < 0) return fail(SG_EINVAL, "sg_solve_bvps: bad tol or max_iter");
   if (o.warm_start && !d_Y) return fail(SG_EINVAL, "sg_solve_bvps: warm_start needs d_Y");
-  if (o.precision != SG_PREC_FP64 && o.precision != SG_PREC_MIXED)
+  if (o.precision != SG_PREC_FP64 && !fp32_direction(o.precision))
     return fail(SG_EINVAL, "sg_solve_bvps: unknown precision");
   if (reinterpret_cast<uintptr_t>(d_work) % 256 != 0)
     return fail(SG_EINVAL, "sg_solve_bvps: workspace must be 256-byte aligned");
@@ -541,8 +546,9 @@ extern "C" int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t
   a.blocks_per_sm = o.blocks_per_sm;
   a.sync_at_end = 1;
   a.Yin = o.warm_start ? d_Y : nullptr;
+  a.res_pair = o.precision == SG_PREC_MIXED_PAIR ? 1 : 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (o.precision == SG_PREC_MIXED) {
+  if (fp32_direction(o.precision)) {
     Workspace w = carve(d_work, n, n_max_intervals, sizeof(float));
     if (o.graph) return run_solve_graph<float>(a, w, st, d_lambda0, d_u0, d_V, d_status, d_iters, d_Y);
     return run_solve<float>(a, w, st, d_lambda0, d_u0, d_V, d_status, d_iters, d_Y);
@@ -601,7 +607,7 @@ extern "C" int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, 
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iter < 0) return fail(SG_EINVAL, "sg_solve_bvps_static: bad tol or max_iter");
   if (o.warm_start && !d_Y) return fail(SG_EINVAL, "sg_solve_bvps_static: warm_start needs d_Y");
-  if (o.precision != SG_PREC_FP64 && o.precision != SG_PREC_MIXED)
+  if (o.precision != SG_PREC_FP64 && !fp32_direction(o.precision))
     return fail(SG_EINVAL, "sg_solve_bvps_static: unknown precision");
   const size_t need = ws_bytes(n, n_max_intervals, o.precision);
   if (need > SG_STATIC_SCRATCH_BYTES)
@@ -626,11 +632,12 @@ extern "C" int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, 
   a.blocks_per_sm = o.blocks_per_sm;
   a.sync_at_end = 1;
   a.Yin = o.warm_start ? d_Y : nullptr;
+  a.res_pair = o.precision == SG_PREC_MIXED_PAIR ? 1 : 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // Every region the solver reads is written first in this call (k_init sets the
   // iterate, the corrections and the per-node state; the counters are zeroed
   // before each use), so the previous call's contents need no clearing here.
-  if (o.precision == SG_PREC_MIXED) {
+  if (fp32_direction(o.precision)) {
     Workspace w = carve(scratch, n, n_max_intervals, sizeof(float));
     return run_solve<float>(a, w, st, d_lambda0, d_u0, d_V, d_status, d_iters, d_Y);
   }

@@ -99,6 +99,7 @@ struct SolveArgs {
   int blocks_per_sm;   // cap on resident 4-warp blocks per SM for the persistent form (0 = occupancy)
   int sync_at_end;
   const double* Yin;   // initial iterate (n x P x 12), or null for the zero-control guess
+  int res_pair;        // FP32-direction form: 1 = residual in pairs of floats, 0 = in FP64
 };
 
 __host__ __device__ __forceinline__ int64_t npts(int Nmax) { return 3 * int64_t(Nmax) + 1; }
@@ -155,12 +156,12 @@ constexpr int kTrialPts = 3 * kTrialIv + 1;      // 127 points
 
 __host__ __device__ __forceinline__ int trial_chunks(int Nmax) { return (Nmax + kTrialIv - 1) / kTrialIv; }
 
-template <typename T>
+template <typename T, bool kPair>
 __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
-  // FP64 form: points and rows in FP64.  Mixed form: the right-hand side and
-  // the stage rows in pair-of-floats arithmetic (about 48 bits, on the FP32
-  // pipe); the boundary rows and the iterate Y + alpha D stay FP64.
-  constexpr bool kPair = sizeof(T) == sizeof(float);
+  // kPair = false: points and rows in FP64 (the FP64 and mixed forms).
+  // kPair = true (the mixed-pair form): the right-hand side and the stage rows
+  // in pair-of-floats arithmetic (about 48 bits, on the FP32 pipe); the
+  // boundary rows and the iterate Y + alpha D stay FP64.
   __shared__ double ys[kTrialPts][12];   // dfnum in the mixed form (same size)
   __shared__ double fs[kTrialPts][12];
   __shared__ double part_s[3 * kTrialIv][2];
@@ -288,6 +289,14 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
     w.part[2 * t] = ss;
     w.part[2 * t + 1] = mx;
   }
+}
+
+// The residual kernel of a solve: FP64, or pairs of floats in the
+// FP32-direction form when asked for.
+template <typename T>
+inline void (*trial_kernel(const SolveArgs& a))(SolveArgs, Workspace) {
+  if constexpr (sizeof(T) == sizeof(float)) return a.res_pair ? k_trial<float, true> : k_trial<float, false>;
+  else return k_trial<double, false>;
 }
 
 // Warp per node: reduce the partial norms in a fixed order and decide.

@@ -26,16 +26,15 @@ __host__ __device__ constexpr int persist_smem_per_warp() {
 // free during the line search); each lane then forms the stage rows of the
 // intervals lane, lane+32, ..., stores them (precision T) for the next
 // condensation, and the warp reduces |.|_2^2 and |.|_inf in a fixed order.
-template <typename T>
-__device__ __forceinline__ void residual_node(const SolveArgs& a, const Workspace& w, int64_t node, int N,
-                                              double alpha, int lane, double* ss_out, double* mx_out) {
+template <typename T, bool kPair>
+__device__ __forceinline__ void residual_node_t(const SolveArgs& a, const Workspace& w, int64_t node, int N,
+                                                double alpha, int lane, double* ss_out, double* mx_out) {
   const int64_t pb = node * npts(a.Nmax);
   const double* Y = w.Y + pb * 12;
   const double* D = w.D + pb * 12;
   // F at every point (the node's Jacobian slot is free during the line
-  // search); in the mixed form F and the stage rows are pairs of floats, as in
-  // the launch-per-phase residual
-  constexpr bool kPair = sizeof(T) == sizeof(float);
+  // search); with kPair F and the stage rows are pairs of floats, as in the
+  // launch-per-phase residual
   double* Fs = reinterpret_cast<double*>(static_cast<T*>(w.Jm) + pb * 144);
   for (int p = lane; p <= 3 * N; p += 32) {
     if constexpr (kPair) {
@@ -127,6 +126,15 @@ __device__ __forceinline__ void residual_node(const SolveArgs& a, const Workspac
   *ss_out = anybad ? INFINITY : ss;
   *mx_out = anybad ? INFINITY : mx;
   __syncwarp();
+}
+
+template <typename T>
+__device__ __forceinline__ void residual_node(const SolveArgs& a, const Workspace& w, int64_t node, int N,
+                                              double alpha, int lane, double* ss_out, double* mx_out) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (a.res_pair) return residual_node_t<T, true>(a, w, node, N, alpha, lane, ss_out, mx_out);
+  }
+  residual_node_t<T, false>(a, w, node, N, alpha, lane, ss_out, mx_out);
 }
 
 template <typename T>

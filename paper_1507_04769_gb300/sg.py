@@ -17,7 +17,8 @@ from . import build as _build
 # --------------------------------------------------------------- constants
 SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_EUNSUPPORTED = 0, 1, 2, 3, 4
 PROBLEM_ATTITUDE, PROBLEM_LQ, PROBLEM_EXAMPLE3 = 0, 1, 2
-PREC_FP64, PREC_MIXED = 0, 1
+# FP64; FP32 direction with an FP64 residual; FP32 direction with a pair-of-floats residual
+PREC_FP64, PREC_MIXED, PREC_MIXED_PAIR = 0, 1, 2
 CONVERGED, MAXITER, NONFINITE, SINGULAR, BADINPUT = 0, 1, 2, 3, 4
 EVAL_FP64, EVAL_TF32X3, EVAL_DF32 = 0, 1, 2
 

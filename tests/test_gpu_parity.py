@@ -177,8 +177,9 @@ def att_case():
     return params, X0, T, N, _oracle(params, X0, T, N)
 
 
-FORMS = [(sg.PREC_FP64, False), (sg.PREC_MIXED, False), (sg.PREC_FP64, True), (sg.PREC_MIXED, True)]
-FORM_IDS = ["fp64", "mixed", "fp64-persistent", "mixed-persistent"]
+FORMS = [(sg.PREC_FP64, False), (sg.PREC_MIXED, False), (sg.PREC_FP64, True), (sg.PREC_MIXED, True),
+         (sg.PREC_MIXED_PAIR, False), (sg.PREC_MIXED_PAIR, True)]
+FORM_IDS = ["fp64", "mixed", "fp64-persistent", "mixed-persistent", "mixedpair", "mixedpair-persistent"]
 GFORMS = [(p, q, g) for (p, q) in FORMS for g in (False, True)]
 GFORM_IDS = [f"{i}{'-graph' if g else ''}" for i in FORM_IDS for g in (False, True)]
 
