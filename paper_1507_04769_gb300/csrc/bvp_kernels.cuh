@@ -165,8 +165,7 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
   __shared__ double ys[kTrialPts][12];   // dfnum in the mixed form (same size)
   __shared__ double fs[kTrialPts][12];
   __shared__ double part_s[3 * kTrialIv][2];
-  __shared__ double cA_s[3][4];          // h a_kj as pairs (mixed form), k = 1..3
-  __shared__ double h_s;
+  __shared__ double cA_s[3][4];          // h a_kj: a pair (pair residual) or FP64, k = 1..3
   const int tid = threadIdx.x;
   const int nchunk = trial_chunks(a.Nmax);
   const int64_t node = blockIdx.x / nchunk;
@@ -180,12 +179,15 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
   const double alpha = s.alpha;
   const int64_t base = node * npts(a.Nmax) + 3 * int64_t(i0);
   auto ypoint = [&](int64_t pt, int c) { return __fma_rn(alpha, w.D[pt * 12 + c], w.Y[pt * 12 + c]); };
-  // the step and the stage coefficients once per block (the last 12 threads)
+  // the stage coefficients h a_kj once per block (the last 12 threads)
   if (tid >= 128 - 12) {
     const int e = tid - (128 - 12), k = e / 4 + 1, jj = e % 4;
     const double h = a.T[node] / N;
-    if (e == 0) h_s = h;
-    if constexpr (kPair) *reinterpret_cast<dfnum*>(&cA_s[k - 1][jj]) = dfnum(h * kLobA[k][jj]);
+    if constexpr (kPair) {
+      *reinterpret_cast<dfnum*>(&cA_s[k - 1][jj]) = dfnum(h * kLobA[k][jj]);
+    } else {
+      cA_s[k - 1][jj] = h * kLobA[k][jj];
+    }
   }
   if (tid <= 3 * niv) {
     if constexpr (kPair) {
@@ -213,7 +215,6 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
     }
   }
   __syncthreads();
-  const double h = h_s;
   if (tid < 3 * niv) {
     // interval j = tid / 3 of the chunk, stage row block k = tid % 3 + 1
     const int j = tid / 3, k = tid % 3 + 1;
@@ -243,16 +244,26 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
       ss = ssd.to_double();
       mx = mxf;
     } else {
+      const double* cA = cA_s[k - 1];
+      const double c0 = cA[0], c1 = cA[1], c2 = cA[2], c3 = cA[3];
+      // |r|_inf and finiteness from the bit patterns (integer pipe): for
+      // non-negative doubles the bit patterns order like the values, and a
+      // non-finite value has all exponent bits set
+      unsigned long long mxb = 0ull;
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
-        const double r = ys[p0 + k][c] - ys[p0][c] -
-                         h * (kLobA[k][0] * fs[p0][c] + kLobA[k][1] * fs[p0 + 1][c] + kLobA[k][2] * fs[p0 + 2][c] +
-                              kLobA[k][3] * fs[p0 + 3][c]);
+        double r = ys[p0 + k][c] - ys[p0][c];
+        r = fma(-c0, fs[p0][c], r);
+        r = fma(-c1, fs[p0 + 1][c], r);
+        r = fma(-c2, fs[p0 + 2][c], r);
+        r = fma(-c3, fs[p0 + 3][c], r);
         res[c] = static_cast<T>(r);
-        bad = bad || !isfinite(r);
-        ss += r * r;
-        mx = fmax(mx, fabs(r));
+        const unsigned long long ab = static_cast<unsigned long long>(__double_as_longlong(r)) & 0x7FFFFFFFFFFFFFFFull;
+        mxb = ab > mxb ? ab : mxb;
+        ss = fma(r, r, ss);
       }
+      bad = bad || mxb >= 0x7FF0000000000000ull;
+      mx = __longlong_as_double(static_cast<long long>(mxb));
     }
     // boundary rows in FP64 from the iterate itself
     if (k == 1 && i0 + j == 0) {

@@ -89,7 +89,7 @@ __device__ __forceinline__ void dsincos(double a, double* s, double* c) {
   }
 }
 __device__ __forceinline__ void dsincos(float a, float* s, float* c) { sincosf(a, s, c); }
-__device__ __forceinline__ double recip(double a) { return 1.0 / a; }
+__device__ __forceinline__ double recip(double a) { return __drcp_rn(a); }   // = 1.0 / a, without the division path
 __device__ __forceinline__ float recip(float a) { return 1.0f / a; }
 
 template <typename T, int N>
