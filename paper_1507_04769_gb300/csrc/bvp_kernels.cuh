@@ -16,9 +16,9 @@
 //               stage residual rows (the right-hand side of the next
 //               condensation); k_ls_reduce takes the Armijo decision per node
 //               in a fixed reduction order
-// T = double gives the FP64 form, T = float the mixed form (FP32 Jacobian,
-// elimination and direction; pair-of-floats residual, FP64 line search and
-// update).
+// T = double gives the FP64 form, T = float the mixed forms (FP32 Jacobian,
+// elimination and direction; FP64 line search and update; the residual in
+// FP64, or in pairs of floats in the mixed-pair form).
 #pragma once
 
 #include <cmath>
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
   // kPair = true (the mixed-pair form): the right-hand side and the stage rows
   // in pair-of-floats arithmetic (about 48 bits, on the FP32 pipe); the
   // boundary rows and the iterate Y + alpha D stay FP64.
-  __shared__ double ys[kTrialPts][12];   // dfnum in the mixed form (same size)
+  __shared__ double ys[kTrialPts][12];   // dfnum in the mixed-pair form (same size)
   __shared__ double fs[kTrialPts][12];
   __shared__ double part_s[3 * kTrialIv][2];
   __shared__ double cA_s[3][4];          // h a_kj: a pair (pair residual) or FP64, k = 1..3

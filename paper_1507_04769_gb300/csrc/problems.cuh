@@ -38,7 +38,7 @@ struct DevProblem {
   double R[9];
   double Bu[18];  // plant input matrix: attitude J^-1 B (rows 3..5 of a 6 x 3), LQ B (6 x 3)
   // the constants of the right-hand side as (hi, lo) float pairs, for the
-  // pair-of-floats residual of the mixed form (filled on the host)
+  // pair-of-floats residual of the mixed-pair form (filled on the host)
   float2 Jinv_f[3], hm_f[3], Kw_f[9], wv_f, ww_f;
   float2 A_f[36], K_f[36], Q_f[36];
 };
@@ -327,7 +327,7 @@ __device__ __forceinline__ void ex3_char(const S* x, const S* lam, S* dx, S* dl)
 
 // ------------------------------------------------------------------ RHS and Jacobian
 // F(y) for y = (x, lambda) in the number type S: double (FP64) or dfnum
-// (pair of floats, the residual of the mixed form).
+// (pair of floats, the residual of the mixed-pair form).
 template <typename S>
 __device__ __forceinline__ void char_rhs_t(const DevProblem& P, const S* y, S* F, const double* ve = nullptr) {
   if (P.kind == SG_PROBLEM_EXAMPLE3) {
