@@ -167,6 +167,11 @@ int sg_grid_info(const sg_grid* g, int64_t* n_nodes, int* d, int* level,
                  const double** d_coords, const int8_t** d_levels, const int16_t** d_index);
 void sg_grid_free(sg_grid* g);
 
+/* Bytes of solver workspace for n nodes of at most n_max_intervals intervals
+ * in the given precision (MIXED and MIXED_PAIR need the same); 0 for n < 0,
+ * n_max_intervals < 1 or an unknown precision.  Host arithmetic, no GPU. */
+size_t sg_solve_workspace_bytes(int64_t n, int n_max_intervals, int precision);
+
 /* ---------------------------------------------------------------- Step II
  * sg_solve_bvps - solve the characteristic BVP of Eq. hamchar at n initial states,
  *   x' = H_lambda', lambda' = -H_x', x(0) = x0, lambda(T) = grad h(x(T)),
@@ -193,7 +198,6 @@ void sg_grid_free(sg_grid* g);
  * The call returns when every node has converged or hit max_iter (the host
  * reads one counter per iteration), so it synchronises `stream`.
  * Errors: SG_EINVAL (sizes, workspace too small, misaligned), SG_ECUDA. */
-size_t sg_solve_workspace_bytes(int64_t n, int n_max_intervals, int precision);
 int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t n,
                   const double* d_T, const int32_t* d_N, int n_max_intervals,
                   const sg_solve_opts* opts, void* d_work, size_t work_bytes,

@@ -505,6 +505,7 @@ using namespace sg;
 
 extern "C" size_t sg_solve_workspace_bytes(int64_t n, int n_max_intervals, int precision) {
   if (n < 0 || n_max_intervals < 1) return 0;
+  if (precision != SG_PREC_FP64 && !fp32_direction(precision)) return 0;
   return ws_bytes(n, n_max_intervals, precision);
 }
 

@@ -56,5 +56,8 @@ def test_workspace_size_grows_with_problem(lib):
     a = sg.workspace_bytes(10, 64, sg.PREC_FP64)
     b = sg.workspace_bytes(20, 64, sg.PREC_FP64)
     c = sg.workspace_bytes(10, 64, sg.PREC_MIXED)
+    # the two FP32-direction forms share the layout; an unknown precision sizes nothing
+    assert sg.workspace_bytes(10, 64, sg.PREC_MIXED_PAIR) == c
+    assert sg.workspace_bytes(10, 64, 7) == 0
     assert 0 < a < b and c < a
     assert sg.workspace_bytes(10, 0, 0) == 0

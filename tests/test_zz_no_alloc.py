@@ -47,7 +47,7 @@ def _static_solve(problem, x0, T, N, n_max, precision):
     return rc, out
 
 
-@pytest.mark.parametrize("precision", [sg.PREC_FP64, sg.PREC_MIXED])
+@pytest.mark.parametrize("precision", [sg.PREC_FP64, sg.PREC_MIXED, sg.PREC_MIXED_PAIR])
 def test_static_solve_matches_workspace_solve_twice(precision):
     problem = sg.problem_from(synth.attitude_params(0))
     lo, hi = synth.box(6)
