@@ -524,7 +524,7 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
     const T piv = __shfl_sync(0xffffffffu, r[k], p);
     const bool good = piv != T(0) && isfinite(piv);
     ok = ok && good;
-    const T inv = good ? T(1) / piv : T(0);
+    const T inv = good ? recip_rn(piv) : T(0);
     const bool is_p = lane == p;
     const T l = (cand && !done && !is_p) ? r[k] * inv : T(0);
 #pragma unroll
@@ -814,7 +814,7 @@ __device__ __forceinline__ void condense_interval_smem(const SolveArgs& a, const
   for (int e = lane; e < 24 * kCols; e += 32) rec[(e / kCols) * kRecLd + e % kCols] = M[e];
   if (lane < 24) {
     const double pv = M[lane * kCols + lane];
-    rec[lane * kRecLd + kRecInv] = (pv != 0.0 && isfinite(pv)) ? 1.0 / pv : 0.0;
+    rec[lane * kRecLd + kRecInv] = (pv != 0.0 && isfinite(pv)) ? recip_rn(pv) : 0.0;
   }
   double* cond = static_cast<double*>(w.Cond) + blk * kBlk;
   for (int e = lane; e < 12 * 25; e += 32) {

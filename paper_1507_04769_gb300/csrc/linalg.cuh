@@ -5,6 +5,11 @@
 
 namespace sg {
 
+// Correctly rounded reciprocal: the value of 1 / x without the division's
+// slow path.
+__device__ __forceinline__ float lin_recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double lin_recip(double x) { return __drcp_rn(x); }
+
 template <typename T>
 __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 
@@ -49,7 +54,7 @@ __device__ bool warp_eliminate(T* M, int lane) {
       }
     }
     __syncwarp();
-    const T inv = good ? T(1) / M[k * C + k] : T(0);
+    const T inv = good ? lin_recip(M[k * C + k]) : T(0);
     for (int r = k + 1 + lane; r < R; r += 32) M[r * C + k] *= inv;
     __syncwarp();
     const int nr = R - k - 1, nc = C - k - 1;
