@@ -475,23 +475,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
 
-// 37-entry rows (F | Y | Z | rhs) as 40-entry vectors (16-byte accesses).
-template <typename T>
-__device__ __forceinline__ void store_row40(T* __restrict__ dst, const T (&r)[37]) {
-  if constexpr (sizeof(T) == 4) {
-    float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) d4[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
-    d4[9] = make_float4(r[36], 0.0f, 0.0f, 0.0f);
-  } else {
-    double2* d2 = reinterpret_cast<double2*>(dst);
-#pragma unroll
-    for (int q = 0; q < 18; ++q) d2[q] = make_double2(r[2 * q], r[2 * q + 1]);
-    d2[18] = make_double2(r[36], 0.0);
-    d2[19] = make_double2(0.0, 0.0);
-  }
-}
-
+// 40-entry rows (F | Y | Z | rhs and padding) loaded as 16-byte vectors.
 template <typename T>
 __device__ __forceinline__ void load_row40(const T* __restrict__ src, T (&r)[40]) {
   if constexpr (sizeof(T) == 4) {
