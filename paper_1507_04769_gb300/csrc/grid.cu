@@ -1,6 +1,7 @@
 // Step I: Smolyak sparse grid on nested Chebyshev-Gauss-Lobatto sets
 // (Section 3.2, Eq. CGL).  The multi-index enumeration is integer work done
 // once on the host; node coordinates are computed on the device.
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -110,25 +111,41 @@ extern "C" int sg_build_grid(int d, int level, const double* h_lo, const double*
   g->h_hi.assign(h_hi, h_hi + d);
   const int64_t total = g->M * d;
 
-  double* d_box = nullptr;
+  // one device allocation (coordinates, levels, indices, box); the host-made
+  // parts go in with one copy
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t ocoords = take(total * sizeof(double));
+  const size_t ohost = off;
+  const size_t obox = take(2 * d * sizeof(double)), olev = take(total * sizeof(int8_t));
+  const size_t okidx = take(total * sizeof(int16_t));
   auto cleanup = [&](int code, const char* what, cudaError_t e) {
-    if (d_box) cudaFree(d_box);
     sg_grid_free(g);
     return e == cudaSuccess ? fail(code, what) : cuda_fail(e, what);
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&g->coords, total * sizeof(double))) != cudaSuccess) return cleanup(SG_ENOMEM, "cudaMalloc coords", e);
-  if ((e = cudaMalloc(&g->lev, total * sizeof(int8_t))) != cudaSuccess) return cleanup(SG_ENOMEM, "cudaMalloc levels", e);
-  if ((e = cudaMalloc(&g->kidx, total * sizeof(int16_t))) != cudaSuccess) return cleanup(SG_ENOMEM, "cudaMalloc index", e);
-  if ((e = cudaMalloc(&d_box, 2 * d * sizeof(double))) != cudaSuccess) return cleanup(SG_ENOMEM, "cudaMalloc box", e);
-  if ((e = cudaMemcpy(g->lev, g->h_lev.data(), total, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(SG_ECUDA, "copy levels", e);
-  if ((e = cudaMemcpy(g->kidx, g->h_kidx.data(), total * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(SG_ECUDA, "copy index", e);
-  if ((e = cudaMemcpy(d_box, h_lo, d * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(SG_ECUDA, "copy lo", e);
-  if ((e = cudaMemcpy(d_box + d, h_hi, d * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup(SG_ECUDA, "copy hi", e);
+  if ((e = cudaMalloc(&g->block, off)) != cudaSuccess) return cleanup(SG_ENOMEM, "cudaMalloc grid", e);
+  char* base = static_cast<char*>(g->block);
+  g->coords = reinterpret_cast<double*>(base + ocoords);
+  g->lev = reinterpret_cast<int8_t*>(base + olev);
+  g->kidx = reinterpret_cast<int16_t*>(base + okidx);
+  double* d_box = reinterpret_cast<double*>(base + obox);
+  {
+    std::vector<unsigned char> h(off - ohost);
+    std::memcpy(h.data() + (obox - ohost), h_lo, d * sizeof(double));
+    std::memcpy(h.data() + (obox - ohost) + d * sizeof(double), h_hi, d * sizeof(double));
+    std::memcpy(h.data() + (olev - ohost), g->h_lev.data(), total * sizeof(int8_t));
+    std::memcpy(h.data() + (okidx - ohost), g->h_kidx.data(), total * sizeof(int16_t));
+    if ((e = cudaMemcpy(base + ohost, h.data(), off - ohost, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cleanup(SG_ECUDA, "copy grid tables", e);
+  }
   SG_TIMED("grid_coords_kernel", nullptr, (grid_coords_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256>>>(total, d, g->lev, g->kidx, d_box, d_box + d, g->coords)));
   if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(SG_ECUDA, "grid_coords_kernel launch", e);
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup(SG_ECUDA, "grid_coords_kernel", e);
-  cudaFree(d_box);
   *out = g;
   return SG_OK;
 }
@@ -148,8 +165,6 @@ extern "C" int sg_grid_info(const sg_grid* g, int64_t* n_nodes, int* d, int* lev
 
 extern "C" void sg_grid_free(sg_grid* g) {
   if (!g) return;
-  if (g->coords) cudaFree(g->coords);
-  if (g->lev) cudaFree(g->lev);
-  if (g->kidx) cudaFree(g->kidx);
+  if (g->block) cudaFree(g->block);
   delete g;
 }

@@ -12,6 +12,7 @@ struct sg_grid {
   double* coords = nullptr;   // device, M x d
   int8_t* lev = nullptr;      // device, M x d
   int16_t* kidx = nullptr;    // device, M x d
+  void* block = nullptr;      // the one device allocation the arrays above live in
   std::vector<int8_t> h_lev;  // host copies of the integer structure
   std::vector<int16_t> h_kidx;
   std::vector<double> h_lo, h_hi;

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -315,44 +316,66 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   // grp[a] = first node with at least a active dimensions (non-decreasing)
   for (int a = kMaxDim; a >= 0; --a) s->grp[a] = s->grp[a] < s->grp[a + 1] ? s->grp[a] : s->grp[a + 1];
 
-  uint16_t* d_fid = nullptr;
-  int16_t* d_fpt = nullptr;
-  double* d_tab1 = nullptr;
-  int32_t* d_order = nullptr;
-  auto cleanup = [&](cudaError_t e, const char* what) {
-    if (d_fid) cudaFree(d_fid);
-    if (d_fpt) cudaFree(d_fpt);
-    if (d_tab1) cudaFree(d_tab1);
-    if (d_order) cudaFree(d_order);
-    sg_surplus_free(s);
-    return e == cudaErrorMemoryAllocation ? fail(SG_ENOMEM, what) : cuda_fail(e, what);
+  // one device allocation: the surplus's arrays and the build's tables; the
+  // host-made tables go in with one copy
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
   };
-  cudaError_t e;
+  const size_t oW = take(M * k * sizeof(double)), oWs = take(M * k * sizeof(double));
+  const size_t oWdf = take(M * k * sizeof(float2)), oxf = take((fine_n + 1) * sizeof(double));
+  const size_t oxfdf = take((fine_n + 1) * sizeof(float2));
+  const size_t otab1 = take(size_t(s->nf) * (fine_n + 1) * sizeof(double));
+  const size_t npack = tf32_pack_floats(M, k);
+  const size_t obp = take(npack * sizeof(float)), oerr = take(sizeof(int));
+  const size_t ohost = off;
+  const size_t obox = take(2 * d * sizeof(double)), onact = take(M), oops = take(M * kMaxDim * sizeof(uint16_t));
+  const size_t ofid = take(M * d * sizeof(uint16_t)), ofpt = take(M * d * sizeof(int16_t));
+  const size_t oorder = take(M * sizeof(int32_t));
+  cudaError_t e = cudaMalloc(&s->block, off);
+  if (e != cudaSuccess) {
+    delete s;
+    return e == cudaErrorMemoryAllocation ? fail(SG_ENOMEM, "sg_build_surpluses: cudaMalloc") : cuda_fail(e, "sg_build_surpluses: cudaMalloc");
+  }
+  char* base = static_cast<char*>(s->block);
+  s->W = reinterpret_cast<double*>(base + oW);
+  s->Ws = reinterpret_cast<double*>(base + oWs);
+  s->Wdf = reinterpret_cast<float2*>(base + oWdf);
+  s->xf = reinterpret_cast<double*>(base + oxf);
+  s->xfdf = reinterpret_cast<float2*>(base + oxfdf);
+  s->bpack = npack ? reinterpret_cast<float*>(base + obp) : nullptr;
+  s->tc_err = reinterpret_cast<int*>(base + oerr);
+  s->box = reinterpret_cast<double*>(base + obox);
+  s->nact = reinterpret_cast<uint8_t*>(base + onact);
+  s->ops = reinterpret_cast<uint16_t*>(base + oops);
+  auto* d_fid = reinterpret_cast<uint16_t*>(base + ofid);
+  auto* d_fpt = reinterpret_cast<int16_t*>(base + ofpt);
+  auto* d_tab1 = reinterpret_cast<double*>(base + otab1);
+  auto* d_order = reinterpret_cast<int32_t*>(base + oorder);
+  auto cleanup = [&](cudaError_t err, const char* what) {
+    sg_surplus_free(s);
+    return err == cudaErrorMemoryAllocation ? fail(SG_ENOMEM, what) : cuda_fail(err, what);
+  };
 #define SG_TRY_CLEAN(expr)                                  \
   if ((e = (expr)) != cudaSuccess) return cleanup(e, #expr);
-  SG_TRY_CLEAN(cudaMalloc(&s->W, M * k * sizeof(double)));
-  SG_TRY_CLEAN(cudaMalloc(&s->Ws, M * k * sizeof(double)));
-  SG_TRY_CLEAN(cudaMalloc(&s->nact, M));
-  SG_TRY_CLEAN(cudaMalloc(&s->ops, M * kMaxDim * sizeof(uint16_t)));
-  SG_TRY_CLEAN(cudaMalloc(&s->box, 2 * d * sizeof(double)));
-  SG_TRY_CLEAN(cudaMalloc(&s->xf, (fine_n + 1) * sizeof(double)));
-  SG_TRY_CLEAN(cudaMalloc(&s->xfdf, (fine_n + 1) * sizeof(float2)));
-  SG_TRY_CLEAN(cudaMalloc(&s->Wdf, M * k * sizeof(float2)));
-  SG_TRY_CLEAN(cudaMalloc(&d_fid, M * d * sizeof(uint16_t)));
-  SG_TRY_CLEAN(cudaMalloc(&d_fpt, M * d * sizeof(int16_t)));
-  SG_TRY_CLEAN(cudaMalloc(&d_tab1, size_t(s->nf) * (fine_n + 1) * sizeof(double)));
-  SG_TRY_CLEAN(cudaMalloc(&d_order, M * sizeof(int32_t)));
-  std::vector<double> box(2 * d);
-  for (int dim = 0; dim < d; ++dim) {
-    box[dim] = g->h_lo[dim];
-    box[d + dim] = g->h_hi[dim] - g->h_lo[dim];
+  {
+    std::vector<unsigned char> h(off - ohost);
+    std::vector<double> box(2 * d);
+    for (int dim = 0; dim < d; ++dim) {
+      box[dim] = g->h_lo[dim];
+      box[d + dim] = g->h_hi[dim] - g->h_lo[dim];
+    }
+    std::memcpy(h.data() + (obox - ohost), box.data(), 2 * d * sizeof(double));
+    std::memcpy(h.data() + (onact - ohost), nact.data(), M);
+    std::memcpy(h.data() + (oops - ohost), ops.data(), M * kMaxDim * sizeof(uint16_t));
+    std::memcpy(h.data() + (ofid - ohost), fid.data(), M * d * sizeof(uint16_t));
+    std::memcpy(h.data() + (ofpt - ohost), fpt.data(), M * d * sizeof(int16_t));
+    std::memcpy(h.data() + (oorder - ohost), order.data(), M * sizeof(int32_t));
+    // (a copy from pageable memory is staged before the call returns)
+    SG_TRY_CLEAN(cudaMemcpyAsync(base + ohost, h.data(), off - ohost, cudaMemcpyHostToDevice, st));
   }
-  SG_TRY_CLEAN(cudaMemcpyAsync(s->box, box.data(), 2 * d * sizeof(double), cudaMemcpyHostToDevice, st));
-  SG_TRY_CLEAN(cudaMemcpyAsync(d_fid, fid.data(), M * d * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
-  SG_TRY_CLEAN(cudaMemcpyAsync(d_fpt, fpt.data(), M * d * sizeof(int16_t), cudaMemcpyHostToDevice, st));
-  SG_TRY_CLEAN(cudaMemcpyAsync(s->nact, nact.data(), M, cudaMemcpyHostToDevice, st));
-  SG_TRY_CLEAN(cudaMemcpyAsync(s->ops, ops.data(), M * kMaxDim * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
-  SG_TRY_CLEAN(cudaMemcpyAsync(d_order, order.data(), M * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   SG_TIMED("k_fine_coords", st, (k_fine_coords<<<static_cast<unsigned>(ceil_div(fine_n + 1, 64)), 64, 0, st>>>(L, s->xf)));
   SG_TIMED("k_fine_table", st, (k_fine_table<<<static_cast<unsigned>(ceil_div(fine_n + 1, 64)), 64, 0, st>>>(L, s->xf, d_tab1)));
   SG_TRY_CLEAN(cudaGetLastError());
@@ -371,10 +394,6 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   if (pack_tf32(s, st) != SG_OK) return cleanup(cudaGetLastError(), "pack_tf32");
   SG_TRY_CLEAN(cudaStreamSynchronize(st));
 #undef SG_TRY_CLEAN
-  cudaFree(d_fid);
-  cudaFree(d_fpt);
-  cudaFree(d_tab1);
-  cudaFree(d_order);
   *out = s;
   return SG_OK;
 }
@@ -390,16 +409,7 @@ extern "C" int sg_surplus_info(const sg_surplus* s, int64_t* n_nodes, int* k, co
 
 extern "C" void sg_surplus_free(sg_surplus* s) {
   if (!s) return;
-  if (s->W) cudaFree(s->W);
-  if (s->Ws) cudaFree(s->Ws);
-  if (s->nact) cudaFree(s->nact);
-  if (s->ops) cudaFree(s->ops);
-  if (s->box) cudaFree(s->box);
-  if (s->xf) cudaFree(s->xf);
-  if (s->xfdf) cudaFree(s->xfdf);
-  if (s->Wdf) cudaFree(s->Wdf);
-  if (s->bpack) cudaFree(s->bpack);
-  if (s->tc_err) cudaFree(s->tc_err);
+  if (s->block) cudaFree(s->block);
   delete s;
 }
 

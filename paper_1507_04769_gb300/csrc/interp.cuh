@@ -52,11 +52,13 @@ struct sg_surplus {
   float* bpack = nullptr;         // split-TF32 [W_hi|W_lo], [W_hi|0] per 32-node chunk (k <= 8)
   int tc_chunks = 0;
   int* tc_err = nullptr;          // set by the tensor-core kernel if a wait timed out
+  void* block = nullptr;          // the one device allocation all the arrays above live in
 };
 
 namespace sg {
 int eval_tf32x3(const EvalArgs& e, const sg_surplus* s, cudaStream_t st);
 int eval_df32(const EvalArgs& e, int d, cudaStream_t st);
 int split_df(int64_t n, const double* src, float2* dst, cudaStream_t st);
+size_t tf32_pack_floats(int64_t M, int k);   // floats of the split-TF32 pack (0 for k > 8)
 int pack_tf32(sg_surplus* s, cudaStream_t st);
 }

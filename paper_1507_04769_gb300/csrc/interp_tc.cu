@@ -294,13 +294,18 @@ __global__ void k_pack_tf32(int64_t M, int k, int nchunks, const double* __restr
   bp[size_t(c) * kTcBPack + kTcBBytes / 4 + off] = b2;
 }
 
+size_t tf32_pack_floats(int64_t M, int k) {
+  if (k > kTcN / 2) return 0;   // the tensor-core path serves k <= 8
+  return size_t(ceil_div(M, kTcChunk)) * kTcBPack;
+}
+
+// s->bpack (tf32_pack_floats(M, k) floats) and s->tc_err come with the
+// surplus's allocation.
 int pack_tf32(sg_surplus* s, cudaStream_t st) {
   if (s->k > kTcN / 2) return SG_OK;   // the tensor-core path serves k <= 8
   const int nchunks = static_cast<int>(ceil_div(s->M, kTcChunk));
   s->tc_chunks = nchunks;
-  cudaError_t e = cudaMalloc(&s->bpack, size_t(nchunks) * kTcBPack * sizeof(float));
-  if (e != cudaSuccess) return cuda_fail(e, "pack_tf32: cudaMalloc");
-  if ((e = cudaMalloc(&s->tc_err, sizeof(int))) != cudaSuccess) return cuda_fail(e, "pack_tf32: cudaMalloc");
+  cudaError_t e;
   if ((e = cudaMemsetAsync(s->tc_err, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "pack_tf32: memset");
   const int64_t total = int64_t(nchunks) * kTcChunk * kTcN;
   SG_TIMED("k_pack_tf32", st,
