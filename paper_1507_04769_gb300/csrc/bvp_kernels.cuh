@@ -156,6 +156,28 @@ constexpr int kTrialPts = 3 * kTrialIv + 1;      // 127 points
 
 __host__ __device__ __forceinline__ int trial_chunks(int Nmax) { return (Nmax + kTrialIv - 1) / kTrialIv; }
 
+// A residual row entry in the precision of the Newton direction.  For FP32
+// the double is truncated to 24 significant bits from its bit pattern (the
+// integer pipe; the rounding of the FP32 direction's input does not matter,
+// and the conversion instruction would run on the FP64 pipe, which the FP64
+// residual saturates).  Below the FP32 normal range it becomes a signed zero;
+// above it, infinity; a NaN stays a NaN.
+template <typename T>
+__device__ __forceinline__ T narrow_row(double x) {
+  if constexpr (sizeof(T) == sizeof(double)) {
+    return x;
+  } else {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
+    const unsigned e = (hi >> 20) & 0x7FFu, sign = hi & 0x80000000u;
+    if (e >= 897u && e <= 1150u)
+      return __uint_as_float(sign | (((hi & 0x7FFFFFFFu) - 0x38000000u) << 3) | (lo >> 29));
+    if (e < 897u) return __uint_as_float(sign);
+    if (e == 0x7FFu && ((hi & 0xFFFFFu) | lo) != 0u) return __uint_as_float(0x7FC00000u);
+    return __uint_as_float(sign | 0x7F800000u);
+  }
+}
+
 template <typename T, bool kPair>
 __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
   // kPair = false: points and rows in FP64 (the FP64 and mixed forms).
@@ -257,7 +279,7 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
         r = fma(-c1, fs[p0 + 1][c], r);
         r = fma(-c2, fs[p0 + 2][c], r);
         r = fma(-c3, fs[p0 + 3][c], r);
-        res[c] = static_cast<T>(r);
+        res[c] = narrow_row<T>(r);
         const unsigned long long ab = static_cast<unsigned long long>(__double_as_longlong(r)) & 0x7FFFFFFFFFFFFFFFull;
         mxb = ab > mxb ? ab : mxb;
         ss = fma(r, r, ss);
