@@ -47,7 +47,8 @@ def test_grid_matches_oracle(d, L):
 
 
 # ------------------------------------------------------------------ surpluses + eval
-@pytest.mark.parametrize("d,L,k", [(6, 2, 3), (6, 3, 1), (3, 5, 2), (2, 6, 4), (1, 7, 1), (6, 0, 2)])
+@pytest.mark.parametrize("d,L,k", [(6, 2, 3), (6, 3, 1), (3, 5, 2), (2, 6, 4), (1, 7, 1), (6, 0, 2),
+                                   (4, 3, 6), (2, 4, 16)])   # k > 4: the kernel's wide-output form
 def test_surpluses_match_oracle(d, L, k):
     lo, hi = synth.box(d)
     g = sg.Grid(d, L, lo, hi)
