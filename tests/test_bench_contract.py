@@ -89,3 +89,35 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["e2e"]["value"] == line["value"]
+
+
+def test_roofline_arithmetic_on_synthetic_kernel_times():
+    """The bench's roofline object: the top modelled kernel, achieved = its
+    algorithmic work / its time, frac = achieved / peak, and the DRAM traffic
+    per launch from the captured bytes per interval."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    iters = np.array([5, 6, 4])
+    N_h = np.array([64, 128, 256])
+    M = 3
+    int_units = float(np.sum(iters * N_h))
+    # one timed step: 6 condensation launches in 12 ms, the outputs kernel once
+    kt = {"k_condense_reg_fp32": (12.0, 6), "k_recover_fp32": (3.0, 6), "k_outputs": (0.1, 1),
+          "k_ls_begin": (0.2, 6)}
+    for prec in (1, 2):   # both FP32-direction forms
+        roof, kernels = bench.roofline(kt, iters, N_h, M, prec)
+        assert roof["kernel"] == "k_condense_reg_fp32" and roof["bound"] == "alu"
+        work = bench.flops_condense_interval() * int_units
+        assert abs(roof["achieved"] - work / 12e-3 / 1e12) <= 1e-9 * roof["achieved"]
+        assert roof["peak"] == bench.PEAK_FP32_TFLOPS
+        assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) <= 1e-12
+        per_unit, kind = bench.DRAM_BYTES_PER_UNIT["k_condense_reg_fp32"]
+        assert kind == "interval" and abs(roof["traffic"] - per_unit * int_units / 6) <= 1e-6 * roof["traffic"]
+        assert abs(sum(k["share"] for k in kernels.values()) - 1.0) <= 1e-12
+        assert "achieved" not in kernels["k_ls_begin"]   # unmodelled kernels carry time and share only
+    # the FP64 form takes the FP64 kernels' models and peak
+    kt64 = {"k_condense_smem_fp64": (70.0, 6), "k_outputs": (0.1, 1)}
+    roof64, _ = bench.roofline(kt64, iters, N_h, M, 0)
+    assert roof64["kernel"] == "k_condense_smem_fp64" and roof64["peak"] == bench.PEAK_FP64_TFLOPS
+    assert roof64["traffic"] is None
