@@ -223,10 +223,15 @@ int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t n,
  *   - The first call on each device looks up the array's device address with
  *     cudaGetSymbolAddress (with that device current) and caches it; make that
  *     first call before any stream capture begins on the device.
+ *     The cached address belongs to the device's context: do not call this
+ *     entry point again after cudaDeviceReset on that device.
  *   - All calls on a device share the one array, which keeps the last call's
  *     contents.  The solver writes every region before reading it, so no
  *     clearing is needed, but calls that overlap on the GPU (concurrent streams
  *     or host threads) race on the array: serialise them.
+ *   - opts->graph must be 0 (SG_EINVAL otherwise): the library's graph form
+ *     instantiates CUDA graphs, and instantiation allocates.  The host-loop
+ *     form and the persistent form (opts->persistent) are both available.
  * Errors: SG_EINVAL, SG_EUNSUPPORTED (device ordinal above 63), SG_ECUDA. */
 #define SG_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, int64_t n,
@@ -353,6 +358,8 @@ int sg_theorem1_bound(int d, int q, double* bound);
  *   d_xT    ntraj x 6 final states;  d_cost ntraj accumulated costs z(T)
  *   d_traj  NULL or ntraj x (nsteps+1) x 6 states;  d_ctrl NULL or
  *           ntraj x nsteps x 3 held controls
+ * The running cost is that of the problem with no target attitude: an
+ * attitude problem with d_target set is rejected (SG_EINVAL).
  * One warp per trajectory.  Asynchronous on `stream`.  Errors: SG_EINVAL, SG_ECUDA. */
 int sg_simulate_closed_loop(const sg_problem* prob, const sg_surplus* s, const double* d_x0,
                             int64_t ntraj, int nsteps, double dt, int mode, double* d_xT,

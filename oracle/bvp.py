@@ -126,6 +126,16 @@ def outputs(prob, Y, T, N):
     return lam0, u0, V
 
 
+def newton_correction(prob, Y, x0, T, N):
+    """The full Newton step D = -J(Y)^-1 F(Y) at an iterate Y, shape (3N+1, 12).
+    Near a root Y* of the collocation system, Y + D - Y* = O(|Y - Y*|^2), so
+    |D| measures how far Y is from the discrete root (used to bound the error
+    of a solve stopped at a residual tolerance)."""
+    F = residual(prob, Y, x0, T, N)
+    D = solve_banded((LBW, UBW), jacobian_banded(prob, Y, T, N), -F)
+    return D.reshape(Y.shape)
+
+
 def solve(prob, x0, T, N, tol=1e-8, max_iter=50, polish=True, Y0=None):
     """Newton on the full collocation system.  Returns a Solution."""
     x0 = np.asarray(x0, dtype=np.float64)

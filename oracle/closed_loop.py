@@ -27,9 +27,12 @@ def plant_rhs(prob, x, u):
 
 
 def running_cost_xu(prob, x, u):
+    """L(x, u) for a given control u (the running cost of problems.py, whose
+    running_cost takes u = u*(x, lambda))."""
     if hasattr(prob, "Jinv"):
         p = prob.p
-        return 0.5 * (p.wv * x[:3] @ x[:3] + p.ww * x[3:6] @ x[3:6] + p.r * u @ u)
+        dv = x[:3] - prob.target
+        return 0.5 * (p.wv * dv @ dv + p.ww * x[3:6] @ x[3:6] + p.r * u @ u)
     return 0.5 * (x @ prob.Q @ x + u @ prob.R @ u)
 
 

@@ -347,54 +347,48 @@ def reachable_normal(B):
     return c / np.linalg.norm(c)
 
 
-def target_attitude(params, x0, guesses=None):
+def euler_321(R):
+    """The angles v = (phi, theta, psi) with rot(v) = R, |theta| < pi/2.
+    From R = Rx(phi) Ry(theta) Rz(psi): R[0, 2] = -sin theta,
+    R[0, :2] = cos theta (cos psi, sin psi), R[1:, 2] = cos theta (sin phi, cos phi)."""
+    return np.array([np.arctan2(R[1, 2], R[2, 2]), -np.arcsin(R[0, 2]), np.arctan2(R[0, 1], R[0, 0])])
+
+
+def target_attitude(params, x0):
     """Eq. optim_attitude: v_e = argmax tr R(v) subject to
-    -C' R(v) H = C' (J w0 - R(v0) H), by SLSQP from several starts (the
-    largest trace wins).  x0 = (v0, w0)."""
-    from scipy.optimize import minimize
+    -C' R(v) H = C' (J w0 - R(v0) H), x0 = (v0, w0); NaN when no rotation
+    satisfies the constraint.
+
+    Solved in closed form from the geometry of rotations, not by an iterative
+    optimiser.  tr R = 1 + 2 cos(a), a the rotation angle of R, so the maximum
+    is the rotation of smallest angle in the feasible set.  The constraint
+    fixes the component along C of the body-frame vector R h, h = H / |H|:
+    C' R h = kappa = -C' (J w0 - R(v0) H) / |H|.  A rotation taking h to a unit
+    vector t turns through at least the angle between h and t, and the turn
+    about h x t attains it.  So the optimum takes h to the point t of the
+    circle {t : |t| = 1, C't = kappa} nearest to h, which lies in the plane of
+    C and h:  t = kappa C + sqrt(1 - kappa^2) p / |p|,  p = h - (C'h) C,
+    and R is the rotation about h x t by the angle between h and t
+    (Rodrigues' formula).  v_e are its 3-2-1 angles."""
     B = np.asarray(params.B, dtype=np.float64)
     J = np.asarray(params.J, dtype=np.float64)
     H = np.asarray(params.hmom, dtype=np.float64)
     C = reachable_normal(B)
     v0, w0 = np.asarray(x0[:3], dtype=np.float64), np.asarray(x0[3:6], dtype=np.float64)
-    rhs = C @ (J * w0 - rot(v0) @ H)
-    cons = {"type": "eq", "fun": lambda v: -C @ rot(v) @ H - rhs}
-    best = None
-    for g in (guesses if guesses is not None else (v0, np.zeros(3))):
-        r = minimize(lambda v: -np.trace(rot(v)), np.asarray(g, dtype=np.float64), constraints=[cons],
-                     method="SLSQP", tol=1e-15, options={"maxiter": 500})
-        if r.success and abs(cons["fun"](r.x)) < 1e-10 and (best is None or r.fun < best.fun):
-            best = r
-    # SLSQP stops on the flat top of tr R about 1e-8 from the maximiser; a few
-    # Newton steps on the optimality conditions (complex-step gradients,
-    # Hessians by central differences of them) finish it
-    def grad(fun, v):
-        g = np.empty(3)
-        for i in range(3):
-            vc = v.astype(np.complex128)
-            vc[i] += 1e-30j
-            g[i] = fun(vc).imag / 1e-30
-        return g
-
-    ftr = lambda v: rot(v)[0, 0] + rot(v)[1, 1] + rot(v)[2, 2]
-    fc = lambda v: -C @ rot(v) @ H - rhs
-    v = best.x.copy()
-    gc = grad(fc, v)
-    mu = -grad(ftr, v) @ gc / (gc @ gc)
-    for _ in range(8):
-        res = np.concatenate([grad(ftr, v) + mu * grad(fc, v), [fc(v).real]])
-        K = np.zeros((4, 4))
-        for j in range(3):
-            e = np.zeros(3)
-            e[j] = 1e-6
-            K[:3, j] = ((grad(ftr, v + e) + mu * grad(fc, v + e)) - (grad(ftr, v - e) + mu * grad(fc, v - e))) / 2e-6
-        gc = grad(fc, v)
-        K[:3, 3] = gc
-        K[3, :3] = gc
-        step = np.linalg.solve(K, -res)
-        v = v + step[:3]
-        mu = mu + step[3]
-    return v
+    kappa = -(C @ (J * w0 - rot(v0) @ H)) / np.linalg.norm(H)
+    if not abs(kappa) <= 1.0:
+        return np.full(3, np.nan)
+    h = H / np.linalg.norm(H)
+    p = h - (C @ h) * C
+    t = kappa * C + np.sqrt(1.0 - kappa * kappa) * p / np.linalg.norm(p)
+    axis = np.cross(h, t)
+    s, c = np.linalg.norm(axis), h @ t
+    if s == 0.0:
+        return np.zeros(3) if c > 0 else np.full(3, np.nan)
+    n = axis / s
+    K = np.array([[0.0, -n[2], n[1]], [n[2], 0.0, -n[0]], [-n[1], n[0], 0.0]])
+    R = np.eye(3) + s * K + (1.0 - c) * (K @ K)   # sin a = s, cos a = c
+    return euler_321(R)
 
 
 def make(params, target=None):

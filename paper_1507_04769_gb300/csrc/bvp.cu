@@ -3,6 +3,7 @@
 // of bvp_kernels.cuh, and the C ABI entry points.
 #include <cmath>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -419,9 +420,21 @@ struct GraphKey {
   bool operator<(const GraphKey& o) const { return bytes < o.bytes; }
 };
 
+// An instantiated solve graph shared between the cache and the callers that
+// launch it: the executable is destroyed when the last holder lets go, so an
+// entry evicted by one host thread stays valid for another thread that has
+// already looked it up and is launching it on its own stream.
+struct GraphExec {
+  cudaGraphExec_t exec = nullptr;
+  ~GraphExec() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+using GraphExecPtr = std::shared_ptr<GraphExec>;
+
 static std::mutex g_graph_mu;
-static std::map<GraphKey, cudaGraphExec_t>& graph_cache() {
-  static auto* m = new std::map<GraphKey, cudaGraphExec_t>();
+static std::map<GraphKey, GraphExecPtr>& graph_cache() {
+  static auto* m = new std::map<GraphKey, GraphExecPtr>();
   return *m;
 }
 static std::vector<GraphKey>& graph_order() {   // insertion order, for eviction
@@ -461,39 +474,43 @@ static int run_solve_graph(const SolveArgs& a, Workspace w, cudaStream_t st, dou
   key.bytes.append(reinterpret_cast<const char*>(&grid), sizeof(grid));
   const int tsz = sizeof(T);
   key.bytes.append(reinterpret_cast<const char*>(&tsz), sizeof(tsz));
-  cudaGraphExec_t exec = nullptr;
+  GraphExecPtr held;   // keeps the executable alive until this solve has synchronised
   {
     std::lock_guard<std::mutex> lk(g_graph_mu);
     auto it = graph_cache().find(key);
-    if (it != graph_cache().end()) exec = it->second;
+    if (it != graph_cache().end()) held = it->second;
   }
-  if (!exec) {
+  if (!held) {
     cudaGraph_t g = nullptr;
     cudaError_t e = a.persistent
                         ? build_persistent_graph<T>(a, w, grid, smem, lambda0, u0, V, status, iters, Yout, &g)
                         : build_solve_graph<T>(a, w, lambda0, u0, V, status, iters, Yout, &g);
     if (e != cudaSuccess) return cuda_fail(e, "sg_solve_bvps: building the solve graph");
-    e = cudaGraphInstantiate(&exec, g, 0);
+    held = std::make_shared<GraphExec>();
+    e = cudaGraphInstantiate(&held->exec, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(e, "sg_solve_bvps: instantiating the solve graph");
-    std::lock_guard<std::mutex> lk(g_graph_mu);
-    if (graph_cache().size() >= kGraphCacheCap) {
-      // evict the oldest graph (its launches have completed: every solve
-      // synchronises its stream before returning)
-      const GraphKey old = graph_order().front();
-      graph_order().erase(graph_order().begin());
-      auto it = graph_cache().find(old);
-      if (it != graph_cache().end()) {
-        cudaGraphExecDestroy(it->second);
-        graph_cache().erase(it);
-      }
+    if (e != cudaSuccess) {
+      held->exec = nullptr;
+      return cuda_fail(e, "sg_solve_bvps: instantiating the solve graph");
     }
-    graph_cache()[key] = exec;
-    graph_order().push_back(key);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto it = graph_cache().find(key);
+    if (it != graph_cache().end()) {
+      held = it->second;   // another thread instantiated the same graph first
+    } else {
+      if (graph_cache().size() >= kGraphCacheCap) {
+        // drop the oldest entry; a thread still launching it holds its own reference
+        const GraphKey old = graph_order().front();
+        graph_order().erase(graph_order().begin());
+        graph_cache().erase(old);
+      }
+      graph_cache()[key] = held;
+      graph_order().push_back(key);
+    }
   }
   {
     KernelTimer kt(a.persistent ? kname<T>("graph_persistent") : kname<T>("graph_solve"), st);
-    SG_CUDA_TRY(cudaGraphLaunch(exec, st));
+    SG_CUDA_TRY(cudaGraphLaunch(held->exec, st));
   }
   SG_CUDA_TRY(cudaStreamSynchronize(st));
   return SG_OK;
@@ -573,7 +590,9 @@ static void* g_static_ptr[kMaxStaticDevices] = {nullptr};
 
 // Device address of g_static_scratch on the current device.  In host code the
 // symbol is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached.  The cache assumes the
+// device's context lives as long as the library: after cudaDeviceReset the
+// cached address is stale.
 static int static_scratch_address(void** out) {
   int dev = -1;
   SG_CUDA_TRY(cudaGetDevice(&dev));
@@ -610,6 +629,10 @@ extern "C" int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, 
   if (o.warm_start && !d_Y) return fail(SG_EINVAL, "sg_solve_bvps_static: warm_start needs d_Y");
   if (o.precision != SG_PREC_FP64 && !fp32_direction(o.precision))
     return fail(SG_EINVAL, "sg_solve_bvps_static: unknown precision");
+  if (o.graph)
+    return fail(SG_EINVAL,
+                "sg_solve_bvps_static: opts->graph must be 0 (the graph form instantiates CUDA graphs, "
+                "which allocate memory)");
   const size_t need = ws_bytes(n, n_max_intervals, o.precision);
   if (need > SG_STATIC_SCRATCH_BYTES)
     return fail(SG_EINVAL, "sg_solve_bvps_static: this batch needs " + std::to_string(need) +

@@ -167,6 +167,8 @@ extern "C" int sg_simulate_closed_loop(const sg_problem* prob, const sg_surplus*
     return fail(SG_EINVAL, "sg_simulate_closed_loop: the surplus must interpolate u* (d = 6 states, k = 3 controls)");
   if (mode != SG_EVAL_FP64 && mode != SG_EVAL_DF32)
     return fail(SG_EINVAL, "sg_simulate_closed_loop: mode must be SG_EVAL_FP64 or SG_EVAL_DF32");
+  if (prob->kind == SG_PROBLEM_ATTITUDE && prob->d_target)
+    return fail(SG_EINVAL, "sg_simulate_closed_loop: per-node target attitudes are not supported");
   ClArgs c{};
   if (!make_dev_problem(*prob, &c.P)) return fail(SG_EINVAL, "sg_simulate_closed_loop: invalid problem");
   c.e.M = s->M;

@@ -1,0 +1,109 @@
+"""The benchmark's timed solve under the oracle.
+
+The bench times one configuration: the level-4 grid (1457 nodes), horizons
+T in {10, 20, 40} with N = 64 / 128 / 256 intervals, Newton stopped at
+|F|_inf <= 1e-8 (not polished), mixed precision (FP32 direction, FP64
+residual), in the execution form the autotuner picks.  Here that exact call is
+made in each form it can pick (host loop, phase graph, persistent) and in the
+FP64 and pair-of-floats forms the bench times beside it, and 36 sampled nodes
+(12 per horizon) plus the origin are checked against the oracle.
+
+A solve stopped at a residual tolerance is not the discrete root, so the bound
+is derived from the iterate itself: the oracle takes the GPU's final iterate
+Y, recomputes its residual (<= tol) and the full Newton step D = -J(Y)^-1 F(Y).
+Near the root Y + D - Y* = O(|Y - Y*|^2), so |lambda0 - lambda0*| <= 2 |D_lambda0|
+and likewise for u* (linear in lambda0) and V (its change along D).  The
+oracle's root Y* is polished to |F| ~ 1e-14.  On top of the per-node bound the
+batch must meet the stated a-priori bound: max |gpu - oracle| / max |oracle|
+<= 1e-6 for lambda(0), u* and V at tol 1e-8 (|D| / |F| is at most about 10 on
+this workload, and |lambda0| is O(1)).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import synth  # noqa: E402
+from oracle import bvp as obvp  # noqa: E402
+from oracle import grid as ogrid  # noqa: E402
+from oracle import problems as oprob  # noqa: E402
+from paper_1507_04769_gb300 import sg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+LO, HI = synth.box(6)
+TOL = 1e-8
+APRIORI_REL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def bench_case():
+    params = synth.attitude_params(0)
+    pr = oprob.make(params)
+    g = sg.Grid(6, 4, LO, HI)
+    og = ogrid.Grid(6, 4, LO, HI)
+    T, N = synth.mixed_horizons(g.M, seed=2)
+    rng = np.random.default_rng(17)
+    idx = [0]                                  # node 0: the box centre, the origin
+    for Tv in (10.0, 20.0, 40.0):
+        cand = np.flatnonzero((T == Tv) & (np.arange(g.M) > 0))
+        idx += sorted(rng.choice(cand, 12, replace=False).tolist())
+    idx = np.array(idx)
+    assert np.all(og.x[0] == 0.0)
+    sols = [obvp.solve(pr, og.x[i], float(T[i]), int(N[i])) for i in idx]
+    assert all(s.status == obvp.CONVERGED for s in sols)
+    return params, pr, g, og, T, N, idx, sols
+
+
+FORMS = [
+    ("mixed-host-loop", sg.PREC_MIXED, dict(persistent=False, graph=False)),
+    ("mixed-phase-graph", sg.PREC_MIXED, dict(persistent=False, graph=True)),
+    ("mixed-persistent", sg.PREC_MIXED, dict(persistent=True, graph=True)),
+    ("fp64-phase-graph", sg.PREC_FP64, dict(persistent=False, graph=True)),
+    ("mixedpair-phase-graph", sg.PREC_MIXED_PAIR, dict(persistent=False, graph=True)),
+]
+
+
+@pytest.mark.parametrize("name,prec,form", FORMS, ids=[f[0] for f in FORMS])
+def test_bench_solve_matches_oracle(bench_case, name, prec, form):
+    params, pr, g, og, T, N, idx, sols = bench_case
+    n_max = int(N.max())
+    res = sg.solve_bvps(sg.problem_from(params), g.coords, torch.as_tensor(T, device="cuda"),
+                        torch.as_tensor(N, dtype=torch.int32, device="cuda"), tol=TOL, precision=prec,
+                        n_max=n_max, return_Y=True, **form)
+    st = res["status"].cpu().numpy()
+    assert np.all(st == sg.CONVERGED), np.bincount(st)
+    Yall = res["Y"].cpu().numpy()
+    lam_g = res["lambda0"].cpu().numpy()[idx]
+    u_g = res["u0"].cpu().numpy()[idx]
+    V_g = res["V"].cpu().numpy()[idx]
+    lam_o = np.array([s.lambda0 for s in sols])
+    u_o = np.array([s.u0 for s in sols])
+    V_o = np.array([s.V for s in sols])
+    floor_l = 1e-12 * np.abs(lam_o).max()
+    floor_u = 1e-12 * np.abs(u_o).max()
+    floor_V = 1e-12 * np.abs(V_o).max()
+    for j, i in enumerate(idx):
+        x0, Ti, Ni = og.x[i], float(T[i]), int(N[i])
+        Y = Yall[i, :3 * Ni + 1]
+        # the GPU's outputs are those of its own final iterate
+        assert np.array_equal(lam_g[j], Y[0, 6:])
+        _, u_y, V_y = obvp.outputs(pr, Y, Ti, Ni)
+        assert np.max(np.abs(u_g[j] - u_y)) <= 1e-13 * max(1.0, np.abs(u_y).max())
+        assert abs(V_g[j] - V_y) <= 1e-12 * max(1.0, abs(V_y))
+        # that iterate meets the tolerance in the oracle's residual
+        F = obvp.residual(pr, Y, x0, Ti, Ni)
+        assert np.max(np.abs(F)) <= TOL * (1 + 1e-6), (name, int(i))
+        # and its distance to the root is bounded by the Newton correction
+        D = obvp.newton_correction(pr, Y, x0, Ti, Ni)
+        _, u_c, V_c = obvp.outputs(pr, Y + D, Ti, Ni)
+        assert np.max(np.abs(lam_g[j] - lam_o[j])) <= 2 * np.max(np.abs(D[0, 6:])) + floor_l, (name, int(i))
+        assert np.max(np.abs(u_g[j] - u_o[j])) <= 2 * np.max(np.abs(u_c - u_y)) + floor_u, (name, int(i))
+        assert abs(V_g[j] - V_o[j]) <= 2 * abs(V_c - V_y) + floor_V, (name, int(i))
+    # the stated a-priori bound over the sampled batch
+    for got, ref in ((lam_g, lam_o), (u_g, u_o), (V_g, V_o)):
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= APRIORI_REL, name
+    # the origin is an equilibrium: 0 iterations and exact zeros
+    assert res["iters"][0].item() == 0 and res["V"][0].item() == 0.0

@@ -197,6 +197,25 @@ def test_residual_recomputed_at_root(att):
     assert np.max(np.abs(F)) <= 1e-12 and s.resid <= 1e-12
 
 
+def test_newton_correction_lands_on_the_root(att, lq):
+    """The Newton step that bounds the distance of an iterate to the root:
+    on the linear problem one step from any iterate lands on the root; on the
+    attitude problem the step from Y* + delta cancels delta to second order."""
+    Y0 = bvp.initial_guess(X0_LQ, 16) + np.random.default_rng(0).standard_normal((49, 12))
+    root = bvp.solve(lq, X0_LQ, 2.0, 16).Y
+    D = bvp.newton_correction(lq, Y0, X0_LQ, 2.0, 16)
+    assert np.max(np.abs(Y0 + D - root)) <= 1e-11 * np.max(np.abs(root))
+    s = bvp.solve(att, 0.5 * X0_ATT, 10.0, 32)
+    delta = np.random.default_rng(1).standard_normal(s.Y.shape)
+    errs = []
+    for eps in (1e-4, 5e-5):
+        Yp = s.Y + eps * delta
+        D = bvp.newton_correction(att, Yp, 0.5 * X0_ATT, 10.0, 32)
+        assert np.max(np.abs(D + eps * delta)) <= 1e-2 * eps          # D ~ -delta
+        errs.append(np.max(np.abs(Yp + D - s.Y)))
+    assert errs[0] / errs[1] > 3.0                                       # quadratic
+
+
 def test_example1_sign_and_scale():
     """Example I worked trajectory (Fig. Trajectories): the printed u(0).  The
     paper defers E, S, R to another reference; with the reading used here the

@@ -79,3 +79,66 @@ def test_closed_loop_cost_is_quadrature_of_running_cost():
     pr, g, w, K = _lq_linear_feedback()
     xs, us, z = cl.simulate(pr, g, w, np.zeros(6), 50, 0.01)
     assert z == 0.0 and np.all(xs == 0.0)
+
+
+# ------------------------------------------------------------------ attitude branch
+def _lambda_for(pr, u, rng):
+    """A costate whose minimiser of H is u: u*(x, lambda) = -B' J^-1 lambda_w / r,
+    so lambda_w = -r J B'^-1 u (B invertible); lambda_v is free."""
+    lw = -pr.p.r * np.asarray(pr.p.J) * np.linalg.solve(pr.B.T, u)
+    return np.concatenate([rng.standard_normal(3), lw])
+
+
+def _attitude_pin(plant_rhs, running_cost_xu, seed=0, target=None):
+    """The largest deviation of plant_rhs and running_cost_xu from the pinned
+    Hamiltonian of problems.Attitude, at random (x, u):
+      f(x, u) = dH*/dlambda at the lambda whose minimiser is u (envelope
+      theorem: u* makes dH/du vanish), by complex-step differentiation;
+      L(x, u) = running_cost at that (x, lambda)."""
+    pr = P.make(synth.attitude_params(0), target=target)
+    rng = np.random.default_rng(seed)
+    dev = 0.0
+    for _ in range(8):
+        x = rng.uniform(-0.7, 0.7, 6)
+        u = rng.standard_normal(3)
+        lam = _lambda_for(pr, u, rng)
+        y = np.concatenate([x, lam])
+        assert np.allclose(pr.ustar(x, lam), u, atol=1e-13)
+        dH = np.empty(6)
+        for c in range(6):
+            yc = y.astype(np.complex128)
+            yc[6 + c] += 1e-30j
+            dH[c] = pr.hamiltonian(yc).imag / 1e-30
+        f = plant_rhs(pr, x, u)
+        dev = max(dev, np.max(np.abs(f - dH)) / max(1.0, np.max(np.abs(dH))))
+        L = running_cost_xu(pr, x, u)
+        Lref = pr.running_cost(y)
+        dev = max(dev, abs(L - Lref) / max(1.0, abs(Lref)))
+    return dev
+
+
+def test_attitude_plant_and_cost_match_the_hamiltonian():
+    assert _attitude_pin(cl.plant_rhs, cl.running_cost_xu) <= 1e-13
+    # with a target attitude (Example II's running cost penalises v - v_e)
+    assert _attitude_pin(cl.plant_rhs, cl.running_cost_xu, seed=1, target=[0.1, -0.2, 0.05]) <= 1e-13
+
+
+def test_planted_closed_loop_mistakes_are_caught():
+    """A sign error in the control term of the plant, a dropped 1/J on it, and
+    the control weight left out of the cost each fail the pin."""
+    def plant_sign(pr, x, u):
+        f = pr.f0(x[:, None])[:, 0]
+        f[3:] = f[3:] - pr.Jinv * (pr.B @ u)
+        return f
+
+    def plant_noJ(pr, x, u):
+        f = pr.f0(x[:, None])[:, 0]
+        f[3:] = f[3:] + pr.B @ u
+        return f
+
+    def cost_no_r(pr, x, u):
+        return 0.5 * (pr.p.wv * x[:3] @ x[:3] + pr.p.ww * x[3:6] @ x[3:6] + u @ u)
+
+    assert _attitude_pin(plant_sign, cl.running_cost_xu) > 1e-3
+    assert _attitude_pin(plant_noJ, cl.running_cost_xu) > 1e-3
+    assert _attitude_pin(cl.plant_rhs, cost_no_r) > 1e-3

@@ -102,3 +102,63 @@ def test_planted_convention_error_fails_printed_trajectory():
     s = bvp.solve(Flipped(PRM, target=ve), X0, synth.EXAMPLE2_T, N, tol=1e-10)
     u0 = -np.asarray(PRM.B).T @ (s.Y[0, 9:12] / np.asarray(PRM.J)) / PRM.r
     assert np.abs(u0 - _printed()[0, 7:9]).max() > 1e-3
+
+
+def _slsqp_target(x0, starts):
+    """A generic constrained optimiser on Eq. optim_attitude (independent of the
+    closed form): SLSQP from several starts, the largest trace kept."""
+    from scipy.optimize import minimize
+    B, J, H = np.asarray(PRM.B), np.asarray(PRM.J), np.asarray(PRM.hmom)
+    C = P.reachable_normal(B)
+    rhs = C @ (J * x0[3:] - P.rot(x0[:3]) @ H)
+    cons = {"type": "eq", "fun": lambda v: -C @ P.rot(v) @ H - rhs}
+    best = None
+    for g in starts:
+        r = minimize(lambda v: -np.trace(P.rot(v)), g, constraints=[cons], method="SLSQP", tol=1e-15,
+                     options={"maxiter": 500})
+        if r.success and abs(cons["fun"](r.x)) < 1e-10 and (best is None or r.fun < best.fun):
+            best = r
+    return best.x
+
+
+def test_target_attitude_matches_a_generic_optimiser():
+    """At random states of the Example II box the closed form and SLSQP agree:
+    the same trace to 1e-12 (SLSQP never finds a larger one) and the same angles
+    to the optimiser's accuracy on the flat maximum (1e-6)."""
+    lo, hi = synth.example2_box()
+    rng = np.random.default_rng(3)
+    for _ in range(6):
+        x0 = rng.uniform(lo, hi)
+        ve = P.target_attitude(PRM, x0)
+        vs = _slsqp_target(x0, (x0[:3], np.zeros(3), ve + 0.1))
+        assert np.trace(P.rot(vs)) <= np.trace(P.rot(ve)) + 1e-12
+        assert abs(np.trace(P.rot(vs)) - np.trace(P.rot(ve))) < 1e-12
+        assert np.max(np.abs(vs - ve)) < 1e-6
+
+
+def test_euler_321_inverts_rot():
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        v = rng.uniform([-np.pi, -1.4, -np.pi], [np.pi, 1.4, np.pi])
+        assert np.allclose(P.euler_321(P.rot(v)), v, atol=1e-13)
+
+
+def test_planted_target_error_is_not_a_maximum():
+    """Taking the farthest point of the feasible circle instead of the nearest
+    gives a feasible attitude whose trace a generic optimiser beats."""
+    B, J, H = np.asarray(PRM.B), np.asarray(PRM.J), np.asarray(PRM.hmom)
+    C = P.reachable_normal(B)
+    x0 = np.array([0.1, np.pi / 8, -0.2, 0.05, 0.0, -0.1])
+    kappa = -(C @ (J * x0[3:] - P.rot(x0[:3]) @ H)) / np.linalg.norm(H)
+    h = H / np.linalg.norm(H)
+    p = h - (C @ h) * C
+    t = kappa * C - np.sqrt(1 - kappa ** 2) * p / np.linalg.norm(p)   # planted: the far point
+    ax = np.cross(h, t)
+    s, c = np.linalg.norm(ax), h @ t
+    n = ax / s
+    K = np.array([[0, -n[2], n[1]], [n[2], 0, -n[0]], [-n[1], n[0], 0]])
+    bad = P.euler_321(np.eye(3) + s * K + (1 - c) * K @ K)
+    assert abs(-C @ P.rot(bad) @ H - C @ (J * x0[3:] - P.rot(x0[:3]) @ H)) < 1e-12   # still feasible
+    vs = _slsqp_target(x0, (x0[:3], np.zeros(3)))
+    assert np.trace(P.rot(vs)) > np.trace(P.rot(bad)) + 1e-3
+    assert np.max(np.abs(P.target_attitude(PRM, x0) - vs)) < 1e-6
