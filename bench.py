@@ -13,8 +13,11 @@ The headline value is converged BVP solves per second of whole-step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
 
-Multi-GPU (torchrun): every rank runs its own independent instance (weak
-scaling, no collective on the data path); value = all ranks' solves / max time.
+Multi-GPU (torchrun): one job split over the ranks (paper_1507_04769_gb300/
+sharded.py): each rank solves a contiguous node range of about equal cost, one
+all-gather brings every node's result to every rank, the surpluses are built
+replicated and the queries are split evenly.  Total work is fixed (strong
+scaling); value = the job's converged solves / max time over ranks.
 """
 from __future__ import annotations
 
@@ -132,8 +135,8 @@ def max_over_ranks(x: float, device) -> float:
 
 
 def sum_over_ranks(n: int, device) -> int:
-    """Sum of a per-rank count over the process group (converged solves of all
-    ranks); the identity without one."""
+    """Sum of a per-rank count over the process group; the identity without
+    one."""
     import torch
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
@@ -141,11 +144,6 @@ def sum_over_ranks(n: int, device) -> int:
     t = torch.tensor([int(n)], dtype=torch.int64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return int(t.item())
-
-
-def rank_query_seed(rank: int) -> int:
-    """Seed of the query batch of one rank: every rank evaluates its own batch."""
-    return 1 + rank
 
 
 class ClockSampler:
@@ -276,6 +274,7 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1507_04769_gb300 import sg
+    from paper_1507_04769_gb300 import sharded
 
     prec = {"mixed": sg.PREC_MIXED, "mixed-pair": sg.PREC_MIXED_PAIR, "fp64": sg.PREC_FP64}[args.precision]
     eval_mode = {"fp64": sg.EVAL_FP64, "df32": sg.EVAL_DF32, "tf32x3": sg.EVAL_TF32X3}[args.eval]
@@ -285,13 +284,18 @@ def gpu_arm(args):
     g0 = sg.Grid(D, LEVEL, lo, hi)
     M = g0.M
     T_h, N_h = synth.mixed_horizons(M, seed=2)
-    xq_h = synth.mixed_queries(N_QUERIES, lo, hi, seed=rank_query_seed(rank))
+    # the job's split over the ranks: node ranges of about equal cost, even query ranges
+    ranges = sharded.partition(sharded.node_costs(N_h), world)
+    n0, n1 = ranges[rank]
+    q0, q1 = sharded.even_range(N_QUERIES, rank, world)
+    n_loc, q_loc = n1 - n0, q1 - q0
+    xq_h = synth.mixed_queries(N_QUERIES, lo, hi, seed=1)[q0:q1]
     T_d = torch.as_tensor(T_h, device=dev)
     N_d = torch.as_tensor(N_h, dtype=torch.int32, device=dev)
     xq_d = torch.as_tensor(xq_h, device=dev)
     n_max = int(N_h.max())
-    ws = torch.empty(sg.workspace_bytes(M, n_max, prec), dtype=torch.uint8, device=dev)
-    u_out = torch.empty((N_QUERIES, 3), dtype=torch.float64, device=dev)
+    ws = torch.empty(max(sg.workspace_bytes(n_loc, n_max, prec), 1), dtype=torch.uint8, device=dev)
+    u_out = torch.empty((q_loc, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -304,17 +308,17 @@ def gpu_arm(args):
         args.form = "phase"
         args.skip_cpu = args.skip_fp64 = args.skip_serving = args.skip_extensions = True
     if args.form == "auto":
-        form, tune_ms = sg.autotune_solve(prob, x0_d, T_d, N_d, tol=TOL, precision=prec, n_max=n_max,
-                                          workspace=ws)
+        form, tune_ms = sg.autotune_solve(prob, x0_d[n0:n1], T_d[n0:n1], N_d[n0:n1], tol=TOL, precision=prec,
+                                          n_max=n_max, workspace=ws)
     else:
         form = {"phase": dict(persistent=False, graph=False, blocks_per_sm=0),
                 "phase-graph": dict(persistent=False, graph=True, blocks_per_sm=0),
                 "persistent": dict(persistent=True, graph=True, blocks_per_sm=0)}[args.form]
-    res_out = {"lambda0": torch.empty((M, 6), dtype=torch.float64, device=dev),
-               "u0": torch.empty((M, 3), dtype=torch.float64, device=dev),
-               "V": torch.empty((M,), dtype=torch.float64, device=dev),
-               "status": torch.empty((M,), dtype=torch.int32, device=dev),
-               "iters": torch.empty((M,), dtype=torch.int32, device=dev)}
+    res_out = {"lambda0": torch.empty((n_loc, 6), dtype=torch.float64, device=dev),
+               "u0": torch.empty((n_loc, 3), dtype=torch.float64, device=dev),
+               "V": torch.empty((n_loc,), dtype=torch.float64, device=dev),
+               "status": torch.empty((n_loc,), dtype=torch.int32, device=dev),
+               "iters": torch.empty((n_loc,), dtype=torch.int32, device=dev)}
 
     def step(events=None):
         if events:
@@ -323,8 +327,8 @@ def gpu_arm(args):
         x0_d.copy_(g.coords)
         if events:
             events[1].record(stream)
-        res = sg.solve_bvps(prob, x0_d, T_d, N_d, tol=TOL, precision=prec, workspace=ws, n_max=n_max,
-                            out=res_out, **form)
+        res = sharded.sharded_solve(prob, x0_d, T_d, N_d, ranges=ranges, tol=TOL, precision=prec, workspace=ws,
+                                    n_max=n_max, out=res_out, **form)
         if events:
             events[2].record(stream)
         S = sg.Surplus(g, res["u0"])
@@ -341,8 +345,7 @@ def gpu_arm(args):
     torch.cuda.synchronize()
     status = res["status"].cpu().numpy()
     iters = res["iters"].cpu().numpy().astype(np.int64)
-    conv_per_step = int(np.sum(status == sg.CONVERGED))
-    conv_all_ranks = sum_over_ranks(conv_per_step, dev)
+    conv_per_step = int(np.sum(status == sg.CONVERGED))   # the whole job's (results are gathered)
 
     # ---------------- timed region
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
@@ -366,16 +369,16 @@ def gpu_arm(args):
         # phase for the per-kernel durations and the executed-kernel count
         phase = dict(persistent=False, graph=False, blocks_per_sm=0)
         for _ in range(2):
-            sg.solve_bvps(prob, x0_d, T_d, N_d, tol=TOL, precision=prec, workspace=ws, n_max=n_max, out=res_out,
-                          **phase)
+            sharded.sharded_solve(prob, x0_d, T_d, N_d, ranges=ranges, tol=TOL, precision=prec, workspace=ws,
+                                  n_max=n_max, out=res_out, **phase)
         torch.cuda.synchronize()
         la = sg.LIB.sg_kernel_launches()
         sg.LIB.sg_timing_enable(1)
         for _ in range(args.steps):
             g = sg.Grid(D, LEVEL, lo, hi)
             x0_d.copy_(g.coords)
-            r2 = sg.solve_bvps(prob, x0_d, T_d, N_d, tol=TOL, precision=prec, workspace=ws, n_max=n_max,
-                               out=res_out, **phase)
+            r2 = sharded.sharded_solve(prob, x0_d, T_d, N_d, ranges=ranges, tol=TOL, precision=prec,
+                                       workspace=ws, n_max=n_max, out=res_out, **phase)
             S2 = sg.Surplus(g, r2["u0"])
             sg.eval_feedback(S2, xq_d, mode=eval_mode, out=u_out)
             flush.zero_()
@@ -388,11 +391,11 @@ def gpu_arm(args):
     phase_ms = {name: sum(ev[s][i].elapsed_time(ev[s][i + 1]) for s in range(args.steps)) / args.steps
                 for i, name in enumerate(["grid", "solve", "surplus", "eval"])}
     t_max = max_over_ranks(sum(step_ms) / 1e3, dev)
-    total_solves = conv_all_ranks * args.steps
+    total_solves = conv_per_step * args.steps
     value = total_solves / t_max
 
     if args.only_steps:
-        roof, kernels = roofline(kt, iters, N_h, M, prec)
+        roof, kernels = roofline(kt, iters[n0:n1], N_h[n0:n1], M, prec, q_loc)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": total_solves / t_max, "unit": UNIT,
                               "only_steps": True, "ms_per_step": 1e3 * t_max / args.steps, "roofline": roof,
@@ -406,7 +409,7 @@ def gpu_arm(args):
     T_pin = torch.as_tensor(T_h).pin_memory()
     N_pin = torch.as_tensor(N_h, dtype=torch.int32).pin_memory()
     xq_pin = torch.as_tensor(xq_h).pin_memory()
-    u_pin = torch.empty((N_QUERIES, 3), dtype=torch.float64).pin_memory()
+    u_pin = torch.empty((q_loc, 3), dtype=torch.float64).pin_memory()
     node_pin = {k: torch.empty((M,) + shp, dtype=dt).pin_memory()
                 for k, shp, dt in (("lambda0", (6,), torch.float64), ("u0", (3,), torch.float64),
                                    ("V", (), torch.float64), ("status", (), torch.int32))}
@@ -439,20 +442,20 @@ def gpu_arm(args):
     e2e_t = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, dev)
     h2d = T_pin.numel() * 8 + N_pin.numel() * 4 + xq_pin.numel() * 8
     d2h = u_pin.numel() * 8 + sum(t.numel() * t.element_size() for t in node_pin.values())
-    e2e_value = conv_all_ranks * args.steps / e2e_t
+    e2e_value = conv_per_step * args.steps / e2e_t
 
     # ---------------- FP64 form on the same GPU (speedup of the mixed form)
     fp64 = None
-    if prec != sg.PREC_FP64 and not args.skip_fp64:
-        ws64 = torch.empty(sg.workspace_bytes(M, n_max, sg.PREC_FP64), dtype=torch.uint8, device=dev)
+    if prec != sg.PREC_FP64 and not args.skip_fp64 and n_loc > 0:
+        ws64 = torch.empty(max(sg.workspace_bytes(n_loc, n_max, sg.PREC_FP64), 1), dtype=torch.uint8, device=dev)
         g = sg.Grid(D, LEVEL, lo, hi)
-        r64 = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=sg.PREC_FP64, workspace=ws64,
+        r64 = sg.solve_bvps(prob, g.coords[n0:n1], T_d[n0:n1], N_d[n0:n1], tol=TOL, precision=sg.PREC_FP64, workspace=ws64,
                             n_max=n_max)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(args.steps):
-            r64 = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=sg.PREC_FP64, workspace=ws64,
+            r64 = sg.solve_bvps(prob, g.coords[n0:n1], T_d[n0:n1], N_d[n0:n1], tol=TOL, precision=sg.PREC_FP64, workspace=ws64,
                                 n_max=n_max)
         b.record(stream)
         torch.cuda.synchronize()
@@ -460,15 +463,15 @@ def gpu_arm(args):
         c64 = int((r64["status"] == sg.CONVERGED).sum().item())
         # per-kernel times of the FP64 form (one launch per phase) for its roofline
         sg.LIB.sg_timing_enable(1)
-        r64 = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=sg.PREC_FP64, workspace=ws64,
+        r64 = sg.solve_bvps(prob, g.coords[n0:n1], T_d[n0:n1], N_d[n0:n1], tol=TOL, precision=sg.PREC_FP64, workspace=ws64,
                             n_max=n_max)
         torch.cuda.synchronize()
         sg.LIB.sg_timing_enable(0)
         kt64 = collect_kernel_times(sg)
         it64 = r64["iters"].cpu().numpy().astype(np.int64)
-        _, kern64 = roofline(kt64, it64, N_h, M, sg.PREC_FP64)
+        _, kern64 = roofline(kt64, it64, N_h[n0:n1], M, sg.PREC_FP64, q_loc)
         mixed_solve_s = phase_ms["solve"] / 1e3
-        dl = (r64["lambda0"] - res["lambda0"]).abs().max().item() / r64["lambda0"].abs().max().item()
+        dl = (r64["lambda0"] - res["lambda0"][n0:n1]).abs().max().item() / r64["lambda0"].abs().max().item()
         fp64 = {"solves_per_s": c64 / t64, "solve_ms": 1e3 * t64,
                 "mixed_solve_ms": 1e3 * mixed_solve_s, "speedup_mixed_over_fp64": t64 / mixed_solve_s,
                 "max_rel_diff_lambda0_mixed_vs_fp64": dl,
@@ -477,13 +480,13 @@ def gpu_arm(args):
         # the other FP32-direction form (residual in FP64, or in pairs of
         # floats), in the timed form's execution form, on its workspace
         other = sg.PREC_MIXED_PAIR if prec == sg.PREC_MIXED else sg.PREC_MIXED
-        rr = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=other, workspace=ws,
+        rr = sg.solve_bvps(prob, g.coords[n0:n1], T_d[n0:n1], N_d[n0:n1], tol=TOL, precision=other, workspace=ws,
                            n_max=n_max, **form)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(args.steps):
-            rr = sg.solve_bvps(prob, g.coords, T_d, N_d, tol=TOL, precision=other, workspace=ws,
+            rr = sg.solve_bvps(prob, g.coords[n0:n1], T_d[n0:n1], N_d[n0:n1], tol=TOL, precision=other, workspace=ws,
                                n_max=n_max, **form)
         b.record(stream)
         torch.cuda.synchronize()
@@ -499,7 +502,7 @@ def gpu_arm(args):
     # ---------------- interpolant modes on the 1e6 queries (FP64, DF32, 3xTF32)
     eval_modes = {}
     if rank == 0:
-        S_ref = sg.Surplus(g0, res_out["u0"])
+        S_ref = sg.Surplus(g0, res["u0"])
         ref = sg.eval_feedback(S_ref, xq_d, mode=sg.EVAL_FP64)
         for name, md in (("fp64", sg.EVAL_FP64), ("df32", sg.EVAL_DF32), ("tf32x3", sg.EVAL_TF32X3)):
             outm = torch.empty_like(ref)
@@ -513,7 +516,7 @@ def gpu_arm(args):
             torch.cuda.synchronize()
             ms = a.elapsed_time(b)
             err = ((outm - ref).abs().max() / ref.abs().max()).item()
-            eval_modes[name] = {"ms_per_1e6": ms * 1e6 / N_QUERIES, "evals_per_s": N_QUERIES / (ms / 1e3),
+            eval_modes[name] = {"ms_per_1e6": ms * 1e6 / q_loc, "evals_per_s": q_loc / (ms / 1e3),
                                 "max_rel_err_vs_fp64": err}
 
     # ---------------- Example III: value function on the q = 12 grid in (t, x)
@@ -623,7 +626,8 @@ def gpu_arm(args):
             probe[name + "_tflops"] = fl.value / (a.elapsed_time(b) / 1e3) / 1e12
 
     # ---------------- roofline of the dominant kernel
-    roof, kernels = roofline(kt, iters, N_h, M, prec)
+    roof, kernels = roofline(kt, iters[n0:n1], N_h[n0:n1], M, prec, q_loc)
+    eval_ms_max = max_over_ranks(phase_ms["eval"], dev)   # every rank's share of the queries
 
     if rank != 0:
         if world > 1:
@@ -642,7 +646,7 @@ def gpu_arm(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong", "vs_baseline": None,
         "dtype": "f64+f32" if prec != sg.PREC_FP64 else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "nodes": M, "grid_level": LEVEL, "d": D,
@@ -654,8 +658,9 @@ def gpu_arm(args):
                    "eval": args.eval,
                    "solve_form": form, "autotune_ms": tune_ms,
                    "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": f"{world} independent instance(s), no collective"},
-        "feedback_evals_per_s": N_QUERIES / (phase_ms["eval"] / 1e3),
+                   "parallelism": (f"{world} rank(s), one job: node ranges of equal cost, one all-gather of "
+                                   "per-node results, surpluses replicated, queries split evenly")},
+        "feedback_evals_per_s": N_QUERIES / (eval_ms_max / 1e3),
         "breakdown_ms": phase_ms,
         "newton_iters_hist": np.bincount(iters).tolist(),
         "converged_per_step": conv_per_step,
@@ -701,9 +706,10 @@ def collect_kernel_times(sg):
     return out
 
 
-def roofline(kt, iters, N_h, M, prec):
+def roofline(kt, iters, N_h, M, prec, nq=N_QUERIES):
     """Per-kernel algorithmic work / measured time; the dominant kernel's entry
-    is the roofline object."""
+    is the roofline object.  iters and N_h are those of the nodes this rank
+    solved; nq is the number of queries it evaluated per step."""
     fp32 = prec != 0   # any form but SG_PREC_FP64 runs the direction in FP32
     suffix = "_fp32" if fp32 else "_fp64"
     tsize = 4 if fp32 else 8
@@ -726,9 +732,9 @@ def roofline(kt, iters, N_h, M, prec):
                                                   + flops_recover_interval()) * int_units, peak_lin, "TFLOP/s"),
         "k_point" + suffix: ("hbm", bytes_point(tsize) * pt_units, None, "GB/s"),
         "k_condense_smem_fp64": ("alu", flops_condense_interval() * int_units, PEAK_FP64_TFLOPS, "TFLOP/s"),
-        "k_eval_fp64": ("alu", flops_eval_query(M, 3) * N_QUERIES, PEAK_FP64_TFLOPS, "TFLOP/s"),
-        "k_eval_df32": ("alu", flops_eval_query_df32(M, 3) * N_QUERIES, PEAK_FP32_TFLOPS, "TFLOP/s"),
-        "k_eval_tf32x3": ("alu", 2 * M * 3 * N_QUERIES, PEAK_FP32_TFLOPS, "TFLOP/s"),
+        "k_eval_fp64": ("alu", flops_eval_query(M, 3) * nq, PEAK_FP64_TFLOPS, "TFLOP/s"),
+        "k_eval_df32": ("alu", flops_eval_query_df32(M, 3) * nq, PEAK_FP32_TFLOPS, "TFLOP/s"),
+        "k_eval_tf32x3": ("alu", 2 * M * 3 * nq, PEAK_FP32_TFLOPS, "TFLOP/s"),
     }
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = 6785.9

@@ -28,11 +28,15 @@ def _rank_main(rank, world, port, q):
     try:
         # per-rank seconds: the job time is the slowest rank's
         t = bench.max_over_ranks(1.0 + rank, torch.device("cpu"))
-        # converged counts add up over ranks (weak scaling: every rank its own instance)
         n = bench.sum_over_ranks(100 + rank, torch.device("cpu"))
-        seed = bench.rank_query_seed(rank)
+        # the bench's split of the level-4 job: node and query ranges of this rank
+        import synth
+        from paper_1507_04769_gb300 import sharded
+        _, N = synth.mixed_horizons(1457, seed=2)
+        nodes = sharded.partition(sharded.node_costs(N), world)[rank]
+        queries = sharded.even_range(bench.N_QUERIES, rank, world)
         dist.barrier()
-        q.put((rank, t, n, seed))
+        q.put((rank, t, n, nodes, queries))
     finally:
         dist.destroy_process_group()
 
@@ -50,7 +54,9 @@ def test_two_gloo_ranks_reduce_timing_and_counts():
     out = sorted(q.get(timeout=5) for _ in range(world))
     assert [o[1] for o in out] == [2.0, 2.0]          # max over ranks
     assert [o[2] for o in out] == [201, 201]          # sum over ranks
-    assert len({o[3] for o in out}) == world          # distinct query batches per rank
+    # the ranks split one job: node ranges and query ranges tile the whole
+    assert out[0][3][0] == 0 and out[0][3][1] == out[1][3][0] and out[1][3][1] == 1457
+    assert out[0][4] == (0, 500_000) and out[1][4] == (500_000, 1_000_000)
 
 
 def test_helpers_without_process_group():
