@@ -58,7 +58,10 @@ DRAM_BYTES_PER_UNIT = {
 WORKLOAD = ("attitude6d_L4_1457nodes_T{10,20,40}_N{64,128,256}_mixedprec"
             "+surplus+1e6queries")
 
-# Derived ALU peaks (unit counts x maximum SM clock, 2070 MHz, 152 SMs):
+# ALU peaks: the roofline divides by the FP32 / FP64 rates measured in the same
+# run by the library's FMA-chain probe (sg_fma_probe); these derived figures
+# are the fallback when no probe figure is given (unit counts x maximum SM
+# clock, 2070 MHz, 152 SMs):
 #   FP32: 128 FMA lanes/SM x 2 flops = 80.6 TFLOP/s
 #   FP64: the nominal 1.25 TFLOP/s of GB300 (about 2 FMA/clk/SM)
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -106,14 +109,6 @@ def bytes_point(tsize: int) -> float:
 def flops_eval_query(M: int, k: int) -> float:
     """Per query: the contraction (2 k flops per node) and one product per node."""
     return M * (2 * k + 1)
-
-
-def flops_eval_query_df32(M: int, k: int) -> float:
-    """Per query on the FP32 pipe (pair-of-floats arithmetic, FMA = 2 flops):
-    per node and output 15 (exact product 3, cross terms 4, exact sum 6, tail
-    2) and 12 for the basis product (1.7 unnormalised pair multiplications of
-    7 on average over the level-4 nodes)."""
-    return M * (15 * k + 12)
 
 
 # ------------------------------------------------------------------ helpers
@@ -205,34 +200,92 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle worker
-def cpu_worker(n_nodes: int, seed: int) -> dict:
-    """Times the oracle on a bounded sample of the workload: n_nodes BVP solves
-    drawn from the level-4 nodes with their horizons (single thread)."""
+def _oracle_solve_node(job):
+    """One oracle BVP solve (a process-pool task): returns converged flag."""
     from oracle import bvp as obvp
-    from oracle import grid as ogrid
     from oracle import problems as oprob
+    x0, T, N = job
+    pr = oprob.make(synth.attitude_params(0))
+    s = obvp.solve(pr, np.asarray(x0), float(T), int(N), tol=TOL, polish=False)
+    return int(s.status == obvp.CONVERGED)
+
+
+def stratified_sample(T, n_nodes: int, seed: int) -> np.ndarray:
+    """n_nodes node indices drawn per horizon in the batch's proportions."""
+    rng = np.random.default_rng(seed)
+    out = []
+    vals, counts = np.unique(T, return_counts=True)
+    quota = np.floor(n_nodes * counts / counts.sum()).astype(int)
+    quota[np.argsort(-(n_nodes * counts / counts.sum() - quota))[:n_nodes - quota.sum()]] += 1
+    for v, q in zip(vals, quota):
+        cand = np.flatnonzero(T == v)
+        out += rng.choice(cand, min(q, cand.size), replace=False).tolist()
+    return np.array(sorted(out))
+
+
+def cpu_model() -> str:
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_worker(n_nodes: int, seed: int, procs: int = 1, steps: int = 1) -> dict:
+    """Times the oracle on bounded samples of the workload: per step n_nodes
+    BVP solves drawn from the level-4 nodes with their horizons (in the batch's
+    horizon proportions), on `procs` processes (one thread each)."""
+    from oracle import grid as ogrid
     lo, hi = synth.box(D)
     g = ogrid.Grid(D, LEVEL, lo, hi)
     T, N = synth.mixed_horizons(g.M, seed=2)
-    idx = np.random.default_rng(seed).choice(g.M, n_nodes, replace=False)
-    pr = oprob.make(synth.attitude_params(0))
-    t0 = time.perf_counter()
-    conv = 0
-    for i in idx:
-        s = obvp.solve(pr, g.x[i], float(T[i]), int(N[i]), tol=TOL, polish=False)
-        conv += int(s.status == obvp.CONVERGED)
-    dt = time.perf_counter() - t0
-    return {"converged": conv, "seconds": dt, "nodes": int(n_nodes), "N": [int(N[i]) for i in idx]}
+    pool = None
+    if procs > 1:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(procs)
+        pool.map(_oracle_solve_node, [(g.x[0], 1.0, 1)] * procs)   # start-up outside the timing
+    per_step = []
+    Ns = []
+    try:
+        for st in range(steps):
+            idx = stratified_sample(T, n_nodes, seed + st)
+            jobs = [(g.x[i], T[i], N[i]) for i in idx]
+            t0 = time.perf_counter()
+            if pool is None:
+                conv = sum(_oracle_solve_node(j) for j in jobs)
+            else:
+                conv = sum(pool.map(_oracle_solve_node, jobs, chunksize=1))
+            per_step.append({"converged": int(conv), "seconds": time.perf_counter() - t0})
+            Ns += [int(N[i]) for i in idx]
+    finally:
+        if pool is not None:
+            pool.close()
+            pool.join()
+    conv = sum(p["converged"] for p in per_step)
+    secs = sum(p["seconds"] for p in per_step)
+    return {"converged": conv, "seconds": secs, "nodes": int(n_nodes) * steps, "procs": procs,
+            "per_step": per_step, "N_counts": {str(k): Ns.count(k) for k in sorted(set(Ns))}}
 
 
-def run_cpu_baseline(n_nodes: int, seed: int = 123) -> dict:
+def run_cpu_baseline(n_nodes: int, seed: int = 123, procs: int = 1, steps: int = 1) -> dict:
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
     for v in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
         env.pop(v, None)
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(n_nodes), str(seed)],
-                       capture_output=True, text=True, env=env, timeout=900)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(n_nodes), str(seed),
+                        str(procs), str(steps)], capture_output=True, text=True, env=env, timeout=1200)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
@@ -240,25 +293,26 @@ def run_cpu_baseline(n_nodes: int, seed: int = 123) -> dict:
 
 # ------------------------------------------------------------------ reference arm
 def reference_arm(args):
+    """The oracle timed on all host cores (one process per core, one thread
+    each), each step a bounded stratified sample of the level-4 nodes."""
     rank, world, _ = _rank_env()
     if rank != 0:
         return 0
-    per_step = 4
-    times, conv = [], 0
-    for s in range(args.warmup + args.steps):
-        r = run_cpu_baseline(per_step, seed=1000 + s)
-        if s >= args.warmup:
-            times.append(r["seconds"])
-            conv += r["converged"]
-    total = sum(times)
+    cores = host_cores()
+    per_step = 8 * cores
+    r = run_cpu_baseline(per_step, seed=1000, procs=cores, steps=args.warmup + args.steps)
+    timed = r["per_step"][args.warmup:]
+    total = sum(p["seconds"] for p in timed)
+    conv = sum(p["converged"] for p in timed)
     value = conv / total
-    sample = (f"{per_step} oracle BVP solves per step (level-4 nodes with their T/N draws), "
-              f"single thread, tol 1e-8")
+    sample = (f"{per_step} oracle BVP solves per step (level-4 nodes, horizons in the batch's proportions), "
+              f"{cores} processes x 1 thread on {cpu_model()}, tol 1e-8")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -387,6 +441,8 @@ def gpu_arm(args):
         launches = sg.LIB.sg_kernel_launches() - la
         kt = collect_kernel_times(sg)
         kt_form = "second timed region, same kernels launched one per phase"
+    # FP64 / FP32 pipe peaks of this GPU, measured now, for the roofline fractions
+    probe = measure_pipe_peaks(sg, stream, local)
     step_ms = [ev[s][0].elapsed_time(ev[s][4]) for s in range(args.steps)]
     phase_ms = {name: sum(ev[s][i].elapsed_time(ev[s][i + 1]) for s in range(args.steps)) / args.steps
                 for i, name in enumerate(["grid", "solve", "surplus", "eval"])}
@@ -395,7 +451,7 @@ def gpu_arm(args):
     value = total_solves / t_max
 
     if args.only_steps:
-        roof, kernels = roofline(kt, iters[n0:n1], N_h[n0:n1], M, prec, q_loc)
+        roof, kernels = roofline(kt, iters[n0:n1], N_h[n0:n1], M, prec, q_loc, probe)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": total_solves / t_max, "unit": UNIT,
                               "only_steps": True, "ms_per_step": 1e3 * t_max / args.steps, "roofline": roof,
@@ -469,7 +525,7 @@ def gpu_arm(args):
         sg.LIB.sg_timing_enable(0)
         kt64 = collect_kernel_times(sg)
         it64 = r64["iters"].cpu().numpy().astype(np.int64)
-        _, kern64 = roofline(kt64, it64, N_h[n0:n1], M, sg.PREC_FP64, q_loc)
+        _, kern64 = roofline(kt64, it64, N_h[n0:n1], M, sg.PREC_FP64, q_loc, probe)
         mixed_solve_s = phase_ms["solve"] / 1e3
         dl = (r64["lambda0"] - res["lambda0"][n0:n1]).abs().max().item() / r64["lambda0"].abs().max().item()
         fp64 = {"solves_per_s": c64 / t64, "solve_ms": 1e3 * t64,
@@ -607,26 +663,8 @@ def gpu_arm(args):
         del server
         torch.cuda.synchronize()
 
-    # ---------------- FP64 / FP32 pipe peaks measured by the library's FMA-chain probe
-    probe = {}
-    if rank == 0:
-        import ctypes as C
-        scratch = torch.empty(152 * 8 * 256 * 8, dtype=torch.uint8, device=dev)
-        sg.LIB.sg_fma_probe.argtypes = [C.c_int, C.c_void_p, C.c_size_t, C.c_int, C.c_int, C.c_int,
-                                        C.POINTER(C.c_double), C.c_void_p]
-        for name, pr, n_it in (("fp64", sg.PREC_FP64, 256), ("fp32", sg.PREC_MIXED, 4096)):
-            fl = C.c_double()
-            for rep in range(3):
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                sg.LIB.sg_fma_probe(pr, C.c_void_p(scratch.data_ptr()), scratch.numel(), 152 * 8, 256, n_it,
-                                    C.byref(fl), C.c_void_p(stream.cuda_stream))
-                b.record(stream)
-                torch.cuda.synchronize()
-            probe[name + "_tflops"] = fl.value / (a.elapsed_time(b) / 1e3) / 1e12
-
     # ---------------- roofline of the dominant kernel
-    roof, kernels = roofline(kt, iters[n0:n1], N_h[n0:n1], M, prec, q_loc)
+    roof, kernels = roofline(kt, iters[n0:n1], N_h[n0:n1], M, prec, q_loc, probe)
     eval_ms_max = max_over_ranks(phase_ms["eval"], dev)   # every rank's share of the queries
 
     if rank != 0:
@@ -637,11 +675,20 @@ def gpu_arm(args):
 
     cpu = None
     if world == 1 and not args.skip_cpu:
-        nodes = args.cpu_nodes
-        r = run_cpu_baseline(nodes)
-        cpu = {"value": r["converged"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nodes} level-4 nodes (N = {sorted(r['N'])}) solved by the oracle to "
-                         f"|F|_inf <= 1e-8, single thread, {r['seconds']:.1f} s"}
+        # the oracle on every host core over the whole level-4 batch, and on
+        # one core over a stratified sample of it
+        cores = host_cores()
+        model = cpu_model()
+        r_all = run_cpu_baseline(M, seed=0, procs=cores)
+        r_one = run_cpu_baseline(args.cpu_nodes, seed=123)
+        cpu = {"value": r_all["converged"] / r_all["seconds"], "unit": UNIT, "cores": cores, "kind": "oracle",
+               "cpu_model": model,
+               "sample": f"all {M} level-4 nodes (N counts {r_all['N_counts']}) solved by the oracle to "
+                         f"|F|_inf <= 1e-8 on {cores} processes x 1 thread ({model}), "
+                         f"{r_all['seconds']:.1f} s",
+               "single_core": {"value": r_one["converged"] / r_one["seconds"], "unit": UNIT, "cores": 1,
+                               "sample": f"{args.cpu_nodes} of the nodes (N counts {r_one['N_counts']}), "
+                                         f"{r_one['seconds']:.1f} s"}}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -685,6 +732,33 @@ def gpu_arm(args):
     return 0
 
 
+def measure_pipe_peaks(sg, stream, gpu_index) -> dict:
+    """FP64 and FP32 FMA rates of this GPU from the library's FMA-chain probe
+    (152 x 8 blocks of 256 threads, dependent FMA chains), the best of three
+    runs each, with the SM clocks sampled while it runs."""
+    import ctypes as C
+    import torch
+    scratch = torch.empty(152 * 8 * 256 * 8, dtype=torch.uint8, device=torch.device("cuda", gpu_index))
+    sg.LIB.sg_fma_probe.argtypes = [C.c_int, C.c_void_p, C.c_size_t, C.c_int, C.c_int, C.c_int,
+                                    C.POINTER(C.c_double), C.c_void_p]
+    probe = {}
+    with ClockSampler(gpu_index) as clk:
+        for name, pr, n_it in (("fp64", sg.PREC_FP64, 256), ("fp32", sg.PREC_MIXED, 4096)):
+            fl = C.c_double()
+            best = 0.0
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sg.LIB.sg_fma_probe(pr, C.c_void_p(scratch.data_ptr()), scratch.numel(), 152 * 8, 256, n_it,
+                                    C.byref(fl), C.c_void_p(stream.cuda_stream))
+                b.record(stream)
+                torch.cuda.synchronize()
+                best = max(best, fl.value / (a.elapsed_time(b) / 1e3) / 1e12)
+            probe[name + "_tflops"] = best
+    probe["clocks"] = clk.summary()
+    return probe
+
+
 def collect_kernel_times(sg):
     import ctypes as C
     n_max, name_len = 64, 64
@@ -706,14 +780,20 @@ def collect_kernel_times(sg):
     return out
 
 
-def roofline(kt, iters, N_h, M, prec, nq=N_QUERIES):
+def roofline(kt, iters, N_h, M, prec, nq=N_QUERIES, peaks=None):
     """Per-kernel algorithmic work / measured time; the dominant kernel's entry
     is the roofline object.  iters and N_h are those of the nodes this rank
-    solved; nq is the number of queries it evaluated per step."""
+    solved; nq is the number of queries it evaluated per step.  peaks: the
+    probe's measured {"fp32_tflops", "fp64_tflops"} (derived figures when
+    absent)."""
+    peaks = peaks or {}
+    pk32 = peaks.get("fp32_tflops") or PEAK_FP32_TFLOPS
+    pk64 = peaks.get("fp64_tflops") or PEAK_FP64_TFLOPS
+    measured = bool(peaks.get("fp32_tflops")) and bool(peaks.get("fp64_tflops"))
     fp32 = prec != 0   # any form but SG_PREC_FP64 runs the direction in FP32
     suffix = "_fp32" if fp32 else "_fp64"
     tsize = 4 if fp32 else 8
-    peak_lin = PEAK_FP32_TFLOPS if fp32 else PEAK_FP64_TFLOPS
+    peak_lin = pk32 if fp32 else pk64
     int_units = float(np.sum(iters * N_h))           # interval-iterations per solve
     pt_units = float(np.sum(iters * (3 * N_h + 1)))  # point-iterations per solve
     seg = -(-N_h // SEG_LEN)                            # segments per node
@@ -722,7 +802,7 @@ def roofline(kt, iters, N_h, M, prec, nq=N_QUERIES):
     steps_timed = None
     models = {
         "k_condense" + suffix: ("alu", flops_condense_interval() * int_units, peak_lin, "TFLOP/s"),
-        "k_condense_reg_fp32": ("alu", flops_condense_interval() * int_units, PEAK_FP32_TFLOPS, "TFLOP/s"),
+        "k_condense_reg_fp32": ("alu", flops_condense_interval() * int_units, pk32, "TFLOP/s"),
         "k_abd" + suffix: ("alu", flops_abd_interval() * int_units, peak_lin, "TFLOP/s"),
         "k_abd_seg" + suffix: ("alu", flops_abd_seg_interval() * seg_units, peak_lin, "TFLOP/s"),
         "k_abd_red" + suffix: ("alu", flops_abd_interval() * red_units, peak_lin, "TFLOP/s"),
@@ -731,10 +811,12 @@ def roofline(kt, iters, N_h, M, prec, nq=N_QUERIES):
         "k_newton_persistent" + suffix: ("alu", (flops_condense_interval() + flops_abd_interval()
                                                   + flops_recover_interval()) * int_units, peak_lin, "TFLOP/s"),
         "k_point" + suffix: ("hbm", bytes_point(tsize) * pt_units, None, "GB/s"),
-        "k_condense_smem_fp64": ("alu", flops_condense_interval() * int_units, PEAK_FP64_TFLOPS, "TFLOP/s"),
-        "k_eval_fp64": ("alu", flops_eval_query(M, 3) * nq, PEAK_FP64_TFLOPS, "TFLOP/s"),
-        "k_eval_df32": ("alu", flops_eval_query_df32(M, 3) * nq, PEAK_FP32_TFLOPS, "TFLOP/s"),
-        "k_eval_tf32x3": ("alu", 2 * M * 3 * nq, PEAK_FP32_TFLOPS, "TFLOP/s"),
+        "k_condense_smem_fp64": ("alu", flops_condense_interval() * int_units, pk64, "TFLOP/s"),
+        # the interpolant: the method's M (2k + 1) flops per query whatever the
+        # arithmetic (pairs of floats and split TF32 do more operations)
+        "k_eval_fp64": ("alu", flops_eval_query(M, 3) * nq, pk64, "TFLOP/s"),
+        "k_eval_df32": ("alu", flops_eval_query(M, 3) * nq, pk32, "TFLOP/s"),
+        "k_eval_tf32x3": ("alu", flops_eval_query(M, 3) * nq, pk32, "TFLOP/s"),
     }
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = 6785.9
@@ -777,10 +859,11 @@ def roofline(kt, iters, N_h, M, prec, nq=N_QUERIES):
             traffic = per_unit * units / e["launches"]
         roof = {"kernel": dom, "bound": e["bound"], "achieved": e["achieved"], "peak": e["peak"],
                 "unit": e["unit"], "frac": e["frac"], "traffic": traffic,
-                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if e["unit"] == "TFLOP/s"
-                                and e["peak"] == PEAK_FP32_TFLOPS else
-                                "nominal GB300 FP64 1.25 TFLOP/s" if e["unit"] == "TFLOP/s" else
-                                "MEASURED_PEAKS.json hbm_gbs"),
+                "peak_source": ("MEASURED_PEAKS.json hbm_gbs" if e["unit"] != "TFLOP/s" else
+                                "measured in this run: FMA-chain probe (sg_fma_probe), "
+                                + ("FP32" if e["peak"] == pk32 else "FP64") if measured else
+                                "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if e["peak"] == pk32 else
+                                "nominal GB300 FP64 1.25 TFLOP/s"),
                 "share_of_gpu_time": e["share"]}
     return roof, kernels
 
@@ -796,7 +879,7 @@ def main():
     ap.add_argument("--eval", choices=["df32", "fp64", "tf32x3"], default="df32")
     ap.add_argument("--form", choices=["auto", "phase", "phase-graph", "persistent"], default="auto",
                     help="execution form of the solve (auto: the library's autotuner picks)")
-    ap.add_argument("--cpu-nodes", type=int, default=100)
+    ap.add_argument("--cpu-nodes", type=int, default=60, help="nodes of the single-core oracle sample")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
@@ -806,7 +889,7 @@ def main():
                     help="warm-up and timed steps only, one launch per phase (for kernel launch lists)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-requests", type=int, default=80)
-    ap.add_argument("--cpu-worker", nargs=2, type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-worker", nargs=4, type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_worker is not None:
         print(json.dumps(cpu_worker(*args.cpu_worker)))

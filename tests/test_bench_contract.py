@@ -81,6 +81,12 @@ def test_reference_arm_other_ranks_exit_without_work():
     assert r.stdout.strip() == ""
 
 
+def bench_host_cores():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench.host_cores()
+
+
 @pytest.mark.slow
 def test_reference_arm_json_line():
     r = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"], {})
@@ -92,7 +98,8 @@ def test_reference_arm_json_line():
         assert k in line
     assert line["unit"] == "solves/s" and line["higher_is_better"] is True
     assert line["value"] > 0
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == bench_host_cores()
+    assert line["cpu_baseline"]["cpu_model"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["e2e"]["value"] == line["value"]
 
@@ -122,6 +129,14 @@ def test_roofline_arithmetic_on_synthetic_kernel_times():
         assert kind == "interval" and abs(roof["traffic"] - per_unit * int_units / 6) <= 1e-6 * roof["traffic"]
         assert abs(sum(k["share"] for k in kernels.values()) - 1.0) <= 1e-12
         assert "achieved" not in kernels["k_ls_begin"]   # unmodelled kernels carry time and share only
+    # with the probe's measured rates the fractions divide by them
+    roof_p, _ = bench.roofline(kt, iters, N_h, M, 1, peaks={"fp32_tflops": 70.0, "fp64_tflops": 1.0})
+    assert roof_p["peak"] == 70.0 and "probe" in roof_p["peak_source"]
+    assert abs(roof_p["frac"] - roof_p["achieved"] / 70.0) <= 1e-12
+    # the interpolant's work is the method's M (2k + 1) flops per query in every mode
+    kte = {"k_eval_df32": (3.0, 1)}
+    _, ke = bench.roofline(kte, iters, N_h, 1457, 1, nq=1000, peaks={"fp32_tflops": 70.0, "fp64_tflops": 1.0})
+    assert abs(ke["k_eval_df32"]["achieved"] - 1457 * 7 * 1000 / 3e-3 / 1e12) <= 1e-12
     # the FP64 form takes the FP64 kernels' models and peak
     kt64 = {"k_condense_smem_fp64": (70.0, 6), "k_outputs": (0.1, 1)}
     roof64, _ = bench.roofline(kt64, iters, N_h, M, 0)
