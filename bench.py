@@ -365,9 +365,10 @@ def gpu_arm(args):
         form, tune_ms = sg.autotune_solve(prob, x0_d[n0:n1], T_d[n0:n1], N_d[n0:n1], tol=TOL, precision=prec,
                                           n_max=n_max, workspace=ws)
     else:
-        form = {"phase": dict(persistent=False, graph=False, blocks_per_sm=0),
-                "phase-graph": dict(persistent=False, graph=True, blocks_per_sm=0),
-                "persistent": dict(persistent=True, graph=True, blocks_per_sm=0)}[args.form]
+        form = {"phase": dict(persistent=False, graph=0, blocks_per_sm=0),
+                "phase-graph": dict(persistent=False, graph=1, blocks_per_sm=0),
+                "phase-graph-per-mesh": dict(persistent=False, graph=2, blocks_per_sm=0),
+                "persistent": dict(persistent=True, graph=1, blocks_per_sm=0)}[args.form]
     res_out = {"lambda0": torch.empty((n_loc, 6), dtype=torch.float64, device=dev),
                "u0": torch.empty((n_loc, 3), dtype=torch.float64, device=dev),
                "V": torch.empty((n_loc,), dtype=torch.float64, device=dev),
@@ -421,7 +422,7 @@ def gpu_arm(args):
         # inside a graph the library's per-launch events see only the graph
         # launch; a second timed region runs the same kernels one launch per
         # phase for the per-kernel durations and the executed-kernel count
-        phase = dict(persistent=False, graph=False, blocks_per_sm=0)
+        phase = dict(persistent=False, graph=0, blocks_per_sm=0)
         for _ in range(2):
             sharded.sharded_solve(prob, x0_d, T_d, N_d, ranges=ranges, tol=TOL, precision=prec, workspace=ws,
                                   n_max=n_max, out=res_out, **phase)
@@ -645,21 +646,34 @@ def gpu_arm(args):
                 "points": 2000, "paper": {"theorem1_bound": 3.66e4, "monte_carlo": 66.60}},
         }
 
-    # ---------------- serving: Poisson-arriving mixed requests, continuous batching
+    # ---------------- serving: Poisson-arriving mixed requests, continuous batching,
+    # swept over arrival rates to the knee of the p99 latency
     serving_rep = None
     if not args.skip_serving and rank == 0:
         from paper_1507_04769_gb300 import serving as srv
         server = srv.Server(slots=4, memory_budget=64 << 30, precision=prec, eval_mode=eval_mode)
         keys = [(2, 20.0), (3, 20.0), (4, 20.0)]
         counts = server.warm(levels=(2, 3, 4, 5), model_keys=keys)
-        reqs = srv.make_requests(args.serve_requests, rate=args.serve_rate, node_counts=counts, seed=11,
-                                 model_keys=keys)
-        server.start()
-        done = srv.replay(server, reqs, realtime=True)
-        serving_rep = {"arrival_rate_per_s": args.serve_rate, "requests": len(done), "slots": 4,
-                       "memory_budget_gb": 64, "latency": srv.latency_report(done),
+        sweep = []
+        for i, rate in enumerate(args.serve_rates):
+            reqs = srv.make_requests(args.serve_requests, rate=rate, node_counts=counts, seed=11 + i,
+                                     model_keys=keys)
+            server.start()
+            it0 = server.pool_iterations
+            t0 = time.perf_counter()
+            done = srv.replay(server, reqs, realtime=True)
+            sweep.append({"arrival_rate_per_s": rate, "requests": len(done), "wall_s": time.perf_counter() - t0,
+                          "pool_iterations": server.pool_iterations - it0,
+                          "latency": srv.latency_report(done)})
+        p99 = [e["latency"]["all"]["p99_ms"] for e in sweep]
+        knee = next((sweep[i]["arrival_rate_per_s"] for i in range(1, len(sweep)) if p99[i] > 2.0 * p99[0]), None)
+        serving_rep = {"slots": 4, "memory_budget_gb": 64, "pool_slots": srv.POOL_SLOTS,
+                       "pool_gb": server.pool.nbytes / 2 ** 30, "sweep": sweep,
+                       "p99_knee_rate_per_s": knee,
                        "sizes": "bvp 1..4096 states (full grid of level 2..5 when the draw reaches it), "
-                                "T in {10,20,40}; eval 1..1e5 queries; sim 1..1024 trajectories x 2000 steps"}
+                                "T in {10,20,40}; eval 1..1e5 queries; sim 1..1024 trajectories x 2000 steps",
+                       "batching": "bvp: solves share Newton iterations of the resident pool (mean_batch = "
+                                   "requests in the pool together); eval/sim: merged launches"}
         del server
         torch.cuda.synchronize()
 
@@ -877,7 +891,8 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "mixed-pair", "fp64"], default="mixed",
                     help="mixed: FP32 direction, FP64 residual; mixed-pair: the residual in pairs of floats")
     ap.add_argument("--eval", choices=["df32", "fp64", "tf32x3"], default="df32")
-    ap.add_argument("--form", choices=["auto", "phase", "phase-graph", "persistent"], default="auto",
+    ap.add_argument("--form", choices=["auto", "phase", "phase-graph", "phase-graph-per-mesh", "persistent"],
+                    default="auto",
                     help="execution form of the solve (auto: the library's autotuner picks)")
     ap.add_argument("--cpu-nodes", type=int, default=60, help="nodes of the single-core oracle sample")
     ap.add_argument("--skip-cpu", action="store_true")
@@ -887,8 +902,9 @@ def main():
                     help="skip the Example III value surface and the error-amplification estimates")
     ap.add_argument("--only-steps", action="store_true",
                     help="warm-up and timed steps only, one launch per phase (for kernel launch lists)")
-    ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--serve-requests", type=int, default=80)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 25.0, 50.0, 100.0, 200.0],
+                    help="arrival rates (requests/s) of the serving sweep")
+    ap.add_argument("--serve-requests", type=int, default=100, help="requests per rate of the sweep")
     ap.add_argument("--cpu-worker", nargs=4, type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_worker is not None:

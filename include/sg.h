@@ -40,7 +40,8 @@ enum {
   SG_EINVAL = 1,        /* bad argument (size, pointer, enum value)        */
   SG_ENOMEM = 2,        /* a handle could not allocate device memory       */
   SG_ECUDA = 3,         /* a CUDA call failed; message has the CUDA error  */
-  SG_EUNSUPPORTED = 4   /* valid but not supported (e.g. dimension > 8)    */
+  SG_EUNSUPPORTED = 4,  /* valid but not supported (e.g. dimension > 8)    */
+  SG_EFULL = 5          /* a solver pool has fewer free slots than asked   */
 };
 
 enum { SG_PROBLEM_ATTITUDE = 0, SG_PROBLEM_LQ = 1, SG_PROBLEM_EXAMPLE3 = 2 };
@@ -135,7 +136,18 @@ typedef struct sg_solve_opts {
                           device-side WHILE conditional nodes (no host round trip
                           per iteration).  One graph is instantiated and cached per
                           (sizes, precision, problem, buffers) the first time and
-                          replayed afterwards                                     */
+                          replayed afterwards.
+                          2: one such graph per mesh size: the nodes of each N are
+                          gathered into a sub-batch laid out for that N (inside
+                          d_work), the sub-batches run concurrently on streams of
+                          their own, and the outputs are scattered back.  Reads
+                          d_N on the host (a synchronisation).  Falls back to 1
+                          when the batch has a single mesh size or more than 8,
+                          when d_Y is given, in the persistent form, or when
+                          d_work cannot hold the sub-batches' layouts (it can
+                          whenever some N is below n_max_intervals, by a wide
+                          margin).  Results are bitwise those of graph = 1 with
+                          the same n_max_intervals                               */
   int32_t warm_start;  /* 1: start Newton from the iterate in d_Y (which must then
                           be given) instead of the zero-control guess; d_Y
                           receives the final iterate as usual                    */
@@ -240,18 +252,84 @@ int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, int64_t n,
                          double* d_V, int32_t* d_status, int32_t* d_iters, double* d_Y,
                          void* stream);
 
+/* ---------------------------------------------------------------- solver pool
+ * A resident pool of node slots for serving (the paper solves every node
+ * independently, Section 3.1, Eq. hamchar; the pool is an interface for
+ * solves that arrive over time and has no counterpart in the paper).  Each
+ * slot holds one node's Newton state (iterate, direction, factor rows) on the
+ * device for the pool's lifetime.  Solves are admitted into free slots between
+ * iterations; sg_pool_iterate advances every slot in progress by one damped
+ * Newton iteration (the slots admitted since the last call first take their
+ * initial residual), as one CUDA graph replay; slots whose solve has ended are
+ * listed by sg_pool_finished and read out (and freed) by sg_pool_collect.  So
+ * work arriving while others iterate joins at the next iteration.  Each slot's
+ * arithmetic is that of the same node in sg_solve_bvps (same kernels, per-node
+ * state, no cross-node reduction): a node's outputs are bitwise those of
+ * sg_solve_bvps with the same problem, options and n_max_intervals, whatever
+ * else is in the pool.
+ *
+ * sg_pool_workspace_bytes - device bytes of a pool of `slots` slots with
+ *   meshes of up to n_max_intervals intervals (0 for invalid arguments).
+ * sg_pool_create - builds a pool in the caller's workspace d_work (device,
+ *   256-byte aligned, at least sg_pool_workspace_bytes; caller-owned, kept
+ *   until sg_pool_free).  opts: tol, max_iter, precision and damping as for
+ *   sg_solve_bvps (persistent, blocks_per_sm and graph are ignored;
+ *   warm_start must be 0).  The problem's parameters are copied; per-node
+ *   target attitudes (d_target) are not supported.  Allocates two pinned host
+ *   arrays of `slots` entries.  Synchronises `stream`.  Errors: SG_EINVAL,
+ *   SG_ECUDA.
+ * sg_pool_free - releases the handle (not the caller's workspace).  No work
+ *   of the pool may be in flight.
+ * sg_pool_info - free slots and slots still iterating (host outputs, may be NULL).
+ * sg_pool_admit - takes `count` free slots for the solves of d_x0 (count x 6),
+ *   d_T (count), d_N (count int32; 1..n_max_intervals, else the slot ends with
+ *   SG_BADINPUT), all device arrays read before the call returns.  slots_out
+ *   (host, count entries) receives the slot of each solve.  All or nothing:
+ *   SG_EFULL when fewer than count slots are free.  Synchronises `stream`.
+ * sg_pool_iterate - one iteration of every slot in progress; *n_active (host,
+ *   may be NULL) receives the number of slots still iterating afterwards.
+ *   Admission fills the lowest free slots, and an iteration's grids span only
+ *   the smallest tier of slots (64, 128, 256, ... or all) that holds every
+ *   slot in progress; each tier's graph is instantiated on first use.
+ *   Synchronises `stream`.  A pool with no slot in progress launches nothing.
+ * sg_pool_finished - host list (up to max_count, increasing) of the slots whose
+ *   solve has ended (converged, failed or out of iterations) and that have not
+ *   been collected; *count receives its length.
+ * sg_pool_collect - writes the outputs of the finished slots `slots` (host
+ *   list of count entries) to row j of each output (device arrays as for
+ *   sg_solve_bvps: count x 6, count x 3, count, count, count) and frees those
+ *   slots.  Synchronises `stream`.  Errors: SG_EINVAL for a slot that is not
+ *   finished or is listed twice.
+ * Calls on one pool are serialised by a lock inside the handle; use one stream
+ * per pool. */
+typedef struct sg_pool sg_pool;
+size_t sg_pool_workspace_bytes(int64_t slots, int n_max_intervals, int precision);
+int sg_pool_create(const sg_problem* prob, int64_t slots, int n_max_intervals, const sg_solve_opts* opts,
+                   void* d_work, size_t work_bytes, sg_pool** out, void* stream);
+void sg_pool_free(sg_pool* pool);
+int sg_pool_info(const sg_pool* pool, int64_t* n_free, int64_t* n_busy);
+int sg_pool_admit(sg_pool* pool, const double* d_x0, const double* d_T, const int32_t* d_N, int64_t count,
+                  int64_t* slots_out, void* stream);
+int sg_pool_iterate(sg_pool* pool, int64_t* n_active, void* stream);
+int sg_pool_finished(sg_pool* pool, int64_t* slots_out, int64_t max_count, int64_t* count);
+int sg_pool_collect(sg_pool* pool, const int64_t* slots, int64_t count, double* d_lambda0, double* d_u0,
+                    double* d_V, int32_t* d_status, int32_t* d_iters, void* stream);
+
 /* sg_autotune_solve - picks the execution form of sg_solve_bvps for a batch
  * (a shape tuner; the method itself is unchanged).  It solves the caller's
- * batch with each candidate form - 0 launch per phase with a host loop, 1 the
- * same as a CUDA graph with device-side loops, 2 and 3 the persistent
+ * batch with each of the SG_AUTOTUNE_CANDIDATES candidate forms - 0 launch per
+ * phase with a host loop, 1 the same as a CUDA graph with device-side loops,
+ * 2 one such graph per mesh size (graph = 2), 3 and 4 the persistent
  * warp-per-node kernel as a graph with all / one resident block(s) per SM -
  * timing each second run with CUDA events, and returns the fastest in *best
  * (base's tolerance, iteration cap, damping and precision are kept).  The
  * choice is cached per (precision, n, n_max_intervals, tol, max_iter,
  * damping); with force = 0 a cached choice is returned without solving.
  * Arguments as for sg_solve_bvps; the outputs hold the last candidate's
- * solution.  report_ms (host, 4 entries, may be NULL) receives the timings.
+ * solution.  report_ms (host, SG_AUTOTUNE_CANDIDATES entries, may be NULL)
+ * receives the timings.
  * Synchronises `stream`.  Errors: those of sg_solve_bvps. */
+#define SG_AUTOTUNE_CANDIDATES 5
 int sg_autotune_solve(const sg_problem* prob, const double* d_x0, int64_t n, const double* d_T,
                       const int32_t* d_N, int n_max_intervals, const sg_solve_opts* base,
                       void* d_work, size_t work_bytes, double* d_lambda0, double* d_u0,

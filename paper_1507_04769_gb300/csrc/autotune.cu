@@ -4,8 +4,9 @@
 // Candidates (in this order; report_ms follows it):
 //   0  launch per phase, host-driven loop
 //   1  launch per phase as a cached CUDA graph (device-side WHILE loops)
-//   2  persistent warp-per-node kernel as a graph, as many blocks per SM as fit
-//   3  persistent warp-per-node kernel as a graph, 1 block (4 warps) per SM
+//   2  one such graph per mesh size, the sizes' sub-batches on concurrent streams
+//   3  persistent warp-per-node kernel as a graph, as many blocks per SM as fit
+//   4  persistent warp-per-node kernel as a graph, 1 block (4 warps) per SM
 // Each candidate runs once to warm up (and build its graph) and once timed
 // with CUDA events on `stream`.  The choice is cached per (precision, n,
 // n_max_intervals, tolerance, iteration cap, damping).
@@ -47,11 +48,13 @@ extern "C" int sg_autotune_solve(const sg_problem* prob, const double* d_x0, int
       return SG_OK;
     }
   }
-  sg_solve_opts cand[4] = {b, b, b, b};
+  constexpr int kCand = SG_AUTOTUNE_CANDIDATES;
+  sg_solve_opts cand[kCand] = {b, b, b, b, b};
   cand[0].persistent = 0; cand[0].graph = 0; cand[0].blocks_per_sm = 0;
   cand[1].persistent = 0; cand[1].graph = 1; cand[1].blocks_per_sm = 0;
-  cand[2].persistent = 1; cand[2].graph = 1; cand[2].blocks_per_sm = 0;
-  cand[3].persistent = 1; cand[3].graph = 1; cand[3].blocks_per_sm = 1;
+  cand[2].persistent = 0; cand[2].graph = 2; cand[2].blocks_per_sm = 0;
+  cand[3].persistent = 1; cand[3].graph = 1; cand[3].blocks_per_sm = 0;
+  cand[4].persistent = 1; cand[4].graph = 1; cand[4].blocks_per_sm = 1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
   SG_CUDA_TRY(cudaEventCreate(&e0));
@@ -59,7 +62,7 @@ extern "C" int sg_autotune_solve(const sg_problem* prob, const double* d_x0, int
   double best_ms = 1e300;
   int best_i = -1;
   int rc = SG_OK;
-  for (int c = 0; c < 4 && rc == SG_OK; ++c) {
+  for (int c = 0; c < kCand && rc == SG_OK; ++c) {
     rc = sg_solve_bvps(prob, d_x0, n, d_T, d_N, n_max_intervals, &cand[c], d_work, work_bytes, d_lambda0, d_u0,
                        d_V, d_status, d_iters, nullptr, stream);
     if (rc != SG_OK) break;

@@ -109,14 +109,11 @@ __host__ __device__ __forceinline__ int64_t npts(int Nmax) { return 3 * int64_t(
 // threads write consecutive 16-byte words); the node's first thread also
 // sets up its state.
 constexpr int kInitPer = 6;   // threads per collocation point
-__global__ void k_init(SolveArgs a, Workspace w) {
-  const int64_t P = npts(a.Nmax);
-  const int64_t u = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (u >= a.n * P * kInitPer) return;
-  const int64_t t = u / kInitPer;
-  const int q = static_cast<int>(u % kInitPer);   // components 2q, 2q + 1
-  const int64_t node = t / P;
-  const int64_t p = t % P;
+
+// Components 2q, 2q + 1 of point p of `node` (u = its global pair index);
+// the point-0, q-0 thread also sets up the node's state.
+__device__ __forceinline__ void init_pair(const SolveArgs& a, const Workspace& w, int64_t node, int64_t p, int q,
+                                          int64_t u) {
   const double* x0 = a.x0 + node * 6;
   double2 y;
   if (a.Yin) {
@@ -141,6 +138,14 @@ __global__ void k_init(SolveArgs a, Workspace w) {
     s.status = ok ? SG_MAXITER : SG_BADINPUT;
     w.ns[node] = s;
   }
+}
+
+__global__ void k_init(SolveArgs a, Workspace w) {
+  const int64_t P = npts(a.Nmax);
+  const int64_t u = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (u >= a.n * P * kInitPer) return;
+  const int64_t t = u / kInitPer;
+  init_pair(a, w, t / P, t % P, static_cast<int>(u % kInitPer), u);
 }
 
 // ---------------------------------------------------------------- residual
@@ -1470,21 +1475,20 @@ __global__ void k_after_update(SolveArgs a, Workspace w) {
 }
 
 // Outputs (Eq. optuv): lambda(0), u*(x0, lambda(0)), V = z(T) + h(x(T)) with
-// z(T) = h sum_i sum_j b_j L(Y_ij) (the Lobatto IIIA step of z' = L).
-__global__ void k_outputs(SolveArgs a, Workspace w, double* lambda0, double* u0, double* V,
-                          int32_t* status, int32_t* iters) {
-  const int lane = threadIdx.x & 31;
-  const int64_t node = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  if (node >= a.n) return;
+// z(T) = h sum_i sum_j b_j L(Y_ij) (the Lobatto IIIA step of z' = L).  One
+// warp per node; the results go to output row `row`.
+__device__ __forceinline__ void node_outputs(const SolveArgs& a, const Workspace& w, int64_t node, int64_t row,
+                                             int lane, double* lambda0, double* u0, double* V, int32_t* status,
+                                             int32_t* iters) {
   const NodeState s = w.ns[node];
   const double* Y = w.Y + node * npts(a.Nmax) * 12;
   if (s.status == SG_BADINPUT) {
     if (lane == 0) {
-      for (int c = 0; c < 6; ++c) lambda0[node * 6 + c] = NAN;
-      for (int c = 0; c < 3; ++c) u0[node * 3 + c] = NAN;
-      V[node] = NAN;
-      status[node] = s.status;
-      iters[node] = 0;
+      for (int c = 0; c < 6; ++c) lambda0[row * 6 + c] = NAN;
+      for (int c = 0; c < 3; ++c) u0[row * 3 + c] = NAN;
+      V[row] = NAN;
+      status[row] = s.status;
+      iters[row] = 0;
     }
     return;
   }
@@ -1500,14 +1504,22 @@ __global__ void k_outputs(SolveArgs a, Workspace w, double* lambda0, double* u0,
   z = warp_sum(z);
   if (lane == 0) {
     const double* yN = Y + 3 * int64_t(N) * 12;
-    V[node] = z + terminal_cost(a.P, yN);
+    V[row] = z + terminal_cost(a.P, yN);
     double u[3];
     optimal_control(a.P, Y, Y + 6, u);
-    for (int c = 0; c < 6; ++c) lambda0[node * 6 + c] = Y[6 + c];
-    for (int c = 0; c < 3; ++c) u0[node * 3 + c] = u[c];
-    status[node] = s.status;
-    iters[node] = s.iters;
+    for (int c = 0; c < 6; ++c) lambda0[row * 6 + c] = Y[6 + c];
+    for (int c = 0; c < 3; ++c) u0[row * 3 + c] = u[c];
+    status[row] = s.status;
+    iters[row] = s.iters;
   }
+}
+
+__global__ void k_outputs(SolveArgs a, Workspace w, double* lambda0, double* u0, double* V,
+                          int32_t* status, int32_t* iters) {
+  const int lane = threadIdx.x & 31;
+  const int64_t node = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  if (node >= a.n) return;
+  node_outputs(a, w, node, node, lane, lambda0, u0, V, status, iters);
 }
 
 __global__ void k_copy_Y(SolveArgs a, Workspace w, double* out) {

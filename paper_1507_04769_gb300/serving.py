@@ -9,16 +9,25 @@ Three request kinds arrive over time:
   * eval  - u*(x) at Q query states from a resident model (1..1e5 queries);
   * sim   - closed-loop simulations from a resident model (1..1024
             trajectories, zero-order hold + RK4, Section 5).
-The server keeps grids, surplus models and per-shape solver workspaces
-resident on the device.  A dispatcher admits queued work whenever a worker
-slot is free and the device-memory budget covers the work's footprint
-(first fit from the queue, so a large request does not block small ones).
-Compatible queued requests (same kind and shape: BVP with the same horizon,
-mesh and precision; evals or simulations of the same model) are merged into
-one launch when a slot picks them up, and their results are split back.
-Each slot owns a CUDA stream, so the work of different slots overlaps on the
-device.  Because every node, query and trajectory is computed independently,
-a request's result is the same alone and inside any merged batch.
+
+BVP solves run in a resident solver pool (sg.SolverPool): a fixed set of node
+slots whose Newton state stays on the device.  One engine thread admits the
+queued BVP requests into free slots (first come, first served), advances every
+slot by one Newton iteration per pool iteration, and hands each request its
+results when all of its nodes have finished.  A request that arrives while
+others are iterating joins them at the next iteration, and slots freed by
+finished nodes are refilled at once (continuous batching at Newton-iteration
+granularity).  The pool's memory is reserved when the server starts.
+
+Evaluations and simulations run on worker slots, each with its own CUDA
+stream, so their work overlaps with the pool's and with each other's on the
+device.  A worker takes the first queued request whose footprint fits the
+device-memory budget left beside the pool (so a large request does not block
+small ones), and merges compatible queued requests (same kind and model) into
+one launch.  Grids and surplus models stay resident.
+
+Every node, query and trajectory is computed independently, so a request's
+result is bitwise the same alone and in any mix.
 """
 from __future__ import annotations
 
@@ -35,7 +44,8 @@ import synth
 from . import sg
 
 MAX_BVP_STATES = 4096
-MAX_BVP_MERGE = 8192          # nodes per merged solve
+POOL_SLOTS = 8192             # node slots of the resident solver pool (a level-5 grid has 4865)
+POOL_NMAX = 256               # mesh intervals per slot (T = 40)
 MAX_EVAL_MERGE = 400_000      # queries per merged evaluation
 MAX_SIM_MERGE = 2048          # trajectories per merged simulation
 
@@ -72,16 +82,16 @@ class Model:
 
 class Server:
     def __init__(self, params=None, *, slots=4, memory_budget=32 << 30, precision=sg.PREC_MIXED,
-                 eval_mode=sg.EVAL_DF32, tol=1e-8, merge=True, device=None):
+                 eval_mode=sg.EVAL_DF32, tol=1e-8, merge=True, device=None, pool_slots=POOL_SLOTS,
+                 pool_nmax=POOL_NMAX):
         self.params = params if params is not None else synth.attitude_params(0)
         self.problem = sg.problem_from(self.params)
         self.lo, self.hi = synth.box(6)
         self.precision, self.eval_mode, self.tol = precision, eval_mode, tol
         self.merge = merge
         self.device = device or torch.device("cuda", torch.cuda.current_device())
-        self.budget = int(memory_budget)
-        self.in_use = 0
-        self.queue: deque[Request] = deque()
+        self.queue: deque[Request] = deque()        # eval and sim requests
+        self.bvp_queue: deque[Request] = deque()    # BVP requests waiting for pool slots
         self.cv = threading.Condition()
         self.models: dict[tuple, Model] = {}
         self.grids: dict[int, sg.Grid] = {}
@@ -93,6 +103,15 @@ class Server:
         self.workers = []
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
         self.errors: list[BaseException] = []
+        # the resident solver pool: its memory is reserved out of the budget
+        self.pool_nmax = int(pool_nmax)
+        self.pool = sg.SolverPool(self.problem, pool_slots, self.pool_nmax, tol=tol, precision=precision,
+                                  device=self.device)
+        self.pool_stream = torch.cuda.Stream(device=self.device)
+        self.budget = max(int(memory_budget) - self.pool.nbytes, 0)
+        self.in_use = 0
+        self.in_pool: dict[int, tuple] = {}          # rid -> (request, slots)
+        self.pool_iterations = 0
 
     # ------------------------------------------------------------ resident state
     def warm(self, levels=(2, 3, 4, 5), model_keys=()):
@@ -115,7 +134,8 @@ class Server:
         g = self.grid(level)
         N = horizon_mesh(T)
         with torch.cuda.stream(stream or torch.cuda.current_stream()):
-            res = sg.solve_bvps(self.problem, g.coords, T, N, tol=self.tol, precision=self.precision, n_max=N)
+            res = sg.solve_bvps(self.problem, g.coords, T, N, tol=self.tol, precision=self.precision,
+                                n_max=self.pool_nmax)
             S = sg.Surplus(g, res["u0"])
         self.models[(level, T)] = Model(g, S, T)
         return res
@@ -125,24 +145,20 @@ class Server:
 
     # ------------------------------------------------------------ footprints
     def footprint(self, reqs) -> int:
+        """Device bytes of an eval or sim batch (BVP solves live in the pool)."""
         r = reqs[0]
         n = sum(q.x.shape[0] for q in reqs)
-        if r.kind == "bvp":
-            N = horizon_mesh(r.T)
-            return sg.workspace_bytes(n, N, self.precision) + n * 8 * 20
         if r.kind == "eval":
             return n * 8 * (6 + 3) * 2
         return n * 8 * (6 + 6 + 1)
 
     def merge_key(self, r: Request):
-        if r.kind == "bvp":
-            return ("bvp", r.T, r.full_grid and r.level)
         return (r.kind, r.level, r.T)
 
     # ------------------------------------------------------------ queue
     def submit(self, req: Request):
         with self.cv:
-            self.queue.append(req)
+            (self.bvp_queue if req.kind == "bvp" else self.queue).append(req)
             self.cv.notify_all()
 
     def _take(self):
@@ -152,13 +168,12 @@ class Server:
             if r.kind in ("eval", "sim") and (r.level, r.T) not in self.models:
                 continue   # its model is being built: leave it queued
             batch = [r]
-            if self.merge and not (r.kind == "bvp" and r.full_grid):
+            if self.merge:
                 key = self.merge_key(r)
-                cap = {"bvp": MAX_BVP_MERGE, "eval": MAX_EVAL_MERGE, "sim": MAX_SIM_MERGE}[r.kind]
+                cap = {"eval": MAX_EVAL_MERGE, "sim": MAX_SIM_MERGE}[r.kind]
                 tot = r.x.shape[0]
                 for q in list(self.queue)[i + 1:]:
-                    if self.merge_key(q) == key and not (q.kind == "bvp" and q.full_grid) and \
-                            tot + q.x.shape[0] <= cap:
+                    if self.merge_key(q) == key and tot + q.x.shape[0] <= cap:
                         batch.append(q)
                         tot += q.x.shape[0]
             need = self.footprint(batch)
@@ -175,15 +190,7 @@ class Server:
         x = torch.as_tensor(np.concatenate([q.x for q in batch]), dtype=torch.float64)
         with torch.cuda.stream(stream):
             xd = x.pin_memory().to(self.device, non_blocking=True)
-            if r.kind == "bvp":
-                N = horizon_mesh(r.T)
-                if r.full_grid:
-                    res = self.build_model(r.level, r.T, stream)
-                else:
-                    res = sg.solve_bvps(self.problem, xd, r.T, N, tol=self.tol, precision=self.precision, n_max=N,
-                                        stream=stream)
-                out = {k: res[k].cpu() for k in ("lambda0", "u0", "V", "status", "iters")}
-            elif r.kind == "eval":
+            if r.kind == "eval":
                 m = self.models[(r.level, r.T)]
                 u = sg.eval_feedback(m.surplus, xd, mode=self.eval_mode, stream=stream)
                 out = {"u": u.cpu()}
@@ -226,12 +233,101 @@ class Server:
                 self.completed.extend(batch)
                 self.cv.notify_all()
 
+    # ------------------------------------------------------------ BVP engine
+    def _admit_bvp(self):
+        """Admits queued BVP requests in arrival order while the pool has room
+        (caller holds the lock).  Returns the requests admitted."""
+        admitted = []
+        n_free, _ = self.pool.info()
+        while self.bvp_queue:
+            r = self.bvp_queue[0]
+            n = r.x.shape[0]
+            if n > n_free:
+                break
+            self.bvp_queue.popleft()
+            admitted.append(r)
+            n_free -= n
+        return admitted
+
+    def _bvp_engine(self):
+        torch.cuda.set_device(self.device)
+        st = self.pool_stream
+        while True:
+            with self.cv:
+                while True:
+                    batch = self._admit_bvp()
+                    if batch or self.in_pool:
+                        break
+                    if self.stop and not self.bvp_queue:
+                        return
+                    self.cv.wait(timeout=0.01)
+            try:
+                t = self.now()
+                for r in batch:
+                    r.admitted = t
+                    with torch.cuda.stream(st):
+                        if r.full_grid:
+                            x0 = self.grid(r.level).coords
+                        else:
+                            x0 = torch.as_tensor(r.x, dtype=torch.float64).pin_memory().to(self.device,
+                                                                                           non_blocking=True)
+                        n = x0.shape[0]
+                        T = torch.full((n,), r.T, dtype=torch.float64, device=self.device)
+                        N = torch.full((n,), horizon_mesh(r.T), dtype=torch.int32, device=self.device)
+                        slots = self.pool.admit(x0, T, N, stream=st)
+                    self.in_pool[r.rid] = (r, slots)
+                    r.batch_size = 0
+                live = len(self.in_pool)
+                for r, _ in self.in_pool.values():
+                    r.batch_size = max(r.batch_size, live)   # requests sharing the pool iterations
+                self.pool.iterate(stream=st)
+                self.pool_iterations += 1
+                done = set(self.pool.finished().tolist())
+                finished = []
+                for rid, (r, slots) in list(self.in_pool.items()):
+                    if set(slots.tolist()) <= done:
+                        out = self.pool.collect(slots, stream=st)
+                        if r.full_grid:
+                            g = self.grid(r.level)
+                            with torch.cuda.stream(st):
+                                S = sg.Surplus(g, out["u0"], stream=st)
+                            st.synchronize()   # built before other streams can use the model
+                            self.models[(r.level, r.T)] = Model(g, S, r.T)
+                        with torch.cuda.stream(st):
+                            r.result = {k: v.cpu().numpy() for k, v in out.items()}
+                        del self.in_pool[rid]
+                        finished.append(r)
+                t = self.now()
+                for r in finished:
+                    r.done = t
+            except BaseException as e:   # recorded and re-raised by drain()
+                self.errors.append(e)
+                with self.cv:
+                    for r, _ in self.in_pool.values():
+                        r.done = self.now()
+                        self.completed.append(r)
+                    self.in_pool.clear()
+                    self.bvp_queue.clear()
+                    self.cv.notify_all()
+                return
+            with self.cv:
+                self.completed.extend(finished)
+                self.cv.notify_all()
+
     def start(self):
+        """Starts the workers and the BVP engine; a drained server can be
+        started again (resident grids, models and the pool are kept)."""
+        self.stop = False
+        self.completed = []
+        self.workers = []
         self.t0 = time.perf_counter()
         for s in range(self.n_slots):
             th = threading.Thread(target=self._worker, args=(s,), daemon=True)
             th.start()
             self.workers.append(th)
+        th = threading.Thread(target=self._bvp_engine, daemon=True)
+        th.start()
+        self.workers.append(th)
 
     def drain(self, timeout=600.0):
         with self.cv:

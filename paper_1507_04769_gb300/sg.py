@@ -15,7 +15,7 @@ import torch
 from . import build as _build
 
 # --------------------------------------------------------------- constants
-SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_EUNSUPPORTED = 0, 1, 2, 3, 4
+SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_EUNSUPPORTED, SG_EFULL = 0, 1, 2, 3, 4, 5
 PROBLEM_ATTITUDE, PROBLEM_LQ, PROBLEM_EXAMPLE3 = 0, 1, 2
 # FP64; FP32 direction with an FP64 residual; FP32 direction with a pair-of-floats residual
 PREC_FP64, PREC_MIXED, PREC_MIXED_PAIR = 0, 1, 2
@@ -74,6 +74,20 @@ def _load():
     lib.sg_sincos_probe.argtypes = [P, I64, P, P, P]
     lib.sg_attitude_targets.argtypes = [C.POINTER(Problem), P, I64, P, P, P]
     lib.sg_attitude_targets.restype = C.c_int
+    lib.sg_pool_workspace_bytes.argtypes = [I64, I32, I32]
+    lib.sg_pool_workspace_bytes.restype = C.c_size_t
+    lib.sg_pool_create.argtypes = [C.POINTER(Problem), I64, I32, C.POINTER(SolveOpts), P, C.c_size_t,
+                                   C.POINTER(P), P]
+    lib.sg_pool_free.argtypes = [P]
+    lib.sg_pool_free.restype = None
+    lib.sg_pool_info.argtypes = [P, C.POINTER(I64), C.POINTER(I64)]
+    lib.sg_pool_admit.argtypes = [P, P, P, P, I64, P, P]
+    lib.sg_pool_iterate.argtypes = [P, C.POINTER(I64), P]
+    lib.sg_pool_finished.argtypes = [P, P, I64, C.POINTER(I64)]
+    lib.sg_pool_collect.argtypes = [P, P, I64, P, P, P, P, P, P]
+    for name in ("sg_pool_create", "sg_pool_info", "sg_pool_admit", "sg_pool_iterate", "sg_pool_finished",
+                 "sg_pool_collect"):
+        getattr(lib, name).restype = C.c_int
     lib.sg_theorem1_bound.argtypes = [I32, I32, C.POINTER(D)]
     lib.sg_theorem1_bound.restype = C.c_int
     for name in ("sg_build_grid", "sg_grid_info", "sg_solve_bvps", "sg_build_surpluses",
@@ -189,6 +203,7 @@ def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=5
     """sg_solve_bvps on device tensors.  x0 (n, 6) f64; T (n,) f64; N (n,) int32.
     `out` may hold preallocated output tensors (keys lambda0, u0, V, status,
     iters); reusing them (and the workspace) lets graph=True replay one graph.
+    graph: 0 host loop, 1 (or True) one cached graph, 2 one graph per mesh size.
     Y0 (n, 3 n_max + 1, 12) f64: warm start from this iterate; it is
     overwritten with the final iterate (and returned as "Y")."""
     x0 = _dev(x0, torch.float64).reshape(-1, 6)
@@ -217,7 +232,7 @@ def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=5
         Y = torch.zeros((n, 3 * n_max + 1, 12), dtype=torch.float64, device=dev) if return_Y else None
     opts = SolveOpts(tol=tol, max_iter=max_iter, precision=precision, damping=int(bool(damping)),
                      persistent=int(bool(persistent)), blocks_per_sm=int(blocks_per_sm),
-                     graph=int(bool(graph)), warm_start=int(Y0 is not None))
+                     graph=int(graph), warm_start=int(Y0 is not None))
     _check(LIB.sg_solve_bvps(C.byref(problem), _ptr(x0), n, _ptr(T), _ptr(N), n_max, C.byref(opts),
                              _ptr(workspace), workspace.numel(), _ptr(out["lambda0"]), _ptr(out["u0"]),
                              _ptr(out["V"]), _ptr(out["status"]), _ptr(out["iters"]),
@@ -227,7 +242,7 @@ def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=5
     return out
 
 
-FORM_NAMES = ["phase-host-loop", "phase-graph", "persistent-graph", "persistent-graph-1blk"]
+FORM_NAMES = ["phase-host-loop", "phase-graph", "phase-graph-per-mesh", "persistent-graph", "persistent-graph-1blk"]
 
 
 def autotune_solve(problem: Problem, x0, T, N, *, tol=1e-8, max_iter=50, precision=PREC_FP64,
@@ -247,12 +262,87 @@ def autotune_solve(problem: Problem, x0, T, N, *, tol=1e-8, max_iter=50, precisi
             torch.empty((n,), dtype=torch.int32, device=dev)]
     base = SolveOpts(tol=tol, max_iter=max_iter, precision=precision, damping=int(bool(damping)))
     best = SolveOpts()
-    ms = (C.c_double * 4)(*([float("nan")] * 4))
+    nc = len(FORM_NAMES)
+    ms = (C.c_double * nc)(*([float("nan")] * nc))
     _check(LIB.sg_autotune_solve(C.byref(problem), _ptr(x0), n, _ptr(T), _ptr(N), n_max, C.byref(base),
                                  _ptr(workspace), workspace.numel(), *[_ptr(t) for t in outs], C.byref(best),
                                  ms, int(bool(force)), _stream(stream)))
-    choice = {"persistent": bool(best.persistent), "graph": bool(best.graph), "blocks_per_sm": best.blocks_per_sm}
-    return choice, {FORM_NAMES[i]: ms[i] for i in range(4)}
+    choice = {"persistent": bool(best.persistent), "graph": int(best.graph), "blocks_per_sm": best.blocks_per_sm}
+    return choice, {FORM_NAMES[i]: ms[i] for i in range(nc)}
+
+
+class SolverPool:
+    """sg_pool_*: resident Newton state for `slots` nodes; solves join and
+    leave between iterations (continuous batching).  The workspace is a torch
+    allocation owned by this object."""
+
+    def __init__(self, problem: Problem, slots: int, n_max: int, *, tol=1e-8, max_iter=50,
+                 precision=PREC_MIXED, damping=True, device=None, stream=None):
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.slots, self.n_max, self.precision = int(slots), int(n_max), precision
+        nbytes = int(LIB.sg_pool_workspace_bytes(self.slots, self.n_max, precision))
+        if nbytes == 0:
+            raise SGError("sg_pool_workspace_bytes: invalid pool size or precision")
+        self.nbytes = nbytes
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self._problem = problem   # kept alive with the handle
+        opts = SolveOpts(tol=tol, max_iter=max_iter, precision=precision, damping=int(bool(damping)))
+        h = C.c_void_p()
+        _check(LIB.sg_pool_create(C.byref(problem), self.slots, self.n_max, C.byref(opts), _ptr(self.workspace),
+                                  nbytes, C.byref(h), _stream(stream)))
+        self._h = h
+
+    def info(self):
+        f, b = C.c_int64(), C.c_int64()
+        _check(LIB.sg_pool_info(self._h, C.byref(f), C.byref(b)))
+        return f.value, b.value
+
+    def admit(self, x0, T, N, stream=None) -> np.ndarray:
+        """Admits the solves of the rows of x0; returns their slots (int64).
+        Raises SGError with code SG_EFULL when too few slots are free."""
+        x0 = _dev(x0, torch.float64, self.device).reshape(-1, 6)
+        n = x0.shape[0]
+        T = _dev(T, torch.float64, self.device).reshape(-1).expand(n).contiguous()
+        N = _dev(N, torch.int32, self.device).reshape(-1).expand(n).contiguous()
+        slots = np.empty(n, dtype=np.int64)
+        rc = LIB.sg_pool_admit(self._h, _ptr(x0), _ptr(T), _ptr(N), n, slots.ctypes.data_as(C.c_void_p),
+                               _stream(stream))
+        if rc == SG_EFULL:
+            raise SGError(f"libsg error {rc}: {LIB.sg_last_error().decode()}")
+        _check(rc)
+        return slots
+
+    def iterate(self, stream=None) -> int:
+        """One Newton iteration of every slot in progress; returns how many still iterate."""
+        a = C.c_int64()
+        _check(LIB.sg_pool_iterate(self._h, C.byref(a), _stream(stream)))
+        return a.value
+
+    def finished(self) -> np.ndarray:
+        out = np.empty(self.slots, dtype=np.int64)
+        c = C.c_int64()
+        _check(LIB.sg_pool_finished(self._h, out.ctypes.data_as(C.c_void_p), self.slots, C.byref(c)))
+        return out[:c.value].copy()
+
+    def collect(self, slots, out=None, stream=None) -> dict:
+        """Outputs of the finished `slots` (row j = slots[j]); frees them."""
+        slots = np.ascontiguousarray(slots, dtype=np.int64)
+        n = slots.shape[0]
+        if out is None:
+            out = {"lambda0": torch.empty((n, 6), dtype=torch.float64, device=self.device),
+                   "u0": torch.empty((n, 3), dtype=torch.float64, device=self.device),
+                   "V": torch.empty((n,), dtype=torch.float64, device=self.device),
+                   "status": torch.empty((n,), dtype=torch.int32, device=self.device),
+                   "iters": torch.empty((n,), dtype=torch.int32, device=self.device)}
+        _check(LIB.sg_pool_collect(self._h, slots.ctypes.data_as(C.c_void_p), n, _ptr(out["lambda0"]),
+                                   _ptr(out["u0"]), _ptr(out["V"]), _ptr(out["status"]), _ptr(out["iters"]),
+                                   _stream(stream)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and LIB is not None:
+            LIB.sg_pool_free(self._h)
+            self._h = None
 
 
 # --------------------------------------------------------------- Step III

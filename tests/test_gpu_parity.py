@@ -256,6 +256,28 @@ def test_graph_replay_reuses_buffers(att_case, persistent):
             assert torch.equal(out[key], ref[key]), (rep, key)
 
 
+@pytest.mark.parametrize("prec", [sg.PREC_MIXED, sg.PREC_FP64], ids=["mixed", "fp64"])
+def test_graph_per_mesh_size_matches_one_graph_bitwise(prec):
+    """graph = 2 (the nodes of each mesh size gathered into a sub-batch with a
+    graph and a stream of its own) gives bitwise the one-graph results, on a
+    batch of three mesh sizes, with invalid inputs among the nodes."""
+    params = synth.attitude_params(0)
+    prob = sg.problem_from(params)
+    X0 = synth.uniform_queries(300, LO, HI, seed=61)
+    T, N = synth.mixed_horizons(300, seed=62)
+    N = N.copy()
+    N[7] = 300                                   # above n_max: SG_BADINPUT
+    X0[11, 2] = np.nan                           # non-finite state: SG_BADINPUT
+    args = (prob, cuda(X0), cuda(T), cuda(N, torch.int32))
+    one = sg.solve_bvps(*args, precision=prec, graph=1, n_max=256)
+    for rep in range(2):                         # the second call replays the cached graphs
+        per = sg.solve_bvps(*args, precision=prec, graph=2, n_max=256)
+        for key in ("lambda0", "u0", "V", "status", "iters"):
+            assert torch.equal(torch.nan_to_num(one[key]), torch.nan_to_num(per[key])), (rep, key)
+    st = one["status"].cpu().numpy()
+    assert st[7] == sg.BADINPUT and st[11] == sg.BADINPUT and np.sum(st == sg.CONVERGED) == 298
+
+
 def test_autotuner_picks_a_form_and_caches_it(att_case):
     params, X0, T, N, _ = att_case
     prob = sg.problem_from(params)
