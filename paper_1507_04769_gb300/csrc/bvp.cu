@@ -189,13 +189,12 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
   const unsigned gseg_blk = static_cast<unsigned>(ceil_div(a.n * seg_count(a.Nmax), seg_warps<T>()));
   const size_t cond_smem = sizeof(double) * kCondWarps * 36 * kCols;
   if constexpr (sizeof(T) == sizeof(double)) {
-    SG_CUDA_TRY(cudaFuncSetAttribute(k_condense_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(cond_smem)));
+    SG_CUDA_TRY(ensure_dynamic_smem(k_condense_smem, static_cast<int>(cond_smem)));
   }
   if (a.persistent) {
     // one warp per node, nodes from a device queue, no host round trip
     const int smem = 4 * persist_smem_per_warp<T>();
-    SG_CUDA_TRY(cudaFuncSetAttribute(k_newton_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    SG_CUDA_TRY(ensure_dynamic_smem(k_newton_persistent<T>, smem));
     int dev = 0, sms = 0, per_sm = 0;
     SG_CUDA_TRY(cudaGetDevice(&dev));
     SG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -457,7 +456,7 @@ static int launch_solve_graph(const SolveArgs& a, Workspace w, cudaStream_t st, 
   int smem = 0;
   if (a.persistent) {
     smem = 4 * persist_smem_per_warp<T>();
-    SG_CUDA_TRY(cudaFuncSetAttribute(k_newton_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    SG_CUDA_TRY(ensure_dynamic_smem(k_newton_persistent<T>, smem));
     int sms = 0, per_sm = 0;
     SG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton_persistent<T>, 128, smem));
@@ -466,8 +465,7 @@ static int launch_solve_graph(const SolveArgs& a, Workspace w, cudaStream_t st, 
     const int64_t want = ceil_div(a.n, 4);
     grid = static_cast<unsigned>(want < int64_t(sms) * per_sm ? want : int64_t(sms) * per_sm);
   } else if constexpr (sizeof(T) == sizeof(double)) {
-    SG_CUDA_TRY(cudaFuncSetAttribute(k_condense_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(sizeof(double) * kCondWarps * 36 * kCols)));
+    SG_CUDA_TRY(ensure_dynamic_smem(k_condense_smem, static_cast<int>(sizeof(double) * kCondWarps * 36 * kCols)));
   }
   // key: every byte that is baked into the graph's kernel parameters
   GraphKey key;
@@ -1079,8 +1077,7 @@ extern "C" int sg_pool_create(const sg_problem* prob, int64_t slots, int n_max_i
   if ((e = cudaMemsetAsync(base + L.x0, 0, L.ws - L.x0, st)) != cudaSuccess)
     return bail(e, "sg_pool_create: clearing the inputs");
   if (!p->fp32) {
-    if ((e = cudaFuncSetAttribute(k_condense_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(sizeof(double) * kCondWarps * 36 * kCols))) != cudaSuccess)
+    if ((e = ensure_dynamic_smem(k_condense_smem, static_cast<int>(sizeof(double) * kCondWarps * 36 * kCols))) != cudaSuccess)
       return bail(e, "sg_pool_create: condensation shared memory");
   }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(e, "sg_pool_create");

@@ -196,12 +196,10 @@ extern "C" int sg_simulate_closed_loop(const sg_problem* prob, const sg_surplus*
   const size_t smem = size_t(kClWarps) * c.d * c.e.nf * 8;
   const unsigned grid = static_cast<unsigned>(ceil_div(ntraj, kClWarps));
   if (mode == SG_EVAL_DF32) {
-    SG_CUDA_TRY(cudaFuncSetAttribute(k_closed_loop<SG_EVAL_DF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(smem)));
+    SG_CUDA_TRY(ensure_dynamic_smem(k_closed_loop<SG_EVAL_DF32>, static_cast<int>(smem)));
     SG_TIMED("k_closed_loop_df32", st, (k_closed_loop<SG_EVAL_DF32><<<grid, 32 * kClWarps, smem, st>>>(c)));
   } else {
-    SG_CUDA_TRY(cudaFuncSetAttribute(k_closed_loop<SG_EVAL_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(smem)));
+    SG_CUDA_TRY(ensure_dynamic_smem(k_closed_loop<SG_EVAL_FP64>, static_cast<int>(smem)));
     SG_TIMED("k_closed_loop_fp64", st, (k_closed_loop<SG_EVAL_FP64><<<grid, 32 * kClWarps, smem, st>>>(c)));
   }
   SG_LAUNCH_CHECK("k_closed_loop");

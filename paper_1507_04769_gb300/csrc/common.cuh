@@ -37,6 +37,26 @@ inline int cuda_fail(cudaError_t e, const char* where) {
     if (_e != cudaSuccess) return ::sg::cuda_fail(_e, name);    \
   } while (0)
 
+// Lets `func` launch with `bytes` of dynamic shared memory.  Above the default
+// 48 KB the cap is raised to the most the device allows (less the kernel's
+// static shared memory), always to the same value: host threads that launch
+// the same kernel with different sizes concurrently can then never lower the
+// cap below another thread's launch.
+template <typename F>
+inline cudaError_t ensure_dynamic_smem(F* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(func));
+  if (e != cudaSuccess) return e;
+  const int cap = optin - static_cast<int>(fa.sharedSizeBytes);
+  if (static_cast<long long>(bytes) > cap) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(func), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              cap);
+}
+
 constexpr int kMaxDim = 8;
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs
 

@@ -211,8 +211,7 @@ static int launch_eval_fp64(const EvalArgs& e, cudaStream_t st) {
   const unsigned blocks = static_cast<unsigned>(ceil_div(e.Q, kEvalThreads));
 #define SG_EVAL_K(KK)                                                                              \
   case KK:                                                                                         \
-    SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_fp64<D, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     static_cast<int>(smem)));                                     \
+    SG_CUDA_TRY(ensure_dynamic_smem(k_eval_fp64<D, KK>, smem));                                  \
     SG_TIMED("k_eval_fp64", st, (k_eval_fp64<D, KK><<<blocks, kEvalThreads, smem, st>>>(e)));      \
     break;
   switch (e.k) {
@@ -222,8 +221,7 @@ static int launch_eval_fp64(const EvalArgs& e, cudaStream_t st) {
     SG_EVAL_K(4)
     SG_EVAL_K(6)
     default:
-      SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_fp64_anyk<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem)));
+      SG_CUDA_TRY(ensure_dynamic_smem(k_eval_fp64_anyk<D>, static_cast<int>(smem)));
       SG_TIMED("k_eval_fp64", st, (k_eval_fp64_anyk<D><<<blocks, kEvalThreads, smem, st>>>(e)));
   }
 #undef SG_EVAL_K

@@ -216,8 +216,7 @@ static size_t df32_smem(const EvalArgs& e, int d) {
 template <int K, int QB>
 static int launch_df32_kq(const EvalArgs& e, int d, size_t smem, cudaStream_t st) {
   const unsigned blocks = static_cast<unsigned>(ceil_div(e.Q, QB));
-  SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_df32<K, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   static_cast<int>(smem)));
+  SG_CUDA_TRY(ensure_dynamic_smem(k_eval_df32<K, QB>, smem));
   SG_TIMED("k_eval_df32", st, (k_eval_df32<K, QB><<<blocks, kDfThreads, smem, st>>>(e, d)));
   SG_LAUNCH_CHECK("k_eval_df32");
   return SG_OK;

@@ -325,8 +325,7 @@ int eval_tf32x3(const EvalArgs& e, const sg_surplus* s, cudaStream_t st) {
   t.err = s->tc_err;
   const size_t smem = 4 * kTcABytes + 4 * kTcBBytes + sizeof(float) * s->d * s->nf * kTcRows + 64;
   if (smem > 227 * 1024) return fail(SG_EUNSUPPORTED, "sg_eval_feedback: grid level too high for TF32X3");
-  SG_CUDA_TRY(cudaFuncSetAttribute(k_eval_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   static_cast<int>(smem)));
+  SG_CUDA_TRY(ensure_dynamic_smem(k_eval_tf32x3, static_cast<int>(smem)));
   const unsigned blocks = static_cast<unsigned>(ceil_div(e.Q, kTcRows));
   SG_TIMED("k_eval_tf32x3", st, (k_eval_tf32x3<<<blocks, kTcThreads, smem, st>>>(t)));
   SG_LAUNCH_CHECK("k_eval_tf32x3");

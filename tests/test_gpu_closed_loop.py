@@ -80,3 +80,42 @@ def test_closed_loop_bad_arguments():
     with pytest.raises(sg.SGError):
         sg.simulate_closed_loop(sg.problem_from(synth.attitude_params(0)), S1,
                                 torch.zeros((1, 6), dtype=torch.float64, device="cuda"), 10, 0.01)
+
+
+def test_concurrent_host_threads_with_different_levels():
+    """Host threads launching the same kernels with different shared-memory
+    sizes at once (closed loops and evaluations of a level-2 and a level-4
+    model, each thread on its own stream): no launch fails, and each result is
+    bitwise the one computed alone."""
+    import threading
+    prob = sg.problem_from(synth.attitude_params(0))
+    surf = {}
+    for L in (2, 4):
+        g = sg.Grid(6, L, LO, HI)
+        surf[L] = (g, sg.Surplus(g, torch.as_tensor(feedback_values(g.coords.cpu().numpy()), device="cuda")))
+    x0 = torch.as_tensor(synth.mixed_queries(64, LO, HI, seed=3), device="cuda")
+    alone = {L: (sg.simulate_closed_loop(prob, surf[L][1], x0, 50, 0.01)["xT"].clone(),
+                 sg.eval_feedback(surf[L][1], x0, mode=sg.EVAL_DF32).clone()) for L in (2, 4)}
+    torch.cuda.synchronize()
+    errors, outs = [], {}
+
+    def work(L):
+        try:
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                for _ in range(30):
+                    xT = sg.simulate_closed_loop(prob, surf[L][1], x0, 50, 0.01, stream=st)["xT"]
+                    u = sg.eval_feedback(surf[L][1], x0, mode=sg.EVAL_DF32, stream=st)
+                st.synchronize()
+            outs[L] = (xT, u)
+        except BaseException as e:   # reported below
+            errors.append(e)
+
+    ths = [threading.Thread(target=work, args=(L,)) for L in (2, 4, 2, 4)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    assert not errors, errors[0]
+    for L in (2, 4):
+        assert torch.equal(outs[L][0], alone[L][0]) and torch.equal(outs[L][1], alone[L][1])
