@@ -109,10 +109,10 @@ __device__ __forceinline__ df df_recip(df a) {
 // The same for a level fixed at compile time: every loop unrolls, so the
 // reciprocals stay in registers (the general form indexes them at run time,
 // which puts them in local memory).
-template <int L>
-__device__ __forceinline__ void basis_row_df_t(double u, const float2* __restrict__ xf, float2* tab, int stride) {
+template <int L, typename Out>
+__device__ __forceinline__ void basis_row_df_t(double u, const float2* __restrict__ xf, Out out) {
   constexpr int fine_n = 1 << L;
-  tab[0] = make_float2(1.0f, 0.0f);
+  out(0, df{1.0f, 0.0f});
   const df uu = df_from(u);
   df rinv[fine_n + 1];
   int hit = -1;
@@ -155,22 +155,23 @@ __device__ __forceinline__ void basis_row_df_t(double u, const float2* __restric
         if (m == 0 || m == n) wm *= 0.5f;
         v = df_mul(df_scale(rinv[m * sf], wm), inv_denom);
       }
-      tab[(id + j) * stride] = make_float2(v.hi, v.lo);
+      out(id + j, v);
     }
     id += cnt;
   }
 }
 
-__device__ inline void basis_row_df(double u, int level, const float2* __restrict__ xf, float2* tab, int stride) {
+template <typename Out>
+__device__ inline void basis_row_df_out(double u, int level, const float2* __restrict__ xf, Out out) {
   switch (level) {
-    case 1: return basis_row_df_t<1>(u, xf, tab, stride);
-    case 2: return basis_row_df_t<2>(u, xf, tab, stride);
-    case 3: return basis_row_df_t<3>(u, xf, tab, stride);
-    case 4: return basis_row_df_t<4>(u, xf, tab, stride);
-    case 5: return basis_row_df_t<5>(u, xf, tab, stride);
+    case 1: return basis_row_df_t<1>(u, xf, out);
+    case 2: return basis_row_df_t<2>(u, xf, out);
+    case 3: return basis_row_df_t<3>(u, xf, out);
+    case 4: return basis_row_df_t<4>(u, xf, out);
+    case 5: return basis_row_df_t<5>(u, xf, out);
     default: break;
   }
-  tab[0] = make_float2(1.0f, 0.0f);
+  out(0, df{1.0f, 0.0f});
   if (level == 0) return;
   const int fine_n = 1 << level;
   const df uu = df_from(u);
@@ -211,11 +212,32 @@ __device__ inline void basis_row_df(double u, int level, const float2* __restric
         if (m == 0 || m == n) wm *= 0.5f;
         v = df_mul(df_scale(rinv[m * sf], wm), inv_denom);
       }
-      tab[(id + j) * stride] = make_float2(v.hi, v.lo);
+      out(id + j, v);
     }
     id += cnt;
   }
 }
 
+// Writers of basis_row_df_out: the pairs, or their leading floats (the
+// values rounded once to FP32).
+struct DfPairOut {
+  float2* tab;
+  int stride;
+  __device__ __forceinline__ void operator()(int id, df v) const { tab[id * stride] = make_float2(v.hi, v.lo); }
+};
+struct DfHiOut {
+  float* tab;
+  int stride;
+  __device__ __forceinline__ void operator()(int id, df v) const { tab[id * stride] = v.hi; }
+};
+
+__device__ inline void basis_row_df(double u, int level, const float2* __restrict__ xf, float2* tab, int stride) {
+  basis_row_df_out(u, level, xf, DfPairOut{tab, stride});
+}
+
+__device__ inline void basis_row_df_hi(double u, int level, const float2* __restrict__ xf, float* tab,
+                                       int stride) {
+  basis_row_df_out(u, level, xf, DfHiOut{tab, stride});
+}
 
 }  // namespace sg

@@ -1,21 +1,33 @@
 // Split-TF32 evaluation of the interpolant contraction on the fifth-generation
-// tensor cores (tcgen05, accumulator in tensor memory).
+// tensor cores (tcgen05, accumulators in tensor memory).
 //
 // u = Phi W with Phi (queries x nodes) generated on the fly and W (nodes x k)
 // the surpluses.  With Phi = Phi_hi + Phi_lo and W = W_hi + W_lo split into
 // TF32 parts, u ~ Phi_hi W_hi + Phi_hi W_lo + Phi_lo W_hi (the 3xTF32 scheme):
-// one accumulator D (128 rows x 16 columns, FP32) receives
+// an accumulator D (128 rows x 16 columns, FP32) receives
 //   Phi_hi x [W_hi | W_lo | 0]  and  Phi_lo x [W_hi | 0 | 0],
 // so that u = D[:, 0:k] + D[:, k:2k] (k <= 8 outputs).
 //
-// One CTA (8 warps) per 128 queries; threads t and t + 128 own query row t,
-// each for one K-step of 8 nodes.  Per chunk of 16 nodes the threads write
-// their rows of Phi_hi and Phi_lo into shared memory in the no-swizzle K-major
-// core-matrix layout (8 rows x 16 bytes per core matrix), thread 0 issues
-// 2 x 2 MMAs of shape M=128, N=16, K=8 and commits them to an mbarrier; the
-// next chunk is written into the other buffer while the tensor cores work.  Every wait on an mbarrier has an iteration
-// limit: on timeout the kernel records an error flag, writes NaN outputs,
-// releases its tensor memory and returns.
+// The 1-D basis tables are computed in pair-of-floats arithmetic (about 48
+// bits) and rounded once to FP32, so Phi carries only the FP32 rounding of its
+// factors and products; the nodes are split over kTcAcc accumulators (each a
+// 16-column block of tensor memory) that are added in FP64 at the end, so the
+// FP32 accumulation runs over at most ceil(M / kTcAcc) nodes.
+//
+// One CTA per 128 queries, warp-specialised:
+//   warps 0..7   producers: threads t and t + 128 own query row t; per chunk
+//                of 16 nodes each writes one K-step (8 nodes) of its row of
+//                Phi_hi and Phi_lo into a stage of a shared-memory ring, in
+//                the no-swizzle K-major core-matrix layout, then arrives on
+//                the stage's "full" mbarrier;
+//   warp 8       lane 0 waits for a full stage, issues its 2 x 2 MMAs
+//                (M = 128, N = 16, K = 8, kind::tf32) and commits them to the
+//                stage's "empty" mbarrier, which the producers wait on before
+//                refilling the stage.
+// No thread waits for another producer; the ring has kTcStages stages.  Every
+// wait on an mbarrier has an iteration limit: on timeout the kernel records
+// an error flag, writes NaN outputs, releases its tensor memory and returns.
+#include "basis.cuh"
 #include "common.cuh"
 #include "diag.cuh"
 #include "interp.cuh"
@@ -23,14 +35,18 @@
 namespace sg {
 
 constexpr int kTcRows = 128;          // queries per CTA (= MMA M)
-constexpr int kTcThreads = 256;       // two threads per query row
+constexpr int kTcProducers = 256;     // two producer threads per query row
+constexpr int kTcThreads = kTcProducers + 32;   // + the MMA warp
 constexpr int kTcN = 16;              // MMA N (2k <= 16)
-constexpr int kTcChunk = 16;          // nodes per chunk (2 MMA K-steps of 8, one per thread of a row)
+constexpr int kTcChunk = 16;          // nodes per stage (2 MMA K-steps of 8, one per producer of a row)
+constexpr int kTcStages = 3;          // ring depth
+constexpr int kTcAcc = 8;             // accumulators (16 tensor-memory columns each)
 constexpr int kTcAStep = kTcRows * 32;          // bytes of one K-step of A (128 rows x 8 tf32)
 constexpr int kTcABytes = 2 * kTcAStep;         // one chunk of Phi_hi or Phi_lo: 8 KB
 constexpr int kTcBStep = kTcN * 32;             // bytes of one K-step of B (16 rows x 8 tf32)
 constexpr int kTcBBytes = 2 * kTcBStep;         // one chunk of one B matrix: 1 KB
 constexpr int kTcBPack = 2 * kTcBBytes / 4;     // floats per chunk of [B1 | B2]
+constexpr int kTcStageBytes = 2 * kTcABytes + 2 * kTcBBytes;   // Phi_hi | Phi_lo | B1 | B2
 constexpr unsigned kTcSpinLimit = 1u << 24;     // bounded mbarrier wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -80,46 +96,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// FP32 barycentric basis values (same construction as the FP64 basis_row).
-__device__ void basis_row_f32(float u, int level, const double* __restrict__ xf, float* tab, int stride) {
-  tab[0] = 1.0f;
-  if (level == 0) return;
-  const int fine_n = 1 << level;
-  float rinv[kMaxFine + 1];
-  int hit = -1;
-  for (int p = 0; p <= fine_n; ++p) {
-    const float diff = u - static_cast<float>(xf[p]);
-    if (diff == 0.0f) hit = p;
-    rinv[p] = diff == 0.0f ? 0.0f : 1.0f / diff;
-  }
-  int id = 1;
-  for (int l = 2; l <= level + 1; ++l) {
-    const int n = 1 << (l - 1);
-    const int sf = fine_n / n;
-    const bool exact = hit >= 0 && (hit % sf) == 0;
-    float den = 0.0f;
-    if (!exact)
-      for (int m = 0; m <= n; ++m) {
-        float wm = (m & 1) ? -1.0f : 1.0f;
-        if (m == 0 || m == n) wm *= 0.5f;
-        den += wm * rinv[m * sf];
-      }
-    const float inv = exact ? 0.0f : 1.0f / den;
-    const int cnt = l == 2 ? 2 : (n >> 1);
-    for (int j = 0; j < cnt; ++j) {
-      const int m = l == 2 ? j * n : 2 * j + 1;
-      float v;
-      if (exact) {
-        v = (m * sf == hit) ? 1.0f : 0.0f;
-      } else {
-        float wm = (m & 1) ? -1.0f : 1.0f;
-        if (m == 0 || m == n) wm *= 0.5f;
-        v = wm * rinv[m * sf] * inv;
-      }
-      tab[(id + j) * stride] = v;
-    }
-    id += cnt;
-  }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 struct TcArgs {
@@ -133,139 +111,186 @@ struct TcArgs {
 __global__ void __launch_bounds__(kTcThreads) k_eval_tf32x3(TcArgs t) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const EvalArgs& e = t.e;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int row = tid & (kTcRows - 1), half = tid / kTcRows;
-  const int64_t q = blockIdx.x * int64_t(kTcRows) + row;
-  const bool live = q < e.Q;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nf = e.nf;
-  // layout: A buffers (2 x [hi, lo]) | B buffers (2 x [B1, B2]) | tables | barriers
-  unsigned char* abuf = smem;                                        // 2 * 2 * kTcABytes
-  unsigned char* bbuf = abuf + 4 * kTcABytes;                        // 2 * 2 * kTcBBytes
-  float* tab = reinterpret_cast<float*>(bbuf + 4 * kTcBBytes);       // d * nf * kTcRows
+  const int nchunks = t.nchunks;
+  // layout: stages (kTcStages x [Phi_hi | Phi_lo | B1 | B2]) | tables | barriers
+  unsigned char* ring = smem;
+  float* tab = reinterpret_cast<float*>(ring + kTcStages * kTcStageBytes);     // d * nf * kTcRows
   uint64_t* bars = reinterpret_cast<uint64_t*>(tab + size_t(t.d) * nf * kTcRows);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2);
+  uint64_t* full = bars;                    // kTcStages, count kTcProducers
+  uint64_t* empty = bars + kTcStages;       // kTcStages, count 1 (tcgen05.commit)
+  uint64_t* done = bars + 2 * kTcStages;    // 1: every MMA has completed
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 1);
+  int* flag = reinterpret_cast<int*>(tmem_holder + 1);   // 0 = all waits succeeded
 
-  // the two threads of a row share the dimensions of its 1-D tables
-  for (int dim = half; dim < t.d; dim += 2) {
-    const double u = live ? (e.xq[q * t.d + dim] - e.lo[dim]) / e.width[dim] : 0.5;
-    basis_row_f32(static_cast<float>(u), e.level, e.xf, tab + (dim * nf) * kTcRows + row, kTcRows);
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tmem_holder)));
+  const int row = tid & (kTcRows - 1), half = (tid >> 7) & 1;
+  const int64_t q = blockIdx.x * int64_t(kTcRows) + row;
+  const bool producer = tid < kTcProducers;
+  const bool live = producer && q < e.Q;
+  if (producer) {
+    // the two threads of a row share its 1-D tables, computed in pairs of
+    // floats and rounded once to FP32
+    for (int dim = half; dim < t.d; dim += 2) {
+      const double u = live ? (e.xq[q * t.d + dim] - e.lo[dim]) / e.width[dim] : 0.5;
+      basis_row_df_hi(u, e.level, e.xfdf, tab + (dim * nf) * kTcRows + row, kTcRows);
+    }
+  } else if (warp == kTcProducers / 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"(16 * kTcAcc));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])));
+    if (lane == 0) {
+      for (int s = 0; s < kTcStages; ++s) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(kTcProducers));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+      }
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)));
+      *flag = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_holder;
-  const uint32_t idesc = idesc_tf32();
   bool ok = true;
-  uint32_t phase[2] = {0u, 0u};
 
-  for (int c = 0; c < t.nchunks; ++c) {
-    const int buf = c & 1;
-    if (c >= 2) {
-      // the MMAs that read this buffer two chunks ago must have finished
-      ok = ok && mbar_wait(smem_u32(&bars[buf]), phase[buf]);
-      phase[buf] ^= 1u;
-    }
-    unsigned char* ahi = abuf + (2 * buf) * kTcABytes;
-    unsigned char* alo = ahi + kTcABytes;
-    // this thread's K-step (8 nodes) of row `row`, as two 16-byte core-matrix
-    // rows: element (r, k) of K-step s at
-    //   s * kTcAStep + ((r / 8) * 2 + (k % 8) / 4) * 128 + (r % 8) * 16 + (k % 4) * 4
+  if (producer) {
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int st = c % kTcStages;
+      if (c >= kTcStages) ok = mbar_wait(smem_u32(&empty[st]), ((c / kTcStages) - 1) & 1);
+      if (!ok) break;
+      unsigned char* stage = ring + st * kTcStageBytes;
+      unsigned char* ahi = stage;
+      unsigned char* alo = stage + kTcABytes;
+      // the chunk's nodes are sorted by active count: its last node has the most
+      const int64_t m0 = int64_t(c) * kTcChunk;
+      const int64_t mlast = (m0 + kTcChunk < e.M ? m0 + kTcChunk : e.M) - 1;
+      const int A = e.nact[mlast] > 0 ? e.nact[mlast] : 1;
 #pragma unroll
-    for (int c2 = 0; c2 < 2; ++c2) {
-      float hv[4], lv[4];
+      for (int c2 = 0; c2 < 2; ++c2) {
+        float hv[4], lv[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int64_t m = int64_t(c) * kTcChunk + half * 8 + c2 * 4 + j;
-        float phi = 0.0f;
-        if (m < e.M) {
-          const uint16_t* o = e.ops + m * kMaxDim;
-          phi = tab[o[0] * kTcRows + row];
-          for (int a = 1; a < e.amax; ++a) phi *= tab[o[a] * kTcRows + row];
+        for (int j = 0; j < 4; ++j) {
+          const int64_t m = m0 + half * 8 + c2 * 4 + j;
+          float phi = 0.0f;
+          if (m < e.M) {
+            // padded slots of ops point at tab[0] = a^1 = 1
+            const uint16_t* o = e.ops + m * kMaxDim;
+            phi = tab[o[0] * kTcRows + row];
+            for (int a = 1; a < A; ++a) phi = __fmul_rn(phi, tab[o[a] * kTcRows + row]);
+          }
+          hv[j] = tf32_round(phi);
+          lv[j] = tf32_round(__fsub_rn(phi, hv[j]));
         }
-        hv[j] = tf32_round(phi);
-        lv[j] = tf32_round(phi - hv[j]);
+        // element (r, k) of K-step s at
+        //   s * kTcAStep + ((r / 8) * 2 + (k % 8) / 4) * 128 + (r % 8) * 16 + (k % 4) * 4
+        const int off = half * kTcAStep + ((row / 8) * 2 + c2) * 128 + (row % 8) * 16;
+        *reinterpret_cast<float4*>(ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<float4*>(alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
       }
-      const int off = half * kTcAStep + ((row / 8) * 2 + c2) * 128 + (row % 8) * 16;
-      *reinterpret_cast<float4*>(ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-      *reinterpret_cast<float4*>(alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+      // the chunk of [B1 | B2], pre-packed in the same layout: the first
+      // kTcBPack / 4 producers copy one 16-byte word each
+      if (tid < kTcBPack / 4) {
+        const float4* src = reinterpret_cast<const float4*>(t.bpack + size_t(c) * kTcBPack);
+        reinterpret_cast<float4*>(stage + 2 * kTcABytes)[tid] = src[tid];
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&full[st]));
     }
-    // the chunk of [B1 | B2], pre-packed in the same layout
-    const float4* src = reinterpret_cast<const float4*>(t.bpack + size_t(c) * kTcBPack);
-    float4* dst = reinterpret_cast<float4*>(bbuf + (2 * buf) * kTcBBytes);
-    for (int x = tid; x < kTcBPack / 4; x += kTcThreads) dst[x] = src[x];
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  } else if (lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = idesc_tf32();
+    const int per_acc = (nchunks + kTcAcc - 1) / kTcAcc;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int st = c % kTcStages;
+      ok = mbar_wait(smem_u32(&full[st]), (c / kTcStages) & 1);
+      if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a_hi = smem_u32(ahi), a_lo = smem_u32(alo);
-      const uint32_t b1 = smem_u32(bbuf + (2 * buf) * kTcBBytes), b2 = b1 + kTcBBytes;
+      unsigned char* stage = ring + st * kTcStageBytes;
+      const uint32_t a_hi = smem_u32(stage), a_lo = a_hi + kTcABytes;
+      const uint32_t b1 = a_hi + 2 * kTcABytes, b2 = b1 + kTcBBytes;
+      const uint32_t acc_col = tmem + static_cast<uint32_t>((c / per_acc) * kTcN);
+      const bool first = (c % per_acc) == 0;
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const uint64_t da_hi = smem_desc(a_hi + s * kTcAStep, 128, 256);
         const uint64_t da_lo = smem_desc(a_lo + s * kTcAStep, 128, 256);
         const uint64_t db1 = smem_desc(b1 + s * kTcBStep, 128, 256);
         const uint64_t db2 = smem_desc(b2 + s * kTcBStep, 128, 256);
-        const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
+        const uint32_t acc = (first && s == 0) ? 0u : 1u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_col),
             "l"(da_hi), "l"(db1), "r"(idesc), "r"(acc));
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_col),
             "l"(da_lo), "l"(db2), "r"(idesc), "r"(1u));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(&bars[buf])));
+          smem_u32(&empty[st])));
     }
+    // completes when every MMA issued above has finished
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_u32(done)));
   }
-  // the last commit covers every MMA issued before it
-  if (t.nchunks > 0) {
-    const int lb = (t.nchunks - 1) & 1;
-    ok = ok && mbar_wait(smem_u32(&bars[lb]), phase[lb]);
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  float v[16];
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+  if (!ok) atomicExch(flag, 1);
+  // epilogue: warps 0..3 read tensor-memory lanes 32w .. 32w + 31 (accumulator rows)
+  double epi_sum[kTcN / 2];
+  bool epi_fin = false;
   if (warp < 4) {
-    // warp w reads accumulator rows (tensor-memory lanes) 32w .. 32w + 31
-    const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    bool fin = mbar_wait(smem_u32(done), 0);
+    if (!fin) atomicExch(flag, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    double sum[kTcN / 2];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-  }
-  const bool all_ok = __syncthreads_and(ok);
-  if (live && half == 0) {
-    for (int cix = 0; cix < e.k; ++cix) {
-      float hi = 0.f, lo = 0.f;
+    for (int j = 0; j < kTcN / 2; ++j) sum[j] = 0.0;
+    const int per_acc = (nchunks + kTcAcc - 1) / kTcAcc;
+    const int nacc = nchunks > 0 ? (nchunks + per_acc - 1) / per_acc : 0;
+    for (int a = 0; a < nacc && fin; ++a) {
+      const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(a * kTcN);
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int cix = 0; cix < e.k; ++cix) {
+        float hi = 0.f, lo = 0.f;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (j == cix) hi = v[j];
-        if (j == e.k + cix) lo = v[j];
+        for (int j = 0; j < 16; ++j) {
+          if (j == cix) hi = __uint_as_float(r[j]);
+          if (j == e.k + cix) lo = __uint_as_float(r[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < kTcN / 2; ++j)
+          if (j == cix) sum[j] += static_cast<double>(hi) + static_cast<double>(lo);
       }
-      e.out[q * e.k + cix] = all_ok ? static_cast<double>(hi) + static_cast<double>(lo) : NAN;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncwarp();
+    epi_fin = fin;
+#pragma unroll
+    for (int j = 0; j < kTcN / 2; ++j) epi_sum[j] = sum[j];
+  }
+  __syncwarp();
+  __syncthreads();   // every wait of every thread is over: the flag is final
+  const bool good = *reinterpret_cast<volatile int*>(flag) == 0;
+  if (warp < 4 && q < e.Q) {
+    for (int cix = 0; cix < e.k; ++cix) {
+      double v = 0.0;
+#pragma unroll
+      for (int j = 0; j < kTcN / 2; ++j)
+        if (j == cix) v = epi_sum[j];
+      e.out[q * e.k + cix] = good && epi_fin ? v : NAN;
     }
   }
-  if (!all_ok && tid == 0) atomicExch(t.err, 1);
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+  if (tid == 0 && !good) atomicExch(t.err, 1);
+  if (warp == kTcProducers / 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(16 * kTcAcc));
 }
 
 // [B1 | B2] per chunk: B1 = [W_hi | W_lo | 0], B2 = [W_hi | 0 | 0] (16 columns),
@@ -323,7 +348,7 @@ int eval_tf32x3(const EvalArgs& e, const sg_surplus* s, cudaStream_t st) {
   t.bpack = s->bpack;
   t.nchunks = s->tc_chunks;
   t.err = s->tc_err;
-  const size_t smem = 4 * kTcABytes + 4 * kTcBBytes + sizeof(float) * s->d * s->nf * kTcRows + 64;
+  const size_t smem = size_t(kTcStages) * kTcStageBytes + sizeof(float) * s->d * s->nf * kTcRows + 128;
   if (smem > 227 * 1024) return fail(SG_EUNSUPPORTED, "sg_eval_feedback: grid level too high for TF32X3");
   SG_CUDA_TRY(ensure_dynamic_smem(k_eval_tf32x3, static_cast<int>(smem)));
   const unsigned blocks = static_cast<unsigned>(ceil_div(e.Q, kTcRows));

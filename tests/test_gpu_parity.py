@@ -374,6 +374,23 @@ def test_tf32x3_within_stated_bound(d, L, k):
     assert rel(u, ref) <= 1e-5
 
 
+def test_tf32x3_smooth_feedback_at_full_size():
+    """A smooth feedback-like function interpolated on the level-4 grid and
+    evaluated at the 1e6 mixed queries of the benchmark: 3xTF32 on the tensor
+    cores within 2e-6 of the FP64 evaluation, relative to max |u| (the FP64
+    evaluation matches the oracle to 1e-10, test_eval_full_size_sampled)."""
+    g = sg.Grid(6, 4, LO, HI)
+    x = g.coords.cpu().numpy()
+    K = np.random.default_rng(0).standard_normal((3, 6))
+    f = -(x @ K.T) + 0.3 * np.sin(x @ K.T) + 0.1 * np.prod(np.cos(x), axis=1)[:, None]
+    S = sg.Surplus(g, cuda(f))
+    xq = cuda(synth.mixed_queries(1_000_000, LO, HI, seed=1))
+    u = sg.eval_feedback(S, xq, mode=sg.EVAL_TF32X3)
+    ref = sg.eval_feedback(S, xq, mode=sg.EVAL_FP64)
+    assert torch.isfinite(u).all()
+    assert ((u - ref).abs().max() / ref.abs().max()).item() <= 2e-6
+
+
 def test_tf32x3_full_size_sampled():
     g = sg.Grid(6, 4, LO, HI)
     og = ogrid.Grid(6, 4, LO, HI)
