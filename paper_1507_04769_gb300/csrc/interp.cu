@@ -330,6 +330,10 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   const size_t obp = take(npack * sizeof(float)), oerr = take(sizeof(int));
   const size_t ohost = off;
   const size_t obox = take(2 * d * sizeof(double)), onact = take(M), oops = take(M * kMaxDim * sizeof(uint16_t));
+  // the tensor-core kernel's table offsets: ops scaled by its 128 table rows
+  // (uint16, so the tables must have at most 511 entries per query)
+  const bool tcoff_ok = npack && size_t(d) * s->nf <= 511;
+  const size_t otcoff = take(tcoff_ok ? M * kMaxDim * sizeof(uint16_t) : 0);
   const size_t ofid = take(M * d * sizeof(uint16_t)), ofpt = take(M * d * sizeof(int16_t));
   const size_t oorder = take(M * sizeof(int32_t));
   cudaError_t e = cudaMalloc(&s->block, off);
@@ -348,6 +352,7 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   s->box = reinterpret_cast<double*>(base + obox);
   s->nact = reinterpret_cast<uint8_t*>(base + onact);
   s->ops = reinterpret_cast<uint16_t*>(base + oops);
+  s->tcoff = tcoff_ok ? reinterpret_cast<uint16_t*>(base + otcoff) : nullptr;
   auto* d_fid = reinterpret_cast<uint16_t*>(base + ofid);
   auto* d_fpt = reinterpret_cast<int16_t*>(base + ofpt);
   auto* d_tab1 = reinterpret_cast<double*>(base + otab1);
@@ -368,6 +373,11 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
     std::memcpy(h.data() + (obox - ohost), box.data(), 2 * d * sizeof(double));
     std::memcpy(h.data() + (onact - ohost), nact.data(), M);
     std::memcpy(h.data() + (oops - ohost), ops.data(), M * kMaxDim * sizeof(uint16_t));
+    if (tcoff_ok) {
+      std::vector<uint16_t> tco(M * kMaxDim);
+      for (size_t x = 0; x < tco.size(); ++x) tco[x] = static_cast<uint16_t>(ops[x] * 128u);
+      std::memcpy(h.data() + (otcoff - ohost), tco.data(), M * kMaxDim * sizeof(uint16_t));
+    }
     std::memcpy(h.data() + (ofid - ohost), fid.data(), M * d * sizeof(uint16_t));
     std::memcpy(h.data() + (ofpt - ohost), fpt.data(), M * d * sizeof(int16_t));
     std::memcpy(h.data() + (oorder - ohost), order.data(), M * sizeof(int32_t));

@@ -49,7 +49,8 @@ struct sg_surplus {
   double* xf = nullptr;           // finest 1-D set, 2^L + 1 points
   float2* xfdf = nullptr;         // finest 1-D set as (hi, lo) pairs
   float2* Wdf = nullptr;          // Ws as (hi, lo) pairs
-  float* bpack = nullptr;         // split-TF32 [W_hi|W_lo], [W_hi|0] per 32-node chunk (k <= 8)
+  float* bpack = nullptr;         // split-TF32 [W_hi|W_lo], [W_hi|0] per 16-node chunk (k <= 8)
+  uint16_t* tcoff = nullptr;      // M x 8: ops * 128, the tensor-core kernel's table offsets (0 if unused)
   int tc_chunks = 0;
   int* tc_err = nullptr;          // set by the tensor-core kernel if a wait timed out
   void* block = nullptr;          // the one device allocation all the arrays above live in

@@ -103,10 +103,38 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 struct TcArgs {
   EvalArgs e;
   int d;
-  const float* bpack;   // nchunks x kTcBPack
+  const float* bpack;      // nchunks x kTcBPack
+  const uint16_t* tcoff;   // M x 8: table offsets (ops x kTcRows); padded slots point at tab[0] = 1
   int nchunks;
   int* err;
 };
+
+// One K-step (8 nodes) of Phi_hi and Phi_lo for query row `row`, nodes
+// m0 .. m0 + 7, each the product of its A basis values.
+template <int A>
+__device__ __forceinline__ void tc_produce_kstep(const TcArgs& t, const float* __restrict__ tabrow, int64_t m0,
+                                                 unsigned char* ahi, unsigned char* alo, int off) {
+#pragma unroll
+  for (int c2 = 0; c2 < 2; ++c2) {
+    float hv[4], lv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t m = m0 + c2 * 4 + j;
+      float phi = 0.0f;
+      if (m < t.e.M) {
+        const uint4 ov = *reinterpret_cast<const uint4*>(t.tcoff + m * kMaxDim);
+        const uint32_t w[4] = {ov.x, ov.y, ov.z, ov.w};
+        phi = tabrow[w[0] & 0xFFFFu];
+#pragma unroll
+        for (int a = 1; a < A; ++a) phi = __fmul_rn(phi, tabrow[(a & 1) ? (w[a >> 1] >> 16) : (w[a >> 1] & 0xFFFFu)]);
+      }
+      hv[j] = tf32_round(phi);
+      lv[j] = tf32_round(__fsub_rn(phi, hv[j]));
+    }
+    *reinterpret_cast<float4*>(ahi + off + c2 * 128) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+    *reinterpret_cast<float4*>(alo + off + c2 * 128) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+  }
+}
 
 __global__ void __launch_bounds__(kTcThreads) k_eval_tf32x3(TcArgs t) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -166,28 +194,22 @@ __global__ void __launch_bounds__(kTcThreads) k_eval_tf32x3(TcArgs t) {
       // the chunk's nodes are sorted by active count: its last node has the most
       const int64_t m0 = int64_t(c) * kTcChunk;
       const int64_t mlast = (m0 + kTcChunk < e.M ? m0 + kTcChunk : e.M) - 1;
-      const int A = e.nact[mlast] > 0 ? e.nact[mlast] : 1;
-#pragma unroll
-      for (int c2 = 0; c2 < 2; ++c2) {
-        float hv[4], lv[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int64_t m = m0 + half * 8 + c2 * 4 + j;
-          float phi = 0.0f;
-          if (m < e.M) {
-            // padded slots of ops point at tab[0] = a^1 = 1
-            const uint16_t* o = e.ops + m * kMaxDim;
-            phi = tab[o[0] * kTcRows + row];
-            for (int a = 1; a < A; ++a) phi = __fmul_rn(phi, tab[o[a] * kTcRows + row]);
-          }
-          hv[j] = tf32_round(phi);
-          lv[j] = tf32_round(__fsub_rn(phi, hv[j]));
-        }
-        // element (r, k) of K-step s at
-        //   s * kTcAStep + ((r / 8) * 2 + (k % 8) / 4) * 128 + (r % 8) * 16 + (k % 4) * 4
-        const int off = half * kTcAStep + ((row / 8) * 2 + c2) * 128 + (row % 8) * 16;
-        *reinterpret_cast<float4*>(ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-        *reinterpret_cast<float4*>(alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+      const int A = e.nact[mlast];
+      // element (r, k) of K-step s at
+      //   s * kTcAStep + ((r / 8) * 2 + (k % 8) / 4) * 128 + (r % 8) * 16 + (k % 4) * 4
+      const int off = half * kTcAStep + ((row / 8) * 2) * 128 + (row % 8) * 16;
+      const float* tabrow = tab + row;
+      const int64_t mk = m0 + half * 8;
+      switch (A) {
+        case 0:
+        case 1: tc_produce_kstep<1>(t, tabrow, mk, ahi, alo, off); break;
+        case 2: tc_produce_kstep<2>(t, tabrow, mk, ahi, alo, off); break;
+        case 3: tc_produce_kstep<3>(t, tabrow, mk, ahi, alo, off); break;
+        case 4: tc_produce_kstep<4>(t, tabrow, mk, ahi, alo, off); break;
+        case 5: tc_produce_kstep<5>(t, tabrow, mk, ahi, alo, off); break;
+        case 6: tc_produce_kstep<6>(t, tabrow, mk, ahi, alo, off); break;
+        case 7: tc_produce_kstep<7>(t, tabrow, mk, ahi, alo, off); break;
+        default: tc_produce_kstep<8>(t, tabrow, mk, ahi, alo, off); break;
       }
       // the chunk of [B1 | B2], pre-packed in the same layout: the first
       // kTcBPack / 4 producers copy one 16-byte word each
@@ -342,10 +364,12 @@ int pack_tf32(sg_surplus* s, cudaStream_t st) {
 
 int eval_tf32x3(const EvalArgs& e, const sg_surplus* s, cudaStream_t st) {
   if (!s->bpack) return fail(SG_EUNSUPPORTED, "sg_eval_feedback: SG_EVAL_TF32X3 needs k <= 8");
+  if (!s->tcoff) return fail(SG_EUNSUPPORTED, "sg_eval_feedback: grid level too high for TF32X3");
   TcArgs t{};
   t.e = e;
   t.d = s->d;
   t.bpack = s->bpack;
+  t.tcoff = s->tcoff;
   t.nchunks = s->tc_chunks;
   t.err = s->tc_err;
   const size_t smem = size_t(kTcStages) * kTcStageBytes + sizeof(float) * s->d * s->nf * kTcRows + 128;
