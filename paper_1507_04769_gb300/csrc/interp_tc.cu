@@ -109,31 +109,49 @@ struct TcArgs {
   int* err;
 };
 
-// One K-step (8 nodes) of Phi_hi and Phi_lo for query row `row`, nodes
-// m0 .. m0 + 7, each the product of its A basis values.
-template <int A>
-__device__ __forceinline__ void tc_produce_kstep(const TcArgs& t, const float* __restrict__ tabrow, int64_t m0,
-                                                 unsigned char* ahi, unsigned char* alo, int off) {
+// Split of x into TF32 parts: hi = x rounded to the nearest TF32 value (ties
+// away from zero: half an ulp of the 10-bit mantissa added to the magnitude,
+// the 13 low bits cleared), lo = x - hi (exact in FP32, Sterbenz) rounded the
+// same way.  Both have zero low bits, so the tensor cores read them as given.
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+  lo = __uint_as_float((__float_as_uint(__fsub_rn(x, hi)) + 0x1000u) & 0xFFFFE000u);
+}
+
+// One K-step (8 nodes) of Phi_hi and Phi_lo for query row `row`: node j of
+// the step has its table offsets at offs[8 j ..] and is the product of its A
+// basis values; nodes j >= nvalid (past the last node) are zero.
+template <int A, bool kFull>
+__device__ __forceinline__ void tc_produce_kstep(const uint16_t* __restrict__ offs, int nvalid,
+                                                 const float* __restrict__ tabrow, unsigned char* ahi,
+                                                 unsigned char* alo, int off) {
 #pragma unroll
   for (int c2 = 0; c2 < 2; ++c2) {
     float hv[4], lv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int64_t m = m0 + c2 * 4 + j;
+      const int jj = c2 * 4 + j;
       float phi = 0.0f;
-      if (m < t.e.M) {
-        const uint4 ov = *reinterpret_cast<const uint4*>(t.tcoff + m * kMaxDim);
+      if (kFull || jj < nvalid) {
+        const uint4 ov = reinterpret_cast<const uint4*>(offs)[jj];
         const uint32_t w[4] = {ov.x, ov.y, ov.z, ov.w};
         phi = tabrow[w[0] & 0xFFFFu];
 #pragma unroll
         for (int a = 1; a < A; ++a) phi = __fmul_rn(phi, tabrow[(a & 1) ? (w[a >> 1] >> 16) : (w[a >> 1] & 0xFFFFu)]);
       }
-      hv[j] = tf32_round(phi);
-      lv[j] = tf32_round(__fsub_rn(phi, hv[j]));
+      tf32_split(phi, hv[j], lv[j]);
     }
     *reinterpret_cast<float4*>(ahi + off + c2 * 128) = make_float4(hv[0], hv[1], hv[2], hv[3]);
     *reinterpret_cast<float4*>(alo + off + c2 * 128) = make_float4(lv[0], lv[1], lv[2], lv[3]);
   }
+}
+
+template <int A>
+__device__ __forceinline__ void tc_produce(const uint16_t* __restrict__ offs, int nvalid,
+                                           const float* __restrict__ tabrow, unsigned char* ahi, unsigned char* alo,
+                                           int off) {
+  if (nvalid >= 8) tc_produce_kstep<A, true>(offs, 8, tabrow, ahi, alo, off);
+  else tc_produce_kstep<A, false>(offs, nvalid, tabrow, ahi, alo, off);
 }
 
 __global__ void __launch_bounds__(kTcThreads) k_eval_tf32x3(TcArgs t) {
@@ -200,16 +218,18 @@ __global__ void __launch_bounds__(kTcThreads) k_eval_tf32x3(TcArgs t) {
       const int off = half * kTcAStep + ((row / 8) * 2) * 128 + (row % 8) * 16;
       const float* tabrow = tab + row;
       const int64_t mk = m0 + half * 8;
+      const int nvalid = static_cast<int>(e.M - mk < 8 ? e.M - mk : 8);
+      const uint16_t* offs = t.tcoff + mk * kMaxDim;
       switch (A) {
         case 0:
-        case 1: tc_produce_kstep<1>(t, tabrow, mk, ahi, alo, off); break;
-        case 2: tc_produce_kstep<2>(t, tabrow, mk, ahi, alo, off); break;
-        case 3: tc_produce_kstep<3>(t, tabrow, mk, ahi, alo, off); break;
-        case 4: tc_produce_kstep<4>(t, tabrow, mk, ahi, alo, off); break;
-        case 5: tc_produce_kstep<5>(t, tabrow, mk, ahi, alo, off); break;
-        case 6: tc_produce_kstep<6>(t, tabrow, mk, ahi, alo, off); break;
-        case 7: tc_produce_kstep<7>(t, tabrow, mk, ahi, alo, off); break;
-        default: tc_produce_kstep<8>(t, tabrow, mk, ahi, alo, off); break;
+        case 1: tc_produce<1>(offs, nvalid, tabrow, ahi, alo, off); break;
+        case 2: tc_produce<2>(offs, nvalid, tabrow, ahi, alo, off); break;
+        case 3: tc_produce<3>(offs, nvalid, tabrow, ahi, alo, off); break;
+        case 4: tc_produce<4>(offs, nvalid, tabrow, ahi, alo, off); break;
+        case 5: tc_produce<5>(offs, nvalid, tabrow, ahi, alo, off); break;
+        case 6: tc_produce<6>(offs, nvalid, tabrow, ahi, alo, off); break;
+        case 7: tc_produce<7>(offs, nvalid, tabrow, ahi, alo, off); break;
+        default: tc_produce<8>(offs, nvalid, tabrow, ahi, alo, off); break;
       }
       // the chunk of [B1 | B2], pre-packed in the same layout: the first
       // kTcBPack / 4 producers copy one 16-byte word each
