@@ -8,7 +8,8 @@ One step = one pass of the whole path on the level-4 6-D attitude workload:
             FP32 Jacobian / elimination / direction; FP64 residual, boundary
             rows, line search and update)
   Step III  surpluses of u*(x) at the nodes
-  on-line   u*(x) at 1e6 query states (half uniform, half N(0, 0.2^2) clipped)
+  on-line   u*(x) at 1e6 query states (half uniform, half N(0, 0.2^2) clipped),
+            3xTF32 on the tensor cores (error against FP64 reported beside)
 The headline value is converged BVP solves per second of whole-step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
@@ -56,7 +57,7 @@ DRAM_BYTES_PER_UNIT = {
     "k_condense_reg_fp32": ((295.942400e6 + 464.498432e6) / 88064, "interval"),
 }
 WORKLOAD = ("attitude6d_L4_1457nodes_T{10,20,40}_N{64,128,256}_mixedprec"
-            "+surplus+1e6queries")
+            "+surplus+1e6queries_tf32x3")
 
 # ALU peaks: the roofline divides by the FP32 / FP64 rates measured in the same
 # run by the library's FMA-chain probe (sg_fma_probe); these derived figures
@@ -890,7 +891,9 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--precision", choices=["mixed", "mixed-pair", "fp64"], default="mixed",
                     help="mixed: FP32 direction, FP64 residual; mixed-pair: the residual in pairs of floats")
-    ap.add_argument("--eval", choices=["df32", "fp64", "tf32x3"], default="df32")
+    ap.add_argument("--eval", choices=["df32", "fp64", "tf32x3"], default="tf32x3",
+                    help="interpolant arithmetic: 3xTF32 on the tensor cores (the precision form), "
+                         "DF32 (FP64-accurate on the FP32 pipe) or FP64")
     ap.add_argument("--form", choices=["auto", "phase", "phase-graph", "phase-graph-per-mesh", "persistent"],
                     default="auto",
                     help="execution form of the solve (auto: the library's autotuner picks)")
