@@ -88,6 +88,9 @@ class Server:
         self.problem = sg.problem_from(self.params)
         self.lo, self.hi = synth.box(6)
         self.precision, self.eval_mode, self.tol = precision, eval_mode, tol
+        # closed loops evaluate the feedback inside their own kernel, in FP64 or
+        # DF32; with 3xTF32 evaluations they take DF32
+        self.sim_mode = sg.EVAL_FP64 if eval_mode == sg.EVAL_FP64 else sg.EVAL_DF32
         self.merge = merge
         self.device = device or torch.device("cuda", torch.cuda.current_device())
         self.queue: deque[Request] = deque()        # eval and sim requests
@@ -196,7 +199,7 @@ class Server:
                 out = {"u": u.cpu()}
             else:
                 m = self.models[(r.level, r.T)]
-                o = sg.simulate_closed_loop(self.problem, m.surplus, xd, r.nsteps, r.dt, mode=self.eval_mode,
+                o = sg.simulate_closed_loop(self.problem, m.surplus, xd, r.nsteps, r.dt, mode=self.sim_mode,
                                             stream=stream)
                 out = {k: o[k].cpu() for k in ("xT", "cost")}
             stream.synchronize()

@@ -34,7 +34,7 @@ def _solo(server, r):
     m = server.models[(r.level, r.T)]
     if r.kind == "eval":
         return {"u": sg.eval_feedback(m.surplus, x, mode=server.eval_mode).cpu().numpy()}
-    o = sg.simulate_closed_loop(server.problem, m.surplus, x, r.nsteps, r.dt, mode=server.eval_mode)
+    o = sg.simulate_closed_loop(server.problem, m.surplus, x, r.nsteps, r.dt, mode=server.sim_mode)
     return {k: o[k].cpu().numpy() for k in ("xT", "cost")}
 
 
@@ -119,6 +119,22 @@ def _model_values(server, level, T):
     res = sg.solve_bvps(server.problem, g.coords, T, serving.horizon_mesh(T), tol=server.tol,
                         precision=server.precision, n_max=server.pool_nmax)
     return res["u0"].cpu().numpy()
+
+
+def test_tensor_core_evaluations_in_the_mix():
+    """A server whose evaluations run 3xTF32 (the bench's mode): evaluations
+    bitwise their solo results, simulations in DF32."""
+    server = serving.Server(slots=2, pool_slots=256, eval_mode=sg.EVAL_TF32X3)
+    keys = [(2, 20.0)]
+    counts = server.warm(levels=(2,), model_keys=keys)
+    reqs = serving.make_requests(12, rate=1e4, node_counts=counts, seed=5, levels=(2,), horizons=(20.0,),
+                                 mix=(1, 1, 1), max_queries=5000, max_traj=16, nsteps=50, model_keys=keys)
+    server.start()
+    done = serving.replay(server, reqs, realtime=False)
+    assert len(done) == len(reqs) and server.sim_mode == sg.EVAL_DF32
+    for r in done:
+        for k, v in _solo(server, r).items():
+            assert np.array_equal(r.result[k], v), (r.kind, r.rid, k)
 
 
 def test_admission_respects_memory_budget():
