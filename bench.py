@@ -459,7 +459,8 @@ def gpu_arm(args):
         kt = collect_kernel_times(sg)
         kt_form = "second timed region, same kernels launched one per phase"
     # FP64 / FP32 pipe peaks of this GPU, measured now, for the roofline fractions
-    probe = measure_pipe_peaks(sg, stream, local)
+    # (not in the launch-list mode, whose launches should be the step's alone)
+    probe = measure_pipe_peaks(sg, stream, local) if not args.only_steps else {}
     step_ms = [ev[s][0].elapsed_time(ev[s][4]) for s in range(args.steps)]
     phase_ms = {name: sum(ev[s][i].elapsed_time(ev[s][i + 1]) for s in range(args.steps)) / args.steps
                 for i, name in enumerate(["grid", "solve", "surplus", "eval"])}

@@ -575,8 +575,9 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
 constexpr int kCondLd = 28;                          // row stride of P, L and U (floats)
 constexpr int kCondSmemFloats = 36 * kCondLd * 2 + 8 * kCondLd + 32;    // P, L, U (ring of 8 rows), pivot order
 
+// (sm is not __restrict__: lanes exchange rows through it across __syncwarp.)
 __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const Workspace& w, int64_t node,
-                                                      int i, int N, int lane, float* __restrict__ sm) {
+                                                      int i, int N, int lane, float* sm) {
   const int64_t wid = node * a.Nmax + i;
   const float hf = static_cast<float>(a.T[node]) / static_cast<float>(N);
   const int64_t pbase = node * npts(a.Nmax) + 3 * int64_t(i);
@@ -816,8 +817,11 @@ __device__ __forceinline__ void blk_build(const float* __restrict__ J, const flo
   }
 }
 
+// sm is deliberately not __restrict__: its entries are written by one lane
+// and read by the others across __syncwarp, and a no-alias promise would let
+// the compiler move those reads above the barrier.
 __device__ __forceinline__ bool condense_interval_blk(const SolveArgs& a, const Workspace& w, int64_t node, int i,
-                                                      int N, int lane, float* __restrict__ sm) {
+                                                      int N, int lane, float* sm) {
   const int64_t wid = node * a.Nmax + i;
   const float hf = static_cast<float>(a.T[node]) / static_cast<float>(N);
   const float* J = static_cast<const float*>(w.Jm) + (node * npts(a.Nmax) + 3 * int64_t(i)) * 144;
