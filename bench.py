@@ -78,21 +78,6 @@ def flops_condense_interval() -> float:
     return 1728 + 36 * 10 + ge
 
 
-def flops_condense_blk_interval() -> float:
-    """Per interval, the block condensation (k_condense_blk): build of the
-    stage-2 system (49 x 12 scaled entries); LU of the 12 x 12 block P with its
-    37 other columns, sum_k (11-k) multipliers + 2 (11-k)(48-k); X = P^-1 M by
-    back substitution on the 37 columns (12 + 2 * 66 each); the stage-3 and
-    stage-4 rows rebuilt as build - c_k (M - X) (37 x 12 x (2 + 2 + 2)); LU of
-    the stage-3 block P3 eliminating the stage-4 rows with it,
-    sum_k (23-k) multipliers + 2 (23-k)(36-k); 24 reciprocals."""
-    lu1 = sum((11 - k) + 2 * (11 - k) * (48 - k) for k in range(12))
-    bs1 = 37 * (12 + 2 * 66)
-    rows = 37 * 12 * 6
-    lu2 = sum((23 - k) + 2 * (23 - k) * (36 - k) for k in range(12))
-    return 49 * 12 + lu1 + bs1 + rows + lu2 + 24
-
-
 def flops_abd_interval() -> float:
     """Per interval: elimination of 12 columns of the 18 x 25 panel, plus the
     back substitution (12 x 12 product and triangular solve)."""
@@ -834,10 +819,6 @@ def roofline(kt, iters, N_h, M, prec, nq=N_QUERIES, peaks=None):
     models = {
         "k_condense" + suffix: ("alu", flops_condense_interval() * int_units, peak_lin, "TFLOP/s"),
         "k_condense_reg_fp32": ("alu", flops_condense_interval() * int_units, pk32, "TFLOP/s"),
-        # the block condensation: every interval's work counted as the block
-        # form's (the few that fall back to partial pivoting redo theirs in
-        # k_condense_fallback, whose time is reported beside it)
-        "k_condense_blk_fp32": ("alu", flops_condense_blk_interval() * int_units, pk32, "TFLOP/s"),
         "k_abd" + suffix: ("alu", flops_abd_interval() * int_units, peak_lin, "TFLOP/s"),
         "k_abd_seg" + suffix: ("alu", flops_abd_seg_interval() * seg_units, peak_lin, "TFLOP/s"),
         "k_abd_red" + suffix: ("alu", flops_abd_interval() * red_units, peak_lin, "TFLOP/s"),

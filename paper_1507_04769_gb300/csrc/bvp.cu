@@ -232,8 +232,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
     SG_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), st));
     SG_TIMED(kname<T>("k_point"), st, (k_point<T><<<gp, 128, 0, st>>>(a, w)));
     if constexpr (sizeof(T) == sizeof(float)) {
-      SG_TIMED("k_condense_blk_fp32", st, (k_condense_blk<<<gwarp_int, 128, 0, st>>>(a, w)));
-      SG_TIMED("k_condense_fallback_fp32", st, (k_condense_fallback<<<gwarp_int, 128, 0, st>>>(a, w)));
+      SG_TIMED("k_condense_reg_fp32", st, (k_condense_reg<<<gwarp_int, 128, 0, st>>>(a, w)));
     } else {
       SG_TIMED("k_condense_smem_fp64", st,
                (k_condense_smem<<<static_cast<unsigned>(ceil_div(nint, kCondWarps)), 32 * kCondWarps, cond_smem,
@@ -368,8 +367,7 @@ static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, dou
   nb.memset0(w.counters, 2 * sizeof(int));
   nb.kernel(k_point<T>, gp, 128, 0, a, w);
   if constexpr (sizeof(T) == sizeof(float)) {
-    nb.kernel(k_condense_blk, gwi, 128, 0, a, w);
-    nb.kernel(k_condense_fallback, gwi, 128, 0, a, w);
+    nb.kernel(k_condense_reg, gwi, 128, 0, a, w);
   } else {
     nb.kernel(k_condense_smem, static_cast<unsigned>(ceil_div(nint, kCondWarps)), 32 * kCondWarps, cond_smem, a, w);
   }
@@ -966,8 +964,7 @@ static cudaError_t build_pool_graph(const SolveArgs& a, const Workspace& w, uint
   rb.memset0(w.counters, 2 * sizeof(int));
   rb.kernel(k_point<T>, gp, 128, 0, a, w);
   if constexpr (sizeof(T) == sizeof(float)) {
-    rb.kernel(k_condense_blk, gwi, 128, 0, a, w);
-    rb.kernel(k_condense_fallback, gwi, 128, 0, a, w);
+    rb.kernel(k_condense_reg, gwi, 128, 0, a, w);
   } else {
     rb.kernel(k_condense_smem, static_cast<unsigned>(ceil_div(nint, kCondWarps)), 32 * kCondWarps, cond_smem, a, w);
   }

@@ -4,12 +4,9 @@
 // One Newton iteration:
 //   k_point     Jacobian dF/dy (precision T) at every collocation point
 //   k_condense  the 36 linearised stage equations of one interval; Gaussian
-//               elimination of the two interior stages (24 columns) leaves
-//               the 12 x 25 block row [S | T | rhs] that couples y_i and
-//               y_{i+1}.  FP32: block elimination using the stage structure
-//               (k_condense_blk), with partial pivoting over the 24 interior
-//               rows for the intervals it leaves (k_condense_fallback); FP64:
-//               partial pivoting (k_condense_smem)
+//               elimination of the two interior stages (24 columns, partial
+//               pivoting over the 24 interior rows) leaves the 12 x 25 block
+//               row [S | T | rhs] that couples y_i and y_{i+1}
 //   k_abd_*     staircase elimination with partial pivoting over
 //               [x(0) rows; block rows; lambda(T) rows] and back substitution
 //               for the mesh-point corrections, segmented so that the serial
@@ -575,7 +572,9 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
 constexpr int kCondLd = 28;                          // row stride of P, L and U (floats)
 constexpr int kCondSmemFloats = 36 * kCondLd * 2 + 8 * kCondLd + 32;    // P, L, U (ring of 8 rows), pivot order
 
-// (sm is not __restrict__: lanes exchange rows through it across __syncwarp.)
+// (sm is not __restrict__: lanes exchange pivot rows through it across
+// __syncwarp, and a no-alias promise would let the compiler read it before
+// the barrier.)
 __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const Workspace& w, int64_t node,
                                                       int i, int N, int lane, float* sm) {
   const int64_t wid = node * a.Nmax + i;
@@ -767,244 +766,9 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
   __syncwarp();   // the tables are reused by the warp's next interval
 }
 
-// ---------------------------------------------------------------- block condensation (FP32)
-// The same condensation exploiting the structure of the Lobatto IIIA stage
-// equations.  In the 36 x 49 system the Jacobian block of stage row k on the
-// interior point j is delta_kj I - h a_kj J_j: every block of one column is a
-// multiple of the same J_j.  With P = I - h a22 J2 (stage-2 rows on Y2),
-//   the Y2 block of stage-k rows (k = 3, 4) = c_k (P - I),  c_k = a_k2 / a22,
-// so eliminating Y2 from them is
-//   [rest of row k] -= c_k (M - X),   M = stage-2 rows [Y3 | y_i | y_{i+1} | rhs],
-//                                    X = P^-1 M,
-// one 12 x 12 solve with 37 right-hand sides instead of 24 rows of updates.
-// Then the stage-3 rows' Y3 block P3 eliminates Y3 from the stage-4 rows.
-// Pivots are taken in place (no row exchange) within each 12 x 12 block; an
-// interval whose block multipliers exceed kBlkGrowth in magnitude, or that
-// meets a zero or non-finite pivot, is left to the partial-pivoting
-// condensation (k_condense_fallback), which it marks in column 25 of its
-// condensed row.  The stored pivot rows and the condensed row have the layout
-// of condense_interval_reg, so recovery and the staircase are unchanged.
-//
-// Layout: one warp per interval, the 49 columns on lanes (lane c holds column
-// c and lanes c < 17 also column 32 + c), the 12 rows of a block in registers.
-// Pivot-column entries (multipliers, U columns) reach the other lanes through
-// a small per-warp table in shared memory.
-constexpr float kBlkGrowth = 4.0f;
-constexpr int kBlkSmemFloats = 2 * 32 + 12 * 12 + 16;   // broadcast (double-buffered) | U columns | 1/pivots
-
-// Column s of the stage-(k+1) rows (k = 1, 2, 3): interior Y2 (s < 12), Y3
-// (s < 24), y_i (s < 36), y_{i+1} (s < 48), rhs (s = 48), with the identity
-// terms of the Jacobian of the stage equations.
-__device__ __forceinline__ void blk_build(const float* __restrict__ J, const float* __restrict__ res, float hf,
-                                          int k, int s, float (&v)[12]) {
-  if (s == 48) {
-#pragma unroll
-    for (int r = 0; r < 12; ++r) v[r] = -res[12 * (k - 1) + r];
-    return;
-  }
-  const int j = s < 12 ? 1 : (s < 24 ? 2 : (s < 36 ? 0 : 3));   // collocation point of the column
-  const int col = s < 12 ? s : (s < 24 ? s - 12 : (s < 36 ? s - 24 : s - 36));
-  const float cf = -hf * kLobAf[k][j];
-  const float* Jc = J + j * 144 + col;
-#pragma unroll
-  for (int r = 0; r < 12; ++r) v[r] = cf * Jc[r * 12];
-  // identity terms: +I on the row's own stage point, -I on y_i
-  const bool own = (j == k) || (k == 3 && j == 3);
-#pragma unroll
-  for (int r = 0; r < 12; ++r) {
-    if (r == col && own) v[r] += 1.0f;
-    if (r == col && j == 0) v[r] -= 1.0f;
-  }
-}
-
-// sm is deliberately not __restrict__: its entries are written by one lane
-// and read by the others across __syncwarp, and a no-alias promise would let
-// the compiler move those reads above the barrier.
-__device__ __forceinline__ bool condense_interval_blk(const SolveArgs& a, const Workspace& w, int64_t node, int i,
-                                                      int N, int lane, float* sm) {
-  const int64_t wid = node * a.Nmax + i;
-  const float hf = static_cast<float>(a.T[node]) / static_cast<float>(N);
-  const float* J = static_cast<const float*>(w.Jm) + (node * npts(a.Nmax) + 3 * int64_t(i)) * 144;
-  const float* res = static_cast<const float*>(w.Res) + wid * kResRows;
-  float* rec = static_cast<float*>(w.Rec) + wid * kRec;
-  float* cond = static_cast<float*>(w.Cond) + wid * kBlk;
-  float* bc = sm;                 // [2][32] multipliers and 1/pivot of the current step
-  float* Ucol = sm + 64;          // [12][12] column k of U above the diagonal (block 1)
-  float* Uinv = sm + 64 + 144;    // [12] 1/pivot (block 1)
-  const int sa = lane, sb = 32 + lane;   // this lane's columns (sb only for lanes < 17)
-  const bool hb = lane < 17;
-  bool ok = true;
-
-  // ---- block 1: stage-2 rows [P | M], LU of P in place, applied to M
-  float va[12], vb[12];
-  blk_build(J, res, hf, 1, sa, va);
-  if (hb) blk_build(J, res, hf, 1, sb, vb);
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    float* b = bc + (k & 1) * 32;
-    if (lane == k) {
-      const float piv = va[k];
-      const float inv = (piv != 0.0f && isfinite(piv)) ? __frcp_rn(piv) : 0.0f;
-      float big = inv == 0.0f ? INFINITY : 0.0f;
-#pragma unroll
-      for (int r = k + 1; r < 12; ++r) {
-        const float l = va[r] * inv;
-        b[r] = l;
-        big = fmaxf(big, fabsf(l));
-      }
-      b[31] = big;
-#pragma unroll
-      for (int r = 0; r < k; ++r) Ucol[k * 12 + r] = va[r];
-      Uinv[k] = inv;
-    }
-    __syncwarp();
-    ok = ok && !(b[31] > kBlkGrowth);
-#pragma unroll
-    for (int r = k + 1; r < 12; ++r) {
-      const float l = b[r];
-      if (sa > k) va[r] = fmaf(-l, va[k], va[r]);
-      if (hb) vb[r] = fmaf(-l, vb[k], vb[r]);
-    }
-  }
-  if (!ok) {
-    if (lane == 0) cond[25] = 1.0f;
-    return false;
-  }
-  // pivot rows 0..11 to the recovery rows: row r, column s (the U part of
-  // the P columns is at and right of the diagonal), 1/pivot in column 49
-#pragma unroll
-  for (int r = 0; r < 12; ++r) {
-    if (sa >= r) rec[r * kRecLd + sa] = va[r];
-    if (hb) rec[r * kRecLd + sb] = vb[r];
-  }
-  if (lane < 12) rec[lane * kRecLd + kRecInv] = Uinv[lane];
-  // X = U^-1 (L^-1 M) on the M columns (s >= 12), then D = M - X
-#pragma unroll
-  for (int k = 11; k >= 0; --k) {
-    const float inv = Uinv[k];
-    const float xa = va[k] * inv, xb = vb[k] * inv;
-    va[k] = xa;
-    vb[k] = xb;
-#pragma unroll
-    for (int r = 0; r < k; ++r) {
-      const float u = Ucol[k * 12 + r];
-      va[r] = fmaf(-u, xa, va[r]);
-      vb[r] = fmaf(-u, xb, vb[r]);
-    }
-  }
-  const float c3 = kLobAf[2][1] / kLobAf[1][1], c4 = kLobAf[3][1] / kLobAf[1][1];
-  // ---- block 2: stage-3 and stage-4 rows on the columns s >= 12, minus c_k D
-  float t3a[12], t4a[12], t3b[12], t4b[12];
-  {
-    float m[12];
-    if (sa >= 12) {
-      blk_build(J, res, hf, 1, sa, m);
-      blk_build(J, res, hf, 2, sa, t3a);
-      blk_build(J, res, hf, 3, sa, t4a);
-#pragma unroll
-      for (int r = 0; r < 12; ++r) {
-        const float d = m[r] - va[r];
-        t3a[r] = fmaf(-c3, d, t3a[r]);
-        t4a[r] = fmaf(-c4, d, t4a[r]);
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < 12; ++r) t3a[r] = t4a[r] = 0.0f;
-    }
-    if (hb) {
-      blk_build(J, res, hf, 1, sb, m);
-      blk_build(J, res, hf, 2, sb, t3b);
-      blk_build(J, res, hf, 3, sb, t4b);
-#pragma unroll
-      for (int r = 0; r < 12; ++r) {
-        const float d = m[r] - vb[r];
-        t3b[r] = fmaf(-c3, d, t3b[r]);
-        t4b[r] = fmaf(-c4, d, t4b[r]);
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < 12; ++r) t3b[r] = t4b[r] = 0.0f;
-    }
-  }
-  __syncwarp();   // the block-1 tables are reused below
-  // LU of P3 (stage-3 rows on Y3, columns 12..23) in place; the stage-4 rows
-  // are eliminated with it
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    float* b = bc + (k & 1) * 32;
-    if (lane == 12 + k) {
-      const float piv = t3a[k];
-      const float inv = (piv != 0.0f && isfinite(piv)) ? __frcp_rn(piv) : 0.0f;
-      float big = inv == 0.0f ? INFINITY : 0.0f;
-#pragma unroll
-      for (int r = k + 1; r < 12; ++r) {
-        const float l = t3a[r] * inv;
-        b[r] = l;
-        big = fmaxf(big, fabsf(l));
-      }
-#pragma unroll
-      for (int r = 0; r < 12; ++r) b[12 + r] = t4a[r] * inv;
-      b[30] = inv;
-      b[31] = big;
-    }
-    __syncwarp();
-    ok = ok && !(b[31] > kBlkGrowth);
-    if (lane < 12) {
-      if (lane == k) rec[(12 + k) * kRecLd + kRecInv] = b[30];
-    }
-    const bool ua = sa > 12 + k;
-#pragma unroll
-    for (int r = k + 1; r < 12; ++r) {
-      const float l = b[r];
-      if (ua) t3a[r] = fmaf(-l, t3a[k], t3a[r]);
-      if (hb) t3b[r] = fmaf(-l, t3b[k], t3b[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < 12; ++r) {
-      const float mr = b[12 + r];
-      if (ua) t4a[r] = fmaf(-mr, t3a[k], t4a[r]);
-      if (hb) t4b[r] = fmaf(-mr, t3b[k], t4b[r]);
-    }
-  }
-  if (!ok) {
-    if (lane == 0) cond[25] = 1.0f;
-    return false;
-  }
-  // pivot rows 12..23: stage-3 rows at and right of their diagonal column
-#pragma unroll
-  for (int r = 0; r < 12; ++r) {
-    if (sa >= 12 + r) rec[(12 + r) * kRecLd + sa] = t3a[r];
-    if (hb) rec[(12 + r) * kRecLd + sb] = t3b[r];
-  }
-  // the condensed block row [S | T | rhs]: stage-4 rows on columns 24..48
-#pragma unroll
-  for (int r = 0; r < 12; ++r) {
-    if (sa >= 24) cond[r * kBlkLd + sa - 24] = t4a[r];
-    if (hb) cond[r * kBlkLd + sb - 24] = t4b[r];
-  }
-  if (lane == 0) cond[25] = 0.0f;
-  return true;
-}
-
 constexpr int kCondRegWarps = 4;
 
-// The block condensation; intervals it leaves (marked in column 25 of the
-// condensed row) are condensed by k_condense_fallback, launched after it.
-__global__ void __launch_bounds__(32 * kCondRegWarps) k_condense_blk(SolveArgs a, Workspace w) {
-  __shared__ __align__(16) float sm[kCondRegWarps][kBlkSmemFloats];
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int64_t wid = blockIdx.x * int64_t(kCondRegWarps) + warp;
-  if (wid >= a.n * a.Nmax) return;
-  const int64_t node = wid / a.Nmax;
-  const int i = static_cast<int>(wid % a.Nmax);
-  if (!w.ns[node].active) return;
-  const int N = a.N[node];
-  if (i >= N) return;
-  condense_interval_blk(a, w, node, i, N, lane, sm[warp]);
-}
-
-__global__ void __launch_bounds__(32 * kCondRegWarps, 6) k_condense_fallback(SolveArgs a, Workspace w) {
+__global__ void __launch_bounds__(32 * kCondRegWarps, 6) k_condense_reg(SolveArgs a, Workspace w) {
   __shared__ __align__(16) float sm[kCondRegWarps][kCondSmemFloats];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -1015,7 +779,6 @@ __global__ void __launch_bounds__(32 * kCondRegWarps, 6) k_condense_fallback(Sol
   if (!w.ns[node].active) return;
   const int N = a.N[node];
   if (i >= N) return;
-  if (static_cast<const float*>(w.Cond)[(node * a.Nmax + i) * int64_t(kBlk) + 25] == 0.0f) return;
   condense_interval_reg(a, w, node, i, N, lane, sm[warp]);
 }
 
