@@ -423,7 +423,7 @@ def gpu_arm(args):
         # inside a graph the library's per-launch events see only the graph
         # launch; a second timed region runs the same kernels one launch per
         # phase for the per-kernel durations and the executed-kernel count
-        phase = dict(persistent=False, graph=0, blocks_per_sm=0)
+        phase = dict(form, persistent=False, graph=0, blocks_per_sm=0)
         for _ in range(2):
             sharded.sharded_solve(prob, x0_d, T_d, N_d, ranges=ranges, tol=TOL, precision=prec, workspace=ws,
                                   n_max=n_max, out=res_out, **phase)

@@ -151,6 +151,10 @@ typedef struct sg_solve_opts {
   int32_t warm_start;  /* 1: start Newton from the iterate in d_Y (which must then
                           be given) instead of the zero-control guess; d_Y
                           receives the final iterate as usual                    */
+  int32_t cond_warps;  /* FP32-direction forms: intervals (one warp each) per block
+                          of the stage condensation, 2, 4 or 8 (0 or anything
+                          else: 4).  A launch shape only: results are bitwise
+                          the same for every value                               */
 } sg_solve_opts;
 
 /* ---------------------------------------------------------------- errors */
@@ -317,10 +321,12 @@ int sg_pool_collect(sg_pool* pool, const int64_t* slots, int64_t count, double* 
 
 /* sg_autotune_solve - picks the execution form of sg_solve_bvps for a batch
  * (a shape tuner; the method itself is unchanged).  It solves the caller's
- * batch with each of the SG_AUTOTUNE_CANDIDATES candidate forms - 0 launch per
- * phase with a host loop, 1 the same as a CUDA graph with device-side loops,
- * 2 one such graph per mesh size (graph = 2), 3 and 4 the persistent
- * warp-per-node kernel as a graph with all / one resident block(s) per SM -
+ * batch with each of the SG_AUTOTUNE_CANDIDATES candidate forms and shapes -
+ * 0 launch per phase with a host loop, 1 the same as a CUDA graph with
+ * device-side loops, 2 one such graph per mesh size (graph = 2), 3 and 4 the
+ * same with condensation blocks of 2 and 8 intervals (cond_warps), 5 and 6
+ * the persistent warp-per-node kernel as a graph with all / one resident
+ * block(s) per SM -
  * timing each second run with CUDA events, and returns the fastest in *best
  * (base's tolerance, iteration cap, damping and precision are kept).  The
  * choice is cached per (precision, n, n_max_intervals, tol, max_iter,
@@ -329,7 +335,7 @@ int sg_pool_collect(sg_pool* pool, const int64_t* slots, int64_t count, double* 
  * solution.  report_ms (host, SG_AUTOTUNE_CANDIDATES entries, may be NULL)
  * receives the timings.
  * Synchronises `stream`.  Errors: those of sg_solve_bvps. */
-#define SG_AUTOTUNE_CANDIDATES 5
+#define SG_AUTOTUNE_CANDIDATES 7
 int sg_autotune_solve(const sg_problem* prob, const double* d_x0, int64_t n, const double* d_T,
                       const int32_t* d_N, int n_max_intervals, const sg_solve_opts* base,
                       void* d_work, size_t work_bytes, double* d_lambda0, double* d_u0,

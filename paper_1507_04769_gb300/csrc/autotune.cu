@@ -5,8 +5,10 @@
 //   0  launch per phase, host-driven loop
 //   1  launch per phase as a cached CUDA graph (device-side WHILE loops)
 //   2  one such graph per mesh size, the sizes' sub-batches on concurrent streams
-//   3  persistent warp-per-node kernel as a graph, as many blocks per SM as fit
-//   4  persistent warp-per-node kernel as a graph, 1 block (4 warps) per SM
+//   3  as 2, condensation blocks of 2 intervals (warps)
+//   4  as 2, condensation blocks of 8 intervals (warps)
+//   5  persistent warp-per-node kernel as a graph, as many blocks per SM as fit
+//   6  persistent warp-per-node kernel as a graph, 1 block (4 warps) per SM
 // Each candidate runs once to warm up (and build its graph) and once timed
 // with CUDA events on `stream`.  The choice is cached per (precision, n,
 // n_max_intervals, tolerance, iteration cap, damping).
@@ -36,7 +38,7 @@ extern "C" int sg_autotune_solve(const sg_problem* prob, const double* d_x0, int
                                  double* report_ms, int force, void* stream) {
   clear_error();
   if (!best) return fail(SG_EINVAL, "sg_autotune_solve: null output");
-  sg_solve_opts b{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0, 0};
+  sg_solve_opts b{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0, 0, 0};
   if (base) b = *base;
   b.warm_start = 0;   // the forms are timed on the zero-control solve
   const TuneKey key{b.precision, n, n_max_intervals, b.tol, b.max_iter, b.damping};
@@ -49,12 +51,19 @@ extern "C" int sg_autotune_solve(const sg_problem* prob, const double* d_x0, int
     }
   }
   constexpr int kCand = SG_AUTOTUNE_CANDIDATES;
-  sg_solve_opts cand[kCand] = {b, b, b, b, b};
-  cand[0].persistent = 0; cand[0].graph = 0; cand[0].blocks_per_sm = 0;
-  cand[1].persistent = 0; cand[1].graph = 1; cand[1].blocks_per_sm = 0;
-  cand[2].persistent = 0; cand[2].graph = 2; cand[2].blocks_per_sm = 0;
-  cand[3].persistent = 1; cand[3].graph = 1; cand[3].blocks_per_sm = 0;
-  cand[4].persistent = 1; cand[4].graph = 1; cand[4].blocks_per_sm = 1;
+  sg_solve_opts cand[kCand];
+  for (int c = 0; c < kCand; ++c) {
+    cand[c] = b;
+    cand[c].blocks_per_sm = 0;
+    cand[c].cond_warps = 4;
+  }
+  cand[0].persistent = 0; cand[0].graph = 0;
+  cand[1].persistent = 0; cand[1].graph = 1;
+  cand[2].persistent = 0; cand[2].graph = 2;
+  cand[3].persistent = 0; cand[3].graph = 2; cand[3].cond_warps = 2;
+  cand[4].persistent = 0; cand[4].graph = 2; cand[4].cond_warps = 8;
+  cand[5].persistent = 1; cand[5].graph = 1;
+  cand[6].persistent = 1; cand[6].graph = 1; cand[6].blocks_per_sm = 1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
   SG_CUDA_TRY(cudaEventCreate(&e0));

@@ -232,7 +232,9 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
     SG_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), st));
     SG_TIMED(kname<T>("k_point"), st, (k_point<T><<<gp, 128, 0, st>>>(a, w)));
     if constexpr (sizeof(T) == sizeof(float)) {
-      SG_TIMED("k_condense_reg_fp32", st, (k_condense_reg<<<gwarp_int, 128, 0, st>>>(a, w)));
+      const int cw = condense_reg_warps(a.cond_warps);
+      SG_TIMED("k_condense_reg_fp32", st,
+               (condense_reg_kernel(cw)<<<static_cast<unsigned>(ceil_div(nint, cw)), 32 * cw, 0, st>>>(a, w)));
     } else {
       SG_TIMED("k_condense_smem_fp64", st,
                (k_condense_smem<<<static_cast<unsigned>(ceil_div(nint, kCondWarps)), 32 * kCondWarps, cond_smem,
@@ -367,7 +369,8 @@ static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, dou
   nb.memset0(w.counters, 2 * sizeof(int));
   nb.kernel(k_point<T>, gp, 128, 0, a, w);
   if constexpr (sizeof(T) == sizeof(float)) {
-    nb.kernel(k_condense_reg, gwi, 128, 0, a, w);
+    const int cw = condense_reg_warps(a.cond_warps);
+    nb.kernel(condense_reg_kernel(cw), static_cast<unsigned>(ceil_div(nint, cw)), 32 * cw, 0, a, w);
   } else {
     nb.kernel(k_condense_smem, static_cast<unsigned>(ceil_div(nint, kCondWarps)), 32 * kCondWarps, cond_smem, a, w);
   }
@@ -694,7 +697,7 @@ extern "C" int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t
     return fail(SG_EINVAL, "sg_solve_bvps: n_max_intervals must be 1..65536");
   if (!d_x0 || !d_T || !d_N || !d_work || !d_lambda0 || !d_u0 || !d_V || !d_status || !d_iters)
     return fail(SG_EINVAL, "sg_solve_bvps: null device pointer");
-  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0, 0};
+  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0, 0, 0};
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iter < 0) return fail(SG_EINVAL, "sg_solve_bvps: bad tol or max_iter");
   if (o.warm_start && !d_Y) return fail(SG_EINVAL, "sg_solve_bvps: warm_start needs d_Y");
@@ -717,6 +720,7 @@ extern "C" int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t
   a.damping = o.damping;
   a.persistent = o.persistent;
   a.blocks_per_sm = o.blocks_per_sm;
+  a.cond_warps = o.cond_warps;
   a.sync_at_end = 1;
   a.Yin = o.warm_start ? d_Y : nullptr;
   a.res_pair = o.precision == SG_PREC_MIXED_PAIR ? 1 : 0;
@@ -787,7 +791,7 @@ extern "C" int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, 
     return fail(SG_EINVAL, "sg_solve_bvps_static: n_max_intervals must be 1..65536");
   if (!d_x0 || !d_T || !d_N || !d_lambda0 || !d_u0 || !d_V || !d_status || !d_iters)
     return fail(SG_EINVAL, "sg_solve_bvps_static: null device pointer");
-  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0, 0};
+  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0, 0, 0};
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iter < 0) return fail(SG_EINVAL, "sg_solve_bvps_static: bad tol or max_iter");
   if (o.warm_start && !d_Y) return fail(SG_EINVAL, "sg_solve_bvps_static: warm_start needs d_Y");
@@ -818,6 +822,7 @@ extern "C" int sg_solve_bvps_static(const sg_problem* prob, const double* d_x0, 
   a.damping = o.damping;
   a.persistent = o.persistent;
   a.blocks_per_sm = o.blocks_per_sm;
+  a.cond_warps = o.cond_warps;
   a.sync_at_end = 1;
   a.Yin = o.warm_start ? d_Y : nullptr;
   a.res_pair = o.precision == SG_PREC_MIXED_PAIR ? 1 : 0;
@@ -964,7 +969,8 @@ static cudaError_t build_pool_graph(const SolveArgs& a, const Workspace& w, uint
   rb.memset0(w.counters, 2 * sizeof(int));
   rb.kernel(k_point<T>, gp, 128, 0, a, w);
   if constexpr (sizeof(T) == sizeof(float)) {
-    rb.kernel(k_condense_reg, gwi, 128, 0, a, w);
+    const int cw = condense_reg_warps(a.cond_warps);
+    rb.kernel(condense_reg_kernel(cw), static_cast<unsigned>(ceil_div(nint, cw)), 32 * cw, 0, a, w);
   } else {
     rb.kernel(k_condense_smem, static_cast<unsigned>(ceil_div(nint, kCondWarps)), 32 * kCondWarps, cond_smem, a, w);
   }
@@ -1020,7 +1026,7 @@ extern "C" int sg_pool_create(const sg_problem* prob, int64_t slots, int n_max_i
   if (slots < 1 || slots > (int64_t(1) << 26)) return fail(SG_EINVAL, "sg_pool_create: slots must be 1..2^26");
   if (n_max_intervals < 1 || n_max_intervals > (1 << 16))
     return fail(SG_EINVAL, "sg_pool_create: n_max_intervals must be 1..65536");
-  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0, 0};
+  sg_solve_opts o{1e-8, 50, SG_PREC_FP64, 1, 0, 0, 0, 0, 0};
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iter < 0) return fail(SG_EINVAL, "sg_pool_create: bad tol or max_iter");
   if (o.precision != SG_PREC_FP64 && !fp32_direction(o.precision))
@@ -1047,6 +1053,7 @@ extern "C" int sg_pool_create(const sg_problem* prob, int64_t slots, int n_max_i
   p->a.tol = o.tol;
   p->a.max_iter = o.max_iter;
   p->a.damping = o.damping;
+  p->a.cond_warps = o.cond_warps;
   p->a.sync_at_end = 1;
   p->a.res_pair = o.precision == SG_PREC_MIXED_PAIR ? 1 : 0;
   p->fp32 = fp32_direction(o.precision);

@@ -97,6 +97,7 @@ struct SolveArgs {
   int damping;
   int persistent;      // one warp per node from a device queue (bvp_persistent.cuh)
   int blocks_per_sm;   // cap on resident 4-warp blocks per SM for the persistent form (0 = occupancy)
+  int cond_warps;      // intervals (warps) per block of the FP32 condensation: 2, 4 or 8
   int sync_at_end;
   const double* Yin;   // initial iterate (n x P x 12), or null for the zero-control guess
   int res_pair;        // FP32-direction form: 1 = residual in pairs of floats, 0 = in FP64
@@ -766,13 +767,14 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
   __syncwarp();   // the tables are reused by the warp's next interval
 }
 
-constexpr int kCondRegWarps = 4;
-
-__global__ void __launch_bounds__(32 * kCondRegWarps, 6) k_condense_reg(SolveArgs a, Workspace w) {
-  __shared__ __align__(16) float sm[kCondRegWarps][kCondSmemFloats];
+// W warps (intervals) per block, a shape the autotuner picks among 2, 4, 8;
+// 24 / W blocks per SM keep 24 warps resident at 80 registers whatever W.
+template <int W>
+__global__ void __launch_bounds__(32 * W, 24 / W) k_condense_reg(SolveArgs a, Workspace w) {
+  __shared__ __align__(16) float sm[W][kCondSmemFloats];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int64_t wid = blockIdx.x * int64_t(kCondRegWarps) + warp;
+  const int64_t wid = blockIdx.x * int64_t(W) + warp;
   if (wid >= a.n * a.Nmax) return;
   const int64_t node = wid / a.Nmax;
   const int i = static_cast<int>(wid % a.Nmax);
@@ -781,6 +783,12 @@ __global__ void __launch_bounds__(32 * kCondRegWarps, 6) k_condense_reg(SolveArg
   if (i >= N) return;
   condense_interval_reg(a, w, node, i, N, lane, sm[warp]);
 }
+
+// The FP32 condensation kernel and its block size for a given shape.
+inline void (*condense_reg_kernel(int cond_warps))(SolveArgs, Workspace) {
+  return cond_warps == 2 ? k_condense_reg<2> : (cond_warps == 8 ? k_condense_reg<8> : k_condense_reg<4>);
+}
+inline int condense_reg_warps(int cond_warps) { return cond_warps == 2 || cond_warps == 8 ? cond_warps : 4; }
 
 // Shared-memory FP64 form (used by the FP64 solve): the 36 x 49 system of one
 // interval in shared memory, one warp per interval, elimination of the first

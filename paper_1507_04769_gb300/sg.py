@@ -35,7 +35,7 @@ class Problem(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("damping", C.c_int32), ("persistent", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("graph", C.c_int32), ("warm_start", C.c_int32)]
+                ("graph", C.c_int32), ("warm_start", C.c_int32), ("cond_warps", C.c_int32)]
 
 
 class SGError(RuntimeError):
@@ -199,7 +199,7 @@ def workspace_bytes(n: int, n_max: int, precision: int = PREC_FP64) -> int:
 def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=50,
                precision=PREC_FP64, damping=True, n_max=None, return_Y=False,
                workspace: torch.Tensor | None = None, persistent=False, blocks_per_sm=0,
-               graph=False, out=None, Y0: torch.Tensor | None = None, stream=None):
+               graph=False, out=None, Y0: torch.Tensor | None = None, cond_warps=4, stream=None):
     """sg_solve_bvps on device tensors.  x0 (n, 6) f64; T (n,) f64; N (n,) int32.
     `out` may hold preallocated output tensors (keys lambda0, u0, V, status,
     iters); reusing them (and the workspace) lets graph=True replay one graph.
@@ -232,7 +232,7 @@ def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=5
         Y = torch.zeros((n, 3 * n_max + 1, 12), dtype=torch.float64, device=dev) if return_Y else None
     opts = SolveOpts(tol=tol, max_iter=max_iter, precision=precision, damping=int(bool(damping)),
                      persistent=int(bool(persistent)), blocks_per_sm=int(blocks_per_sm),
-                     graph=int(graph), warm_start=int(Y0 is not None))
+                     graph=int(graph), warm_start=int(Y0 is not None), cond_warps=int(cond_warps))
     _check(LIB.sg_solve_bvps(C.byref(problem), _ptr(x0), n, _ptr(T), _ptr(N), n_max, C.byref(opts),
                              _ptr(workspace), workspace.numel(), _ptr(out["lambda0"]), _ptr(out["u0"]),
                              _ptr(out["V"]), _ptr(out["status"]), _ptr(out["iters"]),
@@ -242,7 +242,8 @@ def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=5
     return out
 
 
-FORM_NAMES = ["phase-host-loop", "phase-graph", "phase-graph-per-mesh", "persistent-graph", "persistent-graph-1blk"]
+FORM_NAMES = ["phase-host-loop", "phase-graph", "phase-graph-per-mesh", "phase-graph-per-mesh-cond2",
+              "phase-graph-per-mesh-cond8", "persistent-graph", "persistent-graph-1blk"]
 
 
 def autotune_solve(problem: Problem, x0, T, N, *, tol=1e-8, max_iter=50, precision=PREC_FP64,
@@ -267,7 +268,8 @@ def autotune_solve(problem: Problem, x0, T, N, *, tol=1e-8, max_iter=50, precisi
     _check(LIB.sg_autotune_solve(C.byref(problem), _ptr(x0), n, _ptr(T), _ptr(N), n_max, C.byref(base),
                                  _ptr(workspace), workspace.numel(), *[_ptr(t) for t in outs], C.byref(best),
                                  ms, int(bool(force)), _stream(stream)))
-    choice = {"persistent": bool(best.persistent), "graph": int(best.graph), "blocks_per_sm": best.blocks_per_sm}
+    choice = {"persistent": bool(best.persistent), "graph": int(best.graph), "blocks_per_sm": best.blocks_per_sm,
+              "cond_warps": int(best.cond_warps)}
     return choice, {FORM_NAMES[i]: ms[i] for i in range(nc)}
 
 

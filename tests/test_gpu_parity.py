@@ -278,6 +278,21 @@ def test_graph_per_mesh_size_matches_one_graph_bitwise(prec):
     assert st[7] == sg.BADINPUT and st[11] == sg.BADINPUT and np.sum(st == sg.CONVERGED) == 298
 
 
+def test_condensation_block_shape_is_bitwise_neutral(att_case):
+    """cond_warps (intervals per block of the FP32 condensation) is a launch
+    shape: 2, 4 and 8 give bitwise the same solve, in the host loop and the
+    graph per mesh size."""
+    params, X0, T, N, _ = att_case
+    prob = sg.problem_from(params)
+    args = (prob, cuda(X0), cuda(T), cuda(N, torch.int32))
+    ref = sg.solve_bvps(*args, precision=sg.PREC_MIXED, n_max=128, cond_warps=4)
+    for cw in (2, 8):
+        for graph in (0, 2):
+            got = sg.solve_bvps(*args, precision=sg.PREC_MIXED, n_max=128, cond_warps=cw, graph=graph)
+            for key in ("lambda0", "u0", "V", "status", "iters"):
+                assert torch.equal(got[key], ref[key]), (cw, graph, key)
+
+
 def test_autotuner_picks_a_form_and_caches_it(att_case):
     params, X0, T, N, _ = att_case
     prob = sg.problem_from(params)
