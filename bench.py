@@ -47,14 +47,13 @@ N_QUERIES = 1_000_000
 TOL = 1e-8
 SEG_LEN = 16   # intervals per segment of the library's segmented staircase
 
-# dram__bytes_read.sum + dram__bytes_write.sum per unit from the ncu capture
-# summarised in profiles/solver_kernels_attitude6d_600nodes.md (first Newton
-# iteration of 600 level-4 nodes, 88,064 intervals: 298.8 + 483.1 MB).  Set an
-# entry to None when its kernel changes until it is captured again.
-# DRAM bytes per unit of work from an ncu capture of the kernel as it stands
-# (the 600-node solve case: 88,064 intervals in one launch)
+# dram__bytes_read.sum + dram__bytes_write.sum per unit of work from an ncu
+# capture of the kernel as it stands (the 600-node solve case: the first Newton
+# iteration, 88,064 intervals in one launch; profiles/
+# solver_kernels_attitude6d_600nodes.md).  An entry is removed when its kernel
+# changes, until it is captured again.
 DRAM_BYTES_PER_UNIT = {
-    "k_condense_reg_fp32": ((295.942400e6 + 464.498432e6) / 88064, "interval"),
+    "k_condense_reg_fp32": ((295.883776e6 + 464.296192e6) / 88064, "interval"),
 }
 WORKLOAD = ("attitude6d_L4_1457nodes_T{10,20,40}_N{64,128,256}_mixedprec"
             "+surplus+1e6queries_tf32x3")
