@@ -97,7 +97,10 @@ __device__ __forceinline__ df df_scale(df a, float s) {   // s exact power-of-tw
 }
 
 __device__ __forceinline__ df df_recip(df a) {
-  const float q = __frcp_rn(a.hi);
+  // the hardware's approximate reciprocal (a few ulp); the Newton correction
+  // below takes the pair to the same accuracy as from a rounded one
+  float q;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(a.hi));
   // residual 1 - a q, with a = hi + lo
   float r = __fmaf_rn(-a.hi, q, 1.0f);
   r = __fmaf_rn(-a.lo, q, r);
