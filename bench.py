@@ -832,6 +832,7 @@ def roofline(kt, iters, N_h, M, prec, nq=N_QUERIES, peaks=None):
         "k_eval_fp64": ("alu", flops_eval_query(M, 3) * nq, pk64, "TFLOP/s"),
         "k_eval_df32": ("alu", flops_eval_query(M, 3) * nq, pk32, "TFLOP/s"),
         "k_eval_tf32x3": ("alu", flops_eval_query(M, 3) * nq, pk32, "TFLOP/s"),
+        "k_eval_sf_tf32x3": ("alu", flops_eval_query(M, 3) * nq, pk32, "TFLOP/s"),
     }
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = 6785.9

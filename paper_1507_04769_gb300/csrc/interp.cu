@@ -336,6 +336,12 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   const size_t otcoff = take(tcoff_ok ? M * kMaxDim * sizeof(uint16_t) : 0);
   const size_t ofid = take(M * d * sizeof(uint16_t)), ofpt = take(M * d * sizeof(int16_t));
   const size_t oorder = take(M * sizeof(int32_t));
+  // the sum-factorised tensor-core plan (integer structure, host-made)
+  SfPlan sf;
+  const bool sf_ok = sf_plan(d, L, s->nf, k, M, fid, sf);
+  const size_t ometa = take(sf_ok ? sf.meta.size() : 0);
+  const size_t obmap = take(sf_ok ? sf.bmap.size() * sizeof(int32_t) : 0);
+  const size_t osfb = take(sf_ok ? sf.bbytes : 0);   // filled on the device (k_pack_sf)
   cudaError_t e = cudaMalloc(&s->block, off);
   if (e != cudaSuccess) {
     delete s;
@@ -357,6 +363,29 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   auto* d_fpt = reinterpret_cast<int16_t*>(base + ofpt);
   auto* d_tab1 = reinterpret_cast<double*>(base + otab1);
   auto* d_order = reinterpret_cast<int32_t*>(base + oorder);
+  if (sf_ok) {
+    s->sf_ok = 1;
+    s->sf_side = sf.side;
+    s->sf_nks = sf.nks;
+    s->sf_ngemv = sf.ngemv;
+    for (int i = 0; i < 5; ++i) s->sf_gseg[i] = sf.gseg[i];
+    s->sf_kw = sf.kw;
+    s->sf_o_gw = sf.o_gw;
+    s->sf_o_gops = sf.o_gops;
+    s->sf_nepi = sf.nepi;
+    s->sf_tmem = sf.tmem_cols;
+    s->sf_bbytes = sf.bbytes;
+    s->sf_smem = sf.smem;
+    s->sf_bfloats = sf.bmap.size();
+    s->sf_meta_bytes = sf.meta.size();
+    s->sf_o_aops = sf.o_aops;
+    s->sf_o_epi = sf.o_epi;
+    s->sf_o_prog = sf.o_prog;
+    s->sf_o_pstart = sf.o_pstart;
+    s->sf_meta = reinterpret_cast<unsigned char*>(base + ometa);
+    s->sf_bmap = reinterpret_cast<int32_t*>(base + obmap);
+    s->sf_b = reinterpret_cast<float*>(base + osfb);
+  }
   auto cleanup = [&](cudaError_t err, const char* what) {
     sg_surplus_free(s);
     return err == cudaErrorMemoryAllocation ? fail(SG_ENOMEM, what) : cuda_fail(err, what);
@@ -381,6 +410,10 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
     std::memcpy(h.data() + (ofid - ohost), fid.data(), M * d * sizeof(uint16_t));
     std::memcpy(h.data() + (ofpt - ohost), fpt.data(), M * d * sizeof(int16_t));
     std::memcpy(h.data() + (oorder - ohost), order.data(), M * sizeof(int32_t));
+    if (sf_ok) {
+      std::memcpy(h.data() + (ometa - ohost), sf.meta.data(), sf.meta.size());
+      std::memcpy(h.data() + (obmap - ohost), sf.bmap.data(), sf.bmap.size() * sizeof(int32_t));
+    }
     // (a copy from pageable memory is staged before the call returns)
     SG_TRY_CLEAN(cudaMemcpyAsync(base + ohost, h.data(), off - ohost, cudaMemcpyHostToDevice, st));
   }
@@ -400,6 +433,7 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   if (split_df(fine_n + 1, s->xf, s->xfdf, st) != SG_OK || split_df(M * k, s->Ws, s->Wdf, st) != SG_OK)
     return cleanup(cudaGetLastError(), "split_df");
   if (pack_tf32(s, st) != SG_OK) return cleanup(cudaGetLastError(), "pack_tf32");
+  if (sf_pack(s, st) != SG_OK) return cleanup(cudaGetLastError(), "sf_pack");
   SG_TRY_CLEAN(cudaStreamSynchronize(st));
 #undef SG_TRY_CLEAN
   *out = s;
@@ -448,7 +482,7 @@ extern "C" int sg_eval_feedback(const sg_surplus* s, const double* d_xq, int64_t
   for (int a = 0; a <= kMaxDim + 1; ++a) e.grp[a] = s->grp[a];
   e.out = d_out;
   if (mode == SG_EVAL_FP64) return eval_fp64(e, s->d, st);
-  if (mode == SG_EVAL_TF32X3) return eval_tf32x3(e, s, st);
+  if (mode == SG_EVAL_TF32X3) return s->sf_ok ? eval_sf_tf32x3(e, s, st) : eval_tf32x3(e, s, st);
   if (mode == SG_EVAL_DF32) return eval_df32(e, s->d, st);
   return fail(SG_EINVAL, "sg_eval_feedback: unknown mode");
 }

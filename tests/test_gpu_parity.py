@@ -372,7 +372,7 @@ def _tf32x3_bound(og, w, xq):
     return gamma * (np.abs(phi) @ np.abs(w))
 
 
-@pytest.mark.parametrize("d,L,k", [(6, 2, 3), (6, 4, 3), (3, 5, 2), (6, 3, 8)])
+@pytest.mark.parametrize("d,L,k", [(6, 2, 3), (6, 4, 3), (3, 5, 2), (6, 3, 8), (1, 5, 2), (4, 3, 5), (2, 6, 1)])
 def test_tf32x3_within_stated_bound(d, L, k):
     lo, hi = synth.box(d)
     g = sg.Grid(d, L, lo, hi)
@@ -387,6 +387,65 @@ def test_tf32x3_within_stated_bound(d, L, k):
     assert np.all(np.isfinite(u))
     assert np.max(np.abs(u - ref) / bound) <= 1.0
     assert rel(u, ref) <= 1e-5
+
+
+def _kernels_launched(fn):
+    """Names of the library kernels launched by fn (per-launch timing)."""
+    import ctypes as C
+    sg.LIB.sg_timing_enable(1)
+    try:
+        fn()
+        torch.cuda.synchronize()
+    finally:
+        sg.LIB.sg_timing_enable(0)
+    n_max, name_len = 64, 64
+    names = C.create_string_buffer(n_max * name_len)
+    nk = C.c_int()
+    sg.LIB.sg_timing_collect.argtypes = [C.c_int, C.c_char_p, C.c_int, C.c_void_p, C.c_void_p,
+                                         C.POINTER(C.c_int)]
+    assert sg.LIB.sg_timing_collect(n_max, names, name_len, None, None, C.byref(nk)) == 0
+    raw = names.raw
+    return {raw[i * name_len:(i + 1) * name_len].split(b"\0", 1)[0].decode() for i in range(nk.value)}
+
+
+@pytest.mark.parametrize("d,L,k,kernel", [(6, 4, 3, "k_eval_sf_tf32x3"), (6, 2, 8, "k_eval_sf_tf32x3"),
+                                          (1, 5, 2, "k_eval_tf32x3")])
+def test_tf32x3_kernel_for_the_shape(d, L, k, kernel):
+    """The sum-factorised kernel serves grids whose plan fits (d >= 2); others
+    keep the per-node contraction.  Both agree with the FP64 evaluation."""
+    lo, hi = synth.box(d)
+    g = sg.Grid(d, L, lo, hi)
+    f = np.random.default_rng(3).standard_normal((g.M, k))
+    S = sg.Surplus(g, cuda(f))
+    xq = cuda(synth.mixed_queries(5000, lo, hi, seed=4))
+    out = {}
+    names = _kernels_launched(lambda: out.setdefault("u", sg.eval_feedback(S, xq, mode=sg.EVAL_TF32X3)))
+    assert kernel in names, names
+    ref = sg.eval_feedback(S, xq, mode=sg.EVAL_FP64)
+    assert ((out["u"] - ref).abs().max() / ref.abs().max()).item() <= 1e-5
+
+
+def test_tf32x3_at_nodes_edges_and_outside():
+    """Queries on grid nodes (up to the last bit), next to them, on the box
+    faces and outside the box: finite and within the stated bound."""
+    d, L, k = 6, 4, 3
+    lo, hi = synth.box(d)
+    g = sg.Grid(d, L, lo, hi)
+    og = ogrid.Grid(d, L, lo, hi)
+    f = np.random.default_rng(8).standard_normal((og.M, k))
+    S = sg.Surplus(g, cuda(f))
+    w = ointerp.surpluses(og, f)
+    rng = np.random.default_rng(9)
+    nodes = og.x[rng.choice(og.M, 200, replace=False)]
+    near = nodes * (1 + rng.choice([-1, 1], nodes.shape) * 1e-15)
+    faces = synth.uniform_queries(100, lo, hi, seed=10)
+    faces[np.arange(100), rng.integers(0, d, 100)] = np.where(rng.random(100) < 0.5, lo[0], hi[0])
+    outside = synth.uniform_queries(100, lo - 0.2 * (hi - lo), hi + 0.2 * (hi - lo), seed=11)
+    xq = np.concatenate([nodes, near, faces, outside])
+    u = sg.eval_feedback(S, cuda(xq), mode=sg.EVAL_TF32X3).cpu().numpy()
+    ref = ointerp.eval_surplus(og, w, xq)
+    assert np.all(np.isfinite(u))
+    assert np.max(np.abs(u - ref) / _tf32x3_bound(og, w, xq)) <= 1.0
 
 
 def test_tf32x3_smooth_feedback_at_full_size():
