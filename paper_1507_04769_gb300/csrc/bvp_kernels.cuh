@@ -560,9 +560,9 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
 //   Phase A (rows on lanes): lane r holds interior row r (r < 24) or stage-4
 //   row r (24..31); lanes 24..27 also hold stage-4 rows 32..35.  Only the 24
 //   interior columns live in registers.  Partial pivoting over the interior
-//   rows; at step k the pivot lane publishes its row and 1/pivot in the
-//   shared-memory table U (16-byte broadcast reads), and every row records
-//   its multiplier l(r, k) in L.
+//   rows; at step k the pivot lane publishes its row in the
+//   shared-memory table U (16-byte broadcast reads), every lane forms
+//   1/pivot from it, and every row records its multiplier l(r, k) in L.
 //   Phase B (columns on lanes): lane c < 25 owns passive column c.  With the
 //   pivot order p_k, the passive part of pivot row k is
 //       Q_k = P(p_k) - sum_{j<k} l(p_k, j) Q_j
@@ -656,20 +656,17 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
   unsigned kmask = lane < 24 ? ~31u : 0u;
   unsigned ktag = lane < 24 ? itag : 0u;
   float live = 1.0f;                        // 0 once the row is a pivot row
-  bool bad = false;
+  bool bad = false;                         // a zero or non-finite pivot (the same in every lane)
+  float inv_keep = 0.0f;                    // lane j < 8: 1/pivot of the last step k with k % 8 == j
 #pragma unroll
   for (int k = 0; k < 24; ++k) {
     const int q0 = k / 4;
     const unsigned key = ((__float_as_uint(ra[k]) << 1) & kmask) | ktag;
     const unsigned best = __reduce_max_sync(0xffffffffu, key);
     if ((best & 31u) == itag && ktag != 0u) {
-      const float pv = ra[k];
-      const float inv = (pv != 0.0f && isfinite(pv)) ? __frcp_rn(pv) : 0.0f;
-      bad = inv == 0.0f;
       float4* dst = reinterpret_cast<float4*>(U_s + (k & 7) * kCondLd);
 #pragma unroll
       for (int q = q0; q < 6; ++q) dst[q] = make_float4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
-      dst[6] = make_float4(inv, 0.0f, 0.0f, 0.0f);
       perm_s[k] = lane;
       kmask = 0u;
       ktag = 0u;
@@ -677,7 +674,12 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     }
     __syncwarp();
     const float4* src = reinterpret_cast<const float4*>(U_s + (k & 7) * kCondLd);
-    const float inv = src[6].x;
+    // every lane forms 1/pivot from the published row (the same correctly
+    // rounded reciprocal; zero for a zero or non-finite pivot)
+    const float pv = U_s[(k & 7) * kCondLd + k];
+    const float inv = (pv != 0.0f && isfinite(pv)) ? __frcp_rn(pv) : 0.0f;
+    if (lane == (k & 7)) inv_keep = inv;
+    bad = bad || inv == 0.0f;
     const float la = ra[k] * (inv * live);
 #pragma unroll
     for (int q = q0; q < 6; ++q) {
@@ -710,11 +712,11 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
         if (q >= kk / 4)
           reinterpret_cast<float4*>(rec + kk * kRecLd)[q] = reinterpret_cast<const float4*>(U_s + (kk & 7) * kCondLd)[q];
       }
-      if (lane < 8) rec[(k0 + lane) * kRecLd + kRecInv] = U_s[lane * kCondLd + 24];
+      if (lane < 8) rec[(k0 + lane) * kRecLd + kRecInv] = inv_keep;
       __syncwarp();
     }
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) w.ns[node].singular = 1;
+  if (bad && lane == 0) w.ns[node].singular = 1;
   // multipliers to L (a pivot row's entries from its own step on are never read)
   {
     float4* d4 = reinterpret_cast<float4*>(L_s + lane * kCondLd);
@@ -1180,16 +1182,19 @@ __global__ void __launch_bounds__(32 * seg_warps<T>()) k_abd_seg(SolveArgs a, Wo
     // to the lower lane); rows that are no candidates have zero mask and tag
     unsigned kmask = lane < 24 ? ~31u : 0u;
     unsigned ktag = lane < 24 ? itag : 0u;
+    T inv_keep = T(0);   // FP32: lane k < 12 keeps 1/pivot of step k
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       const int q0 = k / V;
       const unsigned key = (mag_key(ya[k]) & kmask) | ktag;
       const unsigned best = __reduce_max_sync(0xffffffffu, key);
       if ((best & 31u) == itag && ktag != 0u) {
-        const T piv = ya[k];
-        const bool good = piv != T(0) && isfinite(piv);
-        bad = bad || !good;
-        ya[k] = good ? recip_rn(piv) : T(0);
+        if constexpr (sizeof(T) == sizeof(double)) {   // FP64: the pivot lane publishes 1/pivot
+          const T piv = ya[k];
+          const bool good = piv != T(0) && isfinite(piv);
+          bad = bad || !good;
+          ya[k] = good ? recip_rn(piv) : T(0);
+        }
         store_row12_from<T>(U_s + k * 12, ya, q0);
         perm_s[k] = lane;
         kmask = 0u;
@@ -1197,7 +1202,18 @@ __global__ void __launch_bounds__(32 * seg_warps<T>()) k_abd_seg(SolveArgs a, Wo
       }
       __syncwarp();
       const T* u = U_s + k * 12;
-      const T la = ktag != 0u ? ya[k] * u[k] : T(0);
+      T inv = u[k];
+      if constexpr (sizeof(T) == sizeof(float)) {
+        // FP32: the row is published with its raw pivot and every lane forms
+        // the same correctly rounded 1/pivot (off the pivot lane's path);
+        // lane k keeps it for the diagonal of the stored row
+        const T piv = inv;
+        const bool good = piv != T(0) && isfinite(piv);
+        bad = bad || !good;
+        inv = good ? recip_rn(piv) : T(0);
+        if (lane == k) inv_keep = inv;
+      }
+      const T la = ktag != 0u ? ya[k] * inv : T(0);
 #pragma unroll
       for (int q = q0; q < 12 / V; ++q) {
         T uv[V];
@@ -1217,6 +1233,9 @@ __global__ void __launch_bounds__(32 * seg_warps<T>()) k_abd_seg(SolveArgs a, Wo
       ya[k] = la;   // column k is done: the row keeps its multiplier there
     }
     if (lane < 24) store_row12_from<T>(L_s + lane * 12, ya, 0);   // a pivot row's entries from its step on are never read
+    if constexpr (sizeof(T) == sizeof(float)) {
+      if (lane < 12) U_s[lane * 12 + lane] = inv_keep;   // 1/pivot on the diagonal of the stored rows
+    }
     const unsigned cmask = __ballot_sync(0xffffffffu, ktag != 0u);   // the 12 rows that were no pivot
     if (ktag != 0u) cslot_s[__popc(cmask & lt_mask)] = lane;
     __syncwarp();

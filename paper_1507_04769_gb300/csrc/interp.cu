@@ -326,7 +326,11 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   const size_t oWdf = take(M * k * sizeof(float2)), oxf = take((fine_n + 1) * sizeof(double));
   const size_t oxfdf = take((fine_n + 1) * sizeof(float2));
   const size_t otab1 = take(size_t(s->nf) * (fine_n + 1) * sizeof(double));
-  const size_t npack = tf32_pack_floats(M, k);
+  // the sum-factorised tensor-core plan (integer structure, host-made); the
+  // per-node tensor-core pack only where that plan does not fit
+  SfPlan sf;
+  const bool sf_ok = sf_plan(d, L, s->nf, k, M, fid, sf);
+  const size_t npack = sf_ok ? 0 : tf32_pack_floats(M, k);
   const size_t obp = take(npack * sizeof(float)), oerr = take(sizeof(int));
   const size_t ohost = off;
   const size_t obox = take(2 * d * sizeof(double)), onact = take(M), oops = take(M * kMaxDim * sizeof(uint16_t));
@@ -336,9 +340,6 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   const size_t otcoff = take(tcoff_ok ? M * kMaxDim * sizeof(uint16_t) : 0);
   const size_t ofid = take(M * d * sizeof(uint16_t)), ofpt = take(M * d * sizeof(int16_t));
   const size_t oorder = take(M * sizeof(int32_t));
-  // the sum-factorised tensor-core plan (integer structure, host-made)
-  SfPlan sf;
-  const bool sf_ok = sf_plan(d, L, s->nf, k, M, fid, sf);
   const size_t ometa = take(sf_ok ? sf.meta.size() : 0);
   const size_t obmap = take(sf_ok ? sf.bmap.size() * sizeof(int32_t) : 0);
   const size_t osfb = take(sf_ok ? sf.bbytes : 0);   // filled on the device (k_pack_sf)
@@ -432,6 +433,7 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   SG_TRY_CLEAN(cudaGetLastError());
   if (split_df(fine_n + 1, s->xf, s->xfdf, st) != SG_OK || split_df(M * k, s->Ws, s->Wdf, st) != SG_OK)
     return cleanup(cudaGetLastError(), "split_df");
+  SG_TRY_CLEAN(cudaMemsetAsync(s->tc_err, 0, sizeof(int), st));
   if (pack_tf32(s, st) != SG_OK) return cleanup(cudaGetLastError(), "pack_tf32");
   if (sf_pack(s, st) != SG_OK) return cleanup(cudaGetLastError(), "sf_pack");
   SG_TRY_CLEAN(cudaStreamSynchronize(st));

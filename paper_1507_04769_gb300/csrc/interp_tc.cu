@@ -318,14 +318,12 @@ size_t tf32_pack_floats(int64_t M, int k) {
   return size_t(ceil_div(M, kTcChunk)) * kTcBPack;
 }
 
-// s->bpack (tf32_pack_floats(M, k) floats) and s->tc_err come with the
+// s->bpack (tf32_pack_floats(M, k) floats) and s->tc_err (zeroed) come with the
 // surplus's allocation.
 int pack_tf32(sg_surplus* s, cudaStream_t st) {
-  if (s->k > kTcN / 2) return SG_OK;   // the tensor-core path serves k <= 8
+  if (s->k > kTcN / 2 || !s->bpack) return SG_OK;   // k <= 8, and only where the pack was allocated
   const int nchunks = static_cast<int>(ceil_div(s->M, kTcChunk));
   s->tc_chunks = nchunks;
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(s->tc_err, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "pack_tf32: memset");
   const int64_t total = int64_t(nchunks) * kTcChunk * kTcN;
   SG_TIMED("k_pack_tf32", st,
            (k_pack_tf32<<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(s->M, s->k, nchunks, s->Ws,
