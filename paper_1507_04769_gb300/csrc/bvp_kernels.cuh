@@ -658,6 +658,7 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
   float live = 1.0f;                        // 0 once the row is a pivot row
   bool bad = false;                         // a zero or non-finite pivot (the same in every lane)
   float inv_keep = 0.0f;                    // lane j < 8: 1/pivot of the last step k with k % 8 == j
+  float lbk[3] = {0.f, 0.f, 0.f};           // multipliers of row r2 at columns sub, sub + 8, sub + 16
 #pragma unroll
   for (int k = 0; k < 24; ++k) {
     const int q0 = k / 4;
@@ -702,7 +703,7 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
         if (c > k) rb[m] = fmaf(-lb, U_s[(k & 7) * kCondLd + c], rb[m]);
       }
     }
-    if (sub == 0) L_s[r2 * kCondLd + k] = lb;
+    if ((k & 7) == sub) lbk[k >> 3] = lb;   // row r2's multiplier of column k, kept by lane sub
     if ((k & 7) == 7) {
       // the ring is full: rows k - 7 .. k to the recovery rows (at and right
       // of the diagonal chunk) with 1/pivot
@@ -717,6 +718,8 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     }
   }
   if (bad && lane == 0) w.ns[node].singular = 1;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) L_s[r2 * kCondLd + sub + 8 * m] = lbk[m];
   // multipliers to L (a pivot row's entries from its own step on are never read)
   {
     float4* d4 = reinterpret_cast<float4*>(L_s + lane * kCondLd);

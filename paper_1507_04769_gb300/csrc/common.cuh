@@ -57,6 +57,14 @@ inline cudaError_t ensure_dynamic_smem(F* func, size_t bytes) {
                               cap);
 }
 
+// The device blocks of grid and surplus handles come from a library-owned
+// stream-ordered pool per device that keeps up to 1 GiB of freed blocks, so
+// building and freeing a handle every step costs no cudaMalloc/cudaFree.
+// block_free synchronises the device first (a handle's last use may be on
+// any stream), as cudaFree does.
+cudaError_t block_alloc(void** p, size_t bytes, cudaStream_t st);
+void block_free(void* p);
+
 constexpr int kMaxDim = 8;
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs
 

@@ -128,7 +128,7 @@ extern "C" int sg_build_grid(int d, int level, const double* h_lo, const double*
     return e == cudaSuccess ? fail(code, what) : cuda_fail(e, what);
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&g->block, off)) != cudaSuccess) return cleanup(SG_ENOMEM, "cudaMalloc grid", e);
+  if ((e = block_alloc(&g->block, off, nullptr)) != cudaSuccess) return cleanup(SG_ENOMEM, "device allocation of the grid", e);
   char* base = static_cast<char*>(g->block);
   g->coords = reinterpret_cast<double*>(base + ocoords);
   g->lev = reinterpret_cast<int8_t*>(base + olev);
@@ -165,6 +165,6 @@ extern "C" int sg_grid_info(const sg_grid* g, int64_t* n_nodes, int* d, int* lev
 
 extern "C" void sg_grid_free(sg_grid* g) {
   if (!g) return;
-  if (g->block) cudaFree(g->block);
+  block_free(g->block);
   delete g;
 }

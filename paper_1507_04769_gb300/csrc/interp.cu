@@ -15,6 +15,8 @@
 #include <cmath>
 #include <numeric>
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -247,26 +249,45 @@ int eval_fp64(const EvalArgs& e, int d, cudaStream_t st) {
 
 using namespace sg;
 
-extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int k, sg_surplus** out,
-                                  void* stream) {
-  clear_error();
-  if (!g || !d_values || !out) return fail(SG_EINVAL, "sg_build_surpluses: null pointer");
-  *out = nullptr;
-  if (k < 1 || k > kMaxOut) return fail(SG_EINVAL, "sg_build_surpluses: k must be 1..16");
-  if (g->level > kMaxLevel) return fail(SG_EUNSUPPORTED, "sg_build_surpluses: level above 8");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+namespace sg {
+namespace {
+// The host-made part of a surplus build: the integer structure of the grid's
+// nodes (function ids, fine positions, level ranges, evaluation order, active
+// dimensions and table offsets, the sum-factorised plan), the layout of the
+// surplus's one device allocation, and the bytes of it that the host fills
+// (all but the box).  It depends on the grid's node structure and on k only,
+// so builds on grids of the same structure (a grid rebuilt every step) reuse
+// it: a small cache keyed by (d, L, k) and checked against the grid's levels
+// and indices.
+struct SurplusHost {
+  int d = 0, L = 0, k = 0, nf = 0, amax = 0;
+  int64_t M = 0;
+  std::vector<int8_t> lev;      // the key: the grid's integer structure
+  std::vector<int16_t> kidx;
+  std::vector<int64_t> level_start;
+  int64_t grp[kMaxDim + 2] = {};
+  bool sf_ok = false, tcoff_ok = false;
+  SfPlan sf;                    // scalar fields (its tables are in `staging`)
+  size_t npack = 0, off = 0, ohost = 0;
+  size_t oW = 0, oWs = 0, oWdf = 0, oxf = 0, oxfdf = 0, otab1 = 0, obp = 0, oerr = 0, osfb = 0;
+  size_t obox = 0, onact = 0, oops = 0, otcoff = 0, ofid = 0, ofpt = 0, oorder = 0, ometa = 0, obmap = 0;
+  std::vector<unsigned char> staging;   // bytes [ohost, off) of the allocation, box zero
+};
+
+std::shared_ptr<const SurplusHost> make_surplus_host(const sg_grid* g, int k) {
+  auto h = std::make_shared<SurplusHost>();
   const int d = g->d, L = g->level, fine_n = 1 << L;
   const int64_t M = g->M;
-  auto* s = new sg_surplus();
-  s->d = d;
-  s->level = L;
-  s->k = k;
-  s->M = M;
-  s->nf = n_functions(L);
-  // host: integer structure (function ids, fine positions, level ranges, order)
+  h->d = d;
+  h->L = L;
+  h->k = k;
+  h->M = M;
+  h->nf = n_functions(L);
+  h->lev = g->h_lev;
+  h->kidx = g->h_kidx;
+  // integer structure (function ids, fine positions, level ranges, order)
   std::vector<uint16_t> fid(M * d);
   std::vector<int16_t> fpt(M * d);
-  std::vector<int64_t> level_start;
   int prev_sum = -1;
   for (int64_t n = 0; n < M; ++n) {
     int sum = 0;
@@ -277,11 +298,11 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
       fpt[n * d + dim] = static_cast<int16_t>(l == 1 ? fine_n / 2 : kk * (fine_n >> (l - 1)));
     }
     if (sum != prev_sum) {
-      level_start.push_back(n);
+      h->level_start.push_back(n);
       prev_sum = sum;
     }
   }
-  level_start.push_back(M);
+  h->level_start.push_back(M);
   // evaluation order: by the number of active dimensions (so that a kernel
   // can take each group with a fixed-length basis product), then the
   // function ids lexicographically
@@ -299,72 +320,148 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   });
   std::vector<uint8_t> nact(M, 0);
   std::vector<uint16_t> ops(M * kMaxDim, 0);
-  for (int a = 0; a <= kMaxDim + 1; ++a) s->grp[a] = M;
+  for (int a = 0; a <= kMaxDim + 1; ++a) h->grp[a] = M;
   for (int64_t r = M - 1; r >= 0; --r) {
     const int32_t n = order[r];
     int na = 0;
     for (int dim = 0; dim < d; ++dim) {
       const int id = fid[int64_t(n) * d + dim];
-      if (id != 0) ops[r * kMaxDim + na++] = static_cast<uint16_t>(dim * s->nf + id);
+      if (id != 0) ops[r * kMaxDim + na++] = static_cast<uint16_t>(dim * h->nf + id);
     }
     nact[r] = static_cast<uint8_t>(na);
-    if (na > s->amax) s->amax = na;
-    for (int a = 0; a <= na; ++a) s->grp[a] = r < s->grp[a] ? r : s->grp[a];
+    if (na > h->amax) h->amax = na;
+    for (int a = 0; a <= na; ++a) h->grp[a] = r < h->grp[a] ? r : h->grp[a];
   }
   // grp[a] = first node with at least a active dimensions (non-decreasing)
-  for (int a = kMaxDim; a >= 0; --a) s->grp[a] = s->grp[a] < s->grp[a + 1] ? s->grp[a] : s->grp[a + 1];
+  for (int a = kMaxDim; a >= 0; --a) h->grp[a] = h->grp[a] < h->grp[a + 1] ? h->grp[a] : h->grp[a + 1];
 
   // one device allocation: the surplus's arrays and the build's tables; the
-  // host-made tables go in with one copy
+  // device-computed ones first, then the host-made ones (one copy)
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
     off += (bytes + 255) & ~size_t(255);
     return o;
   };
-  const size_t oW = take(M * k * sizeof(double)), oWs = take(M * k * sizeof(double));
-  const size_t oWdf = take(M * k * sizeof(float2)), oxf = take((fine_n + 1) * sizeof(double));
-  const size_t oxfdf = take((fine_n + 1) * sizeof(float2));
-  const size_t otab1 = take(size_t(s->nf) * (fine_n + 1) * sizeof(double));
-  // the sum-factorised tensor-core plan (integer structure, host-made); the
-  // per-node tensor-core pack only where that plan does not fit
-  SfPlan sf;
-  const bool sf_ok = sf_plan(d, L, s->nf, k, M, fid, sf);
-  const size_t npack = sf_ok ? 0 : tf32_pack_floats(M, k);
-  const size_t obp = take(npack * sizeof(float)), oerr = take(sizeof(int));
-  const size_t ohost = off;
-  const size_t obox = take(2 * d * sizeof(double)), onact = take(M), oops = take(M * kMaxDim * sizeof(uint16_t));
+  h->oW = take(M * k * sizeof(double));
+  h->oWs = take(M * k * sizeof(double));
+  h->oWdf = take(M * k * sizeof(float2));
+  h->oxf = take((fine_n + 1) * sizeof(double));
+  h->oxfdf = take((fine_n + 1) * sizeof(float2));
+  h->otab1 = take(size_t(h->nf) * (fine_n + 1) * sizeof(double));
+  // the sum-factorised tensor-core plan; the per-node tensor-core pack only
+  // where that plan does not fit
+  h->sf_ok = sf_plan(d, L, h->nf, k, M, fid, h->sf);
+  h->npack = h->sf_ok ? 0 : tf32_pack_floats(M, k);
+  h->obp = take(h->npack * sizeof(float));
+  h->oerr = take(sizeof(int));
+  h->osfb = take(h->sf_ok ? h->sf.bbytes : 0);   // filled on the device (k_pack_sf)
+  h->ohost = off;
+  h->obox = take(2 * d * sizeof(double));
+  h->onact = take(M);
+  h->oops = take(M * kMaxDim * sizeof(uint16_t));
   // the tensor-core kernel's table offsets: ops scaled by its 128 table rows
   // (uint16, so the tables must have at most 511 entries per query)
-  const bool tcoff_ok = npack && size_t(d) * s->nf <= 511;
-  const size_t otcoff = take(tcoff_ok ? M * kMaxDim * sizeof(uint16_t) : 0);
-  const size_t ofid = take(M * d * sizeof(uint16_t)), ofpt = take(M * d * sizeof(int16_t));
-  const size_t oorder = take(M * sizeof(int32_t));
-  const size_t ometa = take(sf_ok ? sf.meta.size() : 0);
-  const size_t obmap = take(sf_ok ? sf.bmap.size() * sizeof(int32_t) : 0);
-  const size_t osfb = take(sf_ok ? sf.bbytes : 0);   // filled on the device (k_pack_sf)
-  cudaError_t e = cudaMalloc(&s->block, off);
+  h->tcoff_ok = h->npack && size_t(d) * h->nf <= 511;
+  h->otcoff = take(h->tcoff_ok ? M * kMaxDim * sizeof(uint16_t) : 0);
+  h->ofid = take(M * d * sizeof(uint16_t));
+  h->ofpt = take(M * d * sizeof(int16_t));
+  h->oorder = take(M * sizeof(int32_t));
+  h->ometa = take(h->sf_ok ? h->sf.meta.size() : 0);
+  h->obmap = take(h->sf_ok ? h->sf.bmap.size() * sizeof(int32_t) : 0);
+  h->off = off;
+  const size_t oh = h->ohost;
+  auto& st = h->staging;
+  st.assign(off - oh, 0);
+  std::memcpy(st.data() + (h->onact - oh), nact.data(), M);
+  std::memcpy(st.data() + (h->oops - oh), ops.data(), M * kMaxDim * sizeof(uint16_t));
+  if (h->tcoff_ok) {
+    std::vector<uint16_t> tco(M * kMaxDim);
+    for (size_t x = 0; x < tco.size(); ++x) tco[x] = static_cast<uint16_t>(ops[x] * 128u);
+    std::memcpy(st.data() + (h->otcoff - oh), tco.data(), M * kMaxDim * sizeof(uint16_t));
+  }
+  std::memcpy(st.data() + (h->ofid - oh), fid.data(), M * d * sizeof(uint16_t));
+  std::memcpy(st.data() + (h->ofpt - oh), fpt.data(), M * d * sizeof(int16_t));
+  std::memcpy(st.data() + (h->oorder - oh), order.data(), M * sizeof(int32_t));
+  if (h->sf_ok) {
+    std::memcpy(st.data() + (h->ometa - oh), h->sf.meta.data(), h->sf.meta.size());
+    std::memcpy(st.data() + (h->obmap - oh), h->sf.bmap.data(), h->sf.bmap.size() * sizeof(int32_t));
+    h->sf.bfloats_ = h->sf.bmap.size();
+    h->sf.meta_bytes_ = h->sf.meta.size();
+    h->sf.meta.clear();
+    h->sf.meta.shrink_to_fit();
+    h->sf.bmap.clear();
+    h->sf.bmap.shrink_to_fit();
+  }
+  return h;
+}
+
+std::shared_ptr<const SurplusHost> surplus_host(const sg_grid* g, int k) {
+  static std::mutex mu;
+  static std::vector<std::shared_ptr<const SurplusHost>> cache;   // most recent last
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& c : cache)
+      if (c->d == g->d && c->L == g->level && c->k == k && c->M == g->M && c->lev == g->h_lev && c->kidx == g->h_kidx)
+        return c;
+  }
+  auto h = make_surplus_host(g, k);
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache.size() >= 8) cache.erase(cache.begin());
+  cache.push_back(h);
+  return h;
+}
+}  // namespace
+}  // namespace sg
+
+extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int k, sg_surplus** out,
+                                  void* stream) {
+  clear_error();
+  if (!g || !d_values || !out) return fail(SG_EINVAL, "sg_build_surpluses: null pointer");
+  *out = nullptr;
+  if (k < 1 || k > kMaxOut) return fail(SG_EINVAL, "sg_build_surpluses: k must be 1..16");
+  if (g->level > kMaxLevel) return fail(SG_EUNSUPPORTED, "sg_build_surpluses: level above 8");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int d = g->d, L = g->level, fine_n = 1 << L;
+  const int64_t M = g->M;
+  std::shared_ptr<const SurplusHost> hp;
+  try {
+    hp = surplus_host(g, k);
+  } catch (const std::bad_alloc&) {
+    return fail(SG_ENOMEM, "sg_build_surpluses: host memory");
+  }
+  const SurplusHost& h = *hp;
+  auto* s = new sg_surplus();
+  s->d = d;
+  s->level = L;
+  s->k = k;
+  s->M = M;
+  s->nf = h.nf;
+  s->amax = h.amax;
+  for (int a = 0; a <= kMaxDim + 1; ++a) s->grp[a] = h.grp[a];
+  cudaError_t e = block_alloc(&s->block, h.off, st);
   if (e != cudaSuccess) {
     delete s;
-    return e == cudaErrorMemoryAllocation ? fail(SG_ENOMEM, "sg_build_surpluses: cudaMalloc") : cuda_fail(e, "sg_build_surpluses: cudaMalloc");
+    return e == cudaErrorMemoryAllocation ? fail(SG_ENOMEM, "sg_build_surpluses: device allocation") : cuda_fail(e, "sg_build_surpluses: device allocation");
   }
   char* base = static_cast<char*>(s->block);
-  s->W = reinterpret_cast<double*>(base + oW);
-  s->Ws = reinterpret_cast<double*>(base + oWs);
-  s->Wdf = reinterpret_cast<float2*>(base + oWdf);
-  s->xf = reinterpret_cast<double*>(base + oxf);
-  s->xfdf = reinterpret_cast<float2*>(base + oxfdf);
-  s->bpack = npack ? reinterpret_cast<float*>(base + obp) : nullptr;
-  s->tc_err = reinterpret_cast<int*>(base + oerr);
-  s->box = reinterpret_cast<double*>(base + obox);
-  s->nact = reinterpret_cast<uint8_t*>(base + onact);
-  s->ops = reinterpret_cast<uint16_t*>(base + oops);
-  s->tcoff = tcoff_ok ? reinterpret_cast<uint16_t*>(base + otcoff) : nullptr;
-  auto* d_fid = reinterpret_cast<uint16_t*>(base + ofid);
-  auto* d_fpt = reinterpret_cast<int16_t*>(base + ofpt);
-  auto* d_tab1 = reinterpret_cast<double*>(base + otab1);
-  auto* d_order = reinterpret_cast<int32_t*>(base + oorder);
-  if (sf_ok) {
+  s->W = reinterpret_cast<double*>(base + h.oW);
+  s->Ws = reinterpret_cast<double*>(base + h.oWs);
+  s->Wdf = reinterpret_cast<float2*>(base + h.oWdf);
+  s->xf = reinterpret_cast<double*>(base + h.oxf);
+  s->xfdf = reinterpret_cast<float2*>(base + h.oxfdf);
+  s->bpack = h.npack ? reinterpret_cast<float*>(base + h.obp) : nullptr;
+  s->tc_err = reinterpret_cast<int*>(base + h.oerr);
+  s->box = reinterpret_cast<double*>(base + h.obox);
+  s->nact = reinterpret_cast<uint8_t*>(base + h.onact);
+  s->ops = reinterpret_cast<uint16_t*>(base + h.oops);
+  s->tcoff = h.tcoff_ok ? reinterpret_cast<uint16_t*>(base + h.otcoff) : nullptr;
+  auto* d_fid = reinterpret_cast<uint16_t*>(base + h.ofid);
+  auto* d_fpt = reinterpret_cast<int16_t*>(base + h.ofpt);
+  auto* d_tab1 = reinterpret_cast<double*>(base + h.otab1);
+  auto* d_order = reinterpret_cast<int32_t*>(base + h.oorder);
+  if (h.sf_ok) {
+    const SfPlan& sf = h.sf;
     s->sf_ok = 1;
     s->sf_side = sf.side;
     s->sf_nks = sf.nks;
@@ -377,15 +474,15 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
     s->sf_tmem = sf.tmem_cols;
     s->sf_bbytes = sf.bbytes;
     s->sf_smem = sf.smem;
-    s->sf_bfloats = sf.bmap.size();
-    s->sf_meta_bytes = sf.meta.size();
+    s->sf_bfloats = sf.bfloats_;
+    s->sf_meta_bytes = sf.meta_bytes_;
     s->sf_o_aops = sf.o_aops;
     s->sf_o_epi = sf.o_epi;
     s->sf_o_prog = sf.o_prog;
     s->sf_o_pstart = sf.o_pstart;
-    s->sf_meta = reinterpret_cast<unsigned char*>(base + ometa);
-    s->sf_bmap = reinterpret_cast<int32_t*>(base + obmap);
-    s->sf_b = reinterpret_cast<float*>(base + osfb);
+    s->sf_meta = reinterpret_cast<unsigned char*>(base + h.ometa);
+    s->sf_bmap = reinterpret_cast<int32_t*>(base + h.obmap);
+    s->sf_b = reinterpret_cast<float*>(base + h.osfb);
   }
   auto cleanup = [&](cudaError_t err, const char* what) {
     sg_surplus_free(s);
@@ -394,35 +491,21 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
 #define SG_TRY_CLEAN(expr)                                  \
   if ((e = (expr)) != cudaSuccess) return cleanup(e, #expr);
   {
-    std::vector<unsigned char> h(off - ohost);
-    std::vector<double> box(2 * d);
+    // the host-made tables (cached), then this grid's box over their zero
+    // bytes; copies from pageable memory are staged before the calls return
+    double box[2 * kMaxDim];
     for (int dim = 0; dim < d; ++dim) {
       box[dim] = g->h_lo[dim];
       box[d + dim] = g->h_hi[dim] - g->h_lo[dim];
     }
-    std::memcpy(h.data() + (obox - ohost), box.data(), 2 * d * sizeof(double));
-    std::memcpy(h.data() + (onact - ohost), nact.data(), M);
-    std::memcpy(h.data() + (oops - ohost), ops.data(), M * kMaxDim * sizeof(uint16_t));
-    if (tcoff_ok) {
-      std::vector<uint16_t> tco(M * kMaxDim);
-      for (size_t x = 0; x < tco.size(); ++x) tco[x] = static_cast<uint16_t>(ops[x] * 128u);
-      std::memcpy(h.data() + (otcoff - ohost), tco.data(), M * kMaxDim * sizeof(uint16_t));
-    }
-    std::memcpy(h.data() + (ofid - ohost), fid.data(), M * d * sizeof(uint16_t));
-    std::memcpy(h.data() + (ofpt - ohost), fpt.data(), M * d * sizeof(int16_t));
-    std::memcpy(h.data() + (oorder - ohost), order.data(), M * sizeof(int32_t));
-    if (sf_ok) {
-      std::memcpy(h.data() + (ometa - ohost), sf.meta.data(), sf.meta.size());
-      std::memcpy(h.data() + (obmap - ohost), sf.bmap.data(), sf.bmap.size() * sizeof(int32_t));
-    }
-    // (a copy from pageable memory is staged before the call returns)
-    SG_TRY_CLEAN(cudaMemcpyAsync(base + ohost, h.data(), off - ohost, cudaMemcpyHostToDevice, st));
+    SG_TRY_CLEAN(cudaMemcpyAsync(base + h.ohost, h.staging.data(), h.off - h.ohost, cudaMemcpyHostToDevice, st));
+    SG_TRY_CLEAN(cudaMemcpyAsync(base + h.obox, box, 2 * d * sizeof(double), cudaMemcpyHostToDevice, st));
   }
   SG_TIMED("k_fine_coords", st, (k_fine_coords<<<static_cast<unsigned>(ceil_div(fine_n + 1, 64)), 64, 0, st>>>(L, s->xf)));
   SG_TIMED("k_fine_table", st, (k_fine_table<<<static_cast<unsigned>(ceil_div(fine_n + 1, 64)), 64, 0, st>>>(L, s->xf, d_tab1)));
   SG_TRY_CLEAN(cudaGetLastError());
-  for (size_t lv = 0; lv + 1 < level_start.size(); ++lv) {
-    const int64_t n0 = level_start[lv], n1 = level_start[lv + 1];
+  for (size_t lv = 0; lv + 1 < h.level_start.size(); ++lv) {
+    const int64_t n0 = h.level_start[lv], n1 = h.level_start[lv + 1];
     auto* kern = k <= 4 ? k_surplus_level<4> : k_surplus_level<kMaxOut>;
     SG_TIMED("k_surplus_level", st,
              (kern<<<static_cast<unsigned>(ceil_div(n1 - n0, kSurpWarps)), 32 * kSurpWarps, 0, st>>>(
@@ -453,7 +536,7 @@ extern "C" int sg_surplus_info(const sg_surplus* s, int64_t* n_nodes, int* k, co
 
 extern "C" void sg_surplus_free(sg_surplus* s) {
   if (!s) return;
-  if (s->block) cudaFree(s->block);
+  block_free(s->block);
   delete s;
 }
 

@@ -51,6 +51,7 @@ struct SfPlan {
   std::vector<unsigned char> meta;   // sops | gops | aops | epi | prog | pstart (copied to shared memory)
   size_t o_gops = 0, o_aops = 0, o_epi = 0, o_prog = 0, o_pstart = 0;
   std::vector<int32_t> bmap;         // per float of the W pack: (W index << 2) | part, or -1
+  size_t bfloats_ = 0, meta_bytes_ = 0;   // their sizes, kept when the tables are moved to a staging copy
 };
 bool sf_plan(int d, int level, int nf, int k, int64_t M, const std::vector<uint16_t>& fid, SfPlan& p);
 }  // namespace sg
