@@ -230,7 +230,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
   int active = h_cnt[1];
   for (int it = 0; it < a.max_iter && active > 0; ++it) {
     SG_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), st));
-    SG_TIMED(kname<T>("k_point"), st, (k_point<T><<<gp, 128, 0, st>>>(a, w)));
+    if (!a.jac_in_trial) SG_TIMED(kname<T>("k_point"), st, (k_point<T><<<gp, 128, 0, st>>>(a, w)));   // else stored by the last trial
     if constexpr (sizeof(T) == sizeof(float)) {
       const int cw = condense_reg_warps(a.cond_warps);
       SG_TIMED("k_condense_reg_fp32", st,
@@ -367,7 +367,7 @@ static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, dou
 
   GraphBuilder nb{newton_body, {}};
   nb.memset0(w.counters, 2 * sizeof(int));
-  nb.kernel(k_point<T>, gp, 128, 0, a, w);
+  if (!a.jac_in_trial) nb.kernel(k_point<T>, gp, 128, 0, a, w);   // else stored by the last trial
   if constexpr (sizeof(T) == sizeof(float)) {
     const int cw = condense_reg_warps(a.cond_warps);
     nb.kernel(condense_reg_kernel(cw), static_cast<unsigned>(ceil_div(nint, cw)), 32 * cw, 0, a, w);
@@ -724,6 +724,9 @@ extern "C" int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t
   a.sync_at_end = 1;
   a.Yin = o.warm_start ? d_Y : nullptr;
   a.res_pair = o.precision == SG_PREC_MIXED_PAIR ? 1 : 0;
+  // the FP32 Jacobian from the FP64 residual kernel (its FP32 pipe is idle
+  // beside the FP64 work) in the launch-per-phase and graph forms
+  a.jac_in_trial = fp32_direction(o.precision) && !a.res_pair && !o.persistent ? 1 : 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (o.graph == 2 && !d_Y) {
     bool ran = false;

@@ -2,7 +2,10 @@
 // four-stage Lobatto IIIA collocation on N equal intervals, damped Newton.
 //
 // One Newton iteration:
-//   k_point     Jacobian dF/dy (precision T) at every collocation point
+//   k_point     Jacobian dF/dy (precision T) at every collocation point (in
+//               the mixed form with the FP64 residual, k_trial stores it
+//               instead: the last trial of a line search is the next
+//               iterate)
 //   k_condense  the 36 linearised stage equations of one interval; Gaussian
 //               elimination of the two interior stages (24 columns, partial
 //               pivoting over the 24 interior rows) leaves the 12 x 25 block
@@ -101,6 +104,7 @@ struct SolveArgs {
   int sync_at_end;
   const double* Yin;   // initial iterate (n x P x 12), or null for the zero-control guess
   int res_pair;        // FP32-direction form: 1 = residual in pairs of floats, 0 = in FP64
+  int jac_in_trial;    // FP32-direction form with the FP64 residual: the residual kernel also stores the Jacobian
 };
 
 __host__ __device__ __forceinline__ int64_t npts(int Nmax) { return 3 * int64_t(Nmax) + 1; }
@@ -184,14 +188,34 @@ __device__ __forceinline__ T narrow_row(double x) {
   }
 }
 
-template <typename T, bool kPair>
+// Round to the nearest FP32 value from the bit pattern (integer pipe), the
+// same value as the conversion instruction, which runs on the FP64 pipe.
+__device__ __forceinline__ float f32_rn_bits(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  if (e < 897u || e > 1150u) return __double2float_rn(x);   // zero, subnormal, huge, non-finite
+  const unsigned sign = hi & 0x80000000u;
+  unsigned f = (((hi & 0x7FFFFFFFu) - 0x38000000u) << 3) | (lo >> 29);   // exponent and 23 bits
+  const unsigned rest = lo & 0x1FFFFFFFu;
+  if (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ++f;   // ties to even; a carry bumps the exponent
+  return __uint_as_float(sign | f);
+}
+
+constexpr int kTrialJLd = 40;   // staged rows of one point in the fused Jacobian: three rows (36) + 4
+
+template <typename T, bool kPair, bool kJac>
 __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
   // kPair = false: points and rows in FP64 (the FP64 and mixed forms).
   // kPair = true (the mixed-pair form): the right-hand side and the stage rows
   // in pair-of-floats arithmetic (about 48 bits, on the FP32 pipe); the
   // boundary rows and the iterate Y + alpha D stay FP64.
-  __shared__ double ys[kTrialPts][12];   // dfnum in the mixed-pair form (same size)
-  __shared__ double fs[kTrialPts][12];
+  // kJac (mixed form): the FP32 Jacobian at the trial point as well, on the
+  // FP32 pipe beside the FP64 residual; the last trial of a line search is
+  // the accepted iterate, so its Jacobian is the next iteration's.
+  __shared__ __align__(16) double yfs[2][kTrialPts][12];   // points and F (dfnum in the mixed-pair form)
+  auto& ys = yfs[0];
+  auto& fs = yfs[1];
   __shared__ double part_s[3 * kTrialIv][2];
   __shared__ double cA_s[3][4];          // h a_kj: a pair (pair residual) or FP64, k = 1..3
   const int tid = threadIdx.x;
@@ -206,6 +230,9 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
   const int niv = N - i0 < kTrialIv ? N - i0 : kTrialIv;
   const double alpha = s.alpha;
   const int64_t base = node * npts(a.Nmax) + 3 * int64_t(i0);
+  float yf[12];   // kJac: the point rounded to FP32
+#pragma unroll
+  for (int c = 0; c < 12; ++c) yf[c] = 0.0f;
   auto ypoint = [&](int64_t pt, int c) { return __fma_rn(alpha, w.D[pt * 12 + c], w.Y[pt * 12 + c]); };
   // the stage coefficients h a_kj once per block (the last 12 threads)
   if (tid >= 128 - 12) {
@@ -239,6 +266,10 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
       for (int c = 0; c < 12; ++c) {
         ys[tid][c] = y[c];
         fs[tid][c] = F[c];
+      }
+      if constexpr (kJac) {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) yf[c] = f32_rn_bits(y[c]);
       }
     }
   }
@@ -328,14 +359,51 @@ __global__ void __launch_bounds__(128) k_trial(SolveArgs a, Workspace w) {
     w.part[2 * t] = ss;
     w.part[2 * t + 1] = mx;
   }
+  if constexpr (kJac) {
+    // The Jacobian of this thread's point.  The points of a warp are
+    // consecutive in Jm; rows are staged three at a time in the point tables
+    // (free now) and the warp writes them as contiguous 144-byte runs.
+    const int lane = tid & 31, warp = tid >> 5;
+    const bool valid = tid <= 3 * niv;
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    if (vmask != 0u) {
+      float* stage = reinterpret_cast<float*>(&yfs[0][0][0]) + warp * 32 * kTrialJLd;
+      float* mine = stage + lane * kTrialJLd;
+      float* Jw = static_cast<float*>(w.Jm) + (base + 32 * warp) * 144;
+      char_jacobian_rows<float>(
+          a.P, yf,
+          [&](int r, const float (&row)[12]) {
+            float4* dst = reinterpret_cast<float4*>(mine + 12 * (r % 3));
+#pragma unroll
+            for (int q4 = 0; q4 < 3; ++q4)
+              dst[q4] = make_float4(row[4 * q4], row[4 * q4 + 1], row[4 * q4 + 2], row[4 * q4 + 3]);
+            if (r % 3 == 2) {
+              __syncwarp();
+              const int h = r / 3;
+              for (int e = lane; e < 32 * 9; e += 32) {
+                const int pt = e / 9, q = e % 9;
+                if ((vmask >> pt) & 1u)
+                  reinterpret_cast<float4*>(Jw + pt * 144 + 36 * h)[q] =
+                      reinterpret_cast<const float4*>(stage + pt * kTrialJLd)[q];
+              }
+              __syncwarp();
+            }
+          },
+          nullptr);
+    }
+  }
 }
 
 // The residual kernel of a solve: FP64, or pairs of floats in the
 // FP32-direction form when asked for.
 template <typename T>
 inline void (*trial_kernel(const SolveArgs& a))(SolveArgs, Workspace) {
-  if constexpr (sizeof(T) == sizeof(float)) return a.res_pair ? k_trial<float, true> : k_trial<float, false>;
-  else return k_trial<double, false>;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (a.res_pair) return k_trial<float, true, false>;
+    return a.jac_in_trial ? k_trial<float, false, true> : k_trial<float, false, false>;
+  } else {
+    return k_trial<double, false, false>;
+  }
 }
 
 // Warp per node: reduce the partial norms in a fixed order and decide.

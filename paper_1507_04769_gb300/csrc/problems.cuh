@@ -390,12 +390,13 @@ __device__ __forceinline__ const double* node_target(const DevProblem& P, int64_
 }
 
 // Jacobian dF/dy (12 x 12) in precision T, from one dual pass over the six
-// state directions.  Row r goes to put_row(r, row[12]), in the order r = 0..11
-// (every thread of a warp makes the same calls, so the sink may work across
-// the warp).  If Fout is non-null and T is double, the FP64 right-hand side
-// from the value parts is written there as well.
-template <typename T, typename Sink>
-__device__ __forceinline__ void char_jacobian_rows(const DevProblem& P, const double* y, Sink&& put_row,
+// state directions, at y of type Y (double, or float already rounded).  Row r
+// goes to put_row(r, row[12]), in the order r = 0..11 (every thread of a warp
+// makes the same calls, so the sink may work across the warp).  If Fout is
+// non-null and y is double, the FP64 right-hand side from the value parts is
+// written there as well.
+template <typename T, typename Y, typename Sink>
+__device__ __forceinline__ void char_jacobian_rows(const DevProblem& P, const Y* y, Sink&& put_row,
                                                    double* Fout) {
   if (P.kind == SG_PROBLEM_EXAMPLE3) {
     using D = Dual<T, 6>;
@@ -424,7 +425,9 @@ __device__ __forceinline__ void char_jacobian_rows(const DevProblem& P, const do
       }
       put_row(r, row);
     }
-    if (Fout) char_rhs(P, y, Fout);
+    if constexpr (sizeof(Y) == sizeof(double)) {
+      if (Fout) char_rhs(P, y, Fout);
+    }
     return;
   }
   if (P.kind == SG_PROBLEM_ATTITUDE) {
@@ -458,7 +461,7 @@ __device__ __forceinline__ void char_jacobian_rows(const DevProblem& P, const do
       }
       put_row(r, row);
     }
-    if (Fout) {
+    if (sizeof(Y) == sizeof(double) && Fout) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) Fout[i] = double(f0[i].v);
 #pragma unroll
@@ -486,7 +489,9 @@ __device__ __forceinline__ void char_jacobian_rows(const DevProblem& P, const do
       }
       put_row(r, row);
     }
-    if (Fout) char_rhs(P, y, Fout);
+    if constexpr (sizeof(Y) == sizeof(double)) {
+      if (Fout) char_rhs(P, y, Fout);
+    }
   }
 }
 
