@@ -181,6 +181,9 @@ int sg_build_grid(int d, int level, const double* h_lo, const double* h_hi, sg_g
  * coordinate in X^{i_k} (0-based).  Any output pointer may be NULL. */
 int sg_grid_info(const sg_grid* g, int64_t* n_nodes, int* d, int* level,
                  const double** d_coords, const int8_t** d_levels, const int16_t** d_index);
+/* Frees a grid handle (NULL is a no-op).  Synchronises the device first, as
+ * cudaFree does; the device block returns to the library's stream-ordered
+ * pool (up to 1 GiB of freed blocks per device is kept for reuse). */
 void sg_grid_free(sg_grid* g);
 
 /* Bytes of solver workspace for n nodes of at most n_max_intervals intervals
@@ -363,12 +366,17 @@ int sg_attitude_targets(const sg_problem* prob, const double* d_x0, int64_t n, d
  *   d_values  M x k doubles (row n = node n of the grid), 1 <= k <= 16
  *   out       new handle owning W (M x k FP64) and the evaluation tables;
  *             it keeps no reference to d_values or to g after the call returns
+ * The host-made tables (the nodes' integer structure, the evaluation plans)
+ * depend only on the grid's node structure and k; the library keeps them for
+ * the last 8 (d, level, k) it saw and reuses them for grids with the same
+ * levels and indices (a grid rebuilt every step).
  * Synchronises `stream` before returning.  Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA. */
 typedef struct sg_surplus sg_surplus;
 int sg_build_surpluses(const sg_grid* g, const double* d_values, int k,
                        sg_surplus** out, void* stream);
 /* Borrowed view of the surpluses: d_W is M x k doubles. */
 int sg_surplus_info(const sg_surplus* s, int64_t* n_nodes, int* k, const double** d_W);
+/* Frees a surplus handle (NULL is a no-op); the same rules as sg_grid_free. */
 void sg_surplus_free(sg_surplus* s);
 
 /* ---------------------------------------------------------------- on-line

@@ -425,6 +425,28 @@ def test_tf32x3_kernel_for_the_shape(d, L, k, kernel):
     assert ((out["u"] - ref).abs().max() / ref.abs().max()).item() <= 1e-5
 
 
+def test_surplus_tables_reused_across_grids():
+    """Surplus builds on grids of the same structure reuse the host-made tables
+    (cached per d, L, k): grids on different boxes, a different k and a
+    different level in between all give the oracle's surpluses and values."""
+    rng = np.random.default_rng(21)
+    for d, L, k, half in [(4, 3, 2, 1.0), (4, 3, 2, 0.3), (4, 3, 3, 0.3), (4, 2, 2, 0.3), (4, 3, 2, 2.0)]:
+        lo, hi = -half * np.ones(d), half * np.ones(d)
+        lo[0] -= 0.5
+        g = sg.Grid(d, L, lo, hi)
+        og = ogrid.Grid(d, L, lo, hi)
+        f = rng.standard_normal((og.M, k))
+        S = sg.Surplus(g, cuda(f))
+        w = ointerp.surpluses(og, f)
+        xq = synth.uniform_queries(200, lo, hi, seed=22)
+        ref = ointerp.eval_surplus(og, w, xq)
+        for mode in (sg.EVAL_FP64, sg.EVAL_DF32):
+            u = sg.eval_feedback(S, cuda(xq), mode=mode).cpu().numpy()
+            assert rel(u, ref) <= 1e-10, (d, L, k, half, mode)
+        u = sg.eval_feedback(S, cuda(xq), mode=sg.EVAL_TF32X3).cpu().numpy()
+        assert np.max(np.abs(u - ref) / _tf32x3_bound(og, w, xq)) <= 1.0, (d, L, k, half)
+
+
 def test_tf32x3_at_nodes_edges_and_outside():
     """Queries on grid nodes (up to the last bit), next to them, on the box
     faces and outside the box: finite and within the stated bound."""
