@@ -13,34 +13,43 @@
 // a prefix whose length depends on the level sum of a only.  With the a's
 // grouped by that prefix, each group's G is one dense product
 //     G_g = Psi[:, 0:K_g] x W_g     (queries x K_g, K_g x (a, c)),
-// a GEMM for the tensor cores whose operand A (Psi, one row per query) is
-// built once per query: 177 products per query instead of 1457 on the
-// level-4 grid in d = 6.  The a's paired with the constant tuple b0 only (the
-// finest first-part levels) are taken the other way round: their Phi_a form
-// the operand A of one more product with the rows w_{(a,b0)}, whose result
-// enters u with the factor 1 (the "direct" group).
+// a GEMM whose operand A (Psi, one row per query) is built once per query:
+// 177 products per query instead of 1457 on the level-4 grid in d = 6.
 //
-// The host builds the plan once per surplus (sf_plan): the operand-A
-// columns (the b's, then the direct a's) as table offsets, the W tiles of
-// every group and K-step in the tensor cores' K-major core-matrix layout,
-// the products of every K-step, and the 16-column chunks of the epilogue.
+// Which products go where.  A K-step (8 columns of Psi) that several groups
+// share is one wide tensor-core product (the groups' accumulator columns
+// are consecutive, so N = 256, 112, 48 at level 4).  The K-steps that only
+// the constant tuple a0 uses, and the a's paired with the constant tuple b0
+// only (the finest first-part levels), are sums over single nodes with k
+// outputs: a tf32 MMA costs about as much for N = 16 as for N = 64, so these
+// columns run on the CUDA cores (FP32 products times FP32 surpluses, summed
+// eight at a time and then compensated).
+//
+// The host builds the plan once per grid structure (sf_plan): the operand-A
+// columns as table offsets, the CUDA-core columns by factor count, the W
+// tiles of every K-step's product in the tensor cores' K-major core-matrix
+// layout followed by the CUDA-core columns' FP32 rows, the products of every
+// K-step, and the 16-column chunks of the epilogue.
 //
 // The kernel: one persistent CTA per SM over tiles of 128 queries,
 // warp-specialised.
 //   warps 0..11  producers, three per query row (part p = tid / 128):
 //                each computes the 1-D tables of dimensions p, p + 3, ...
-//                (pair-of-floats, rounded once to FP32), then, per ring
-//                stage of three K-steps, the K-step p of the row's operand A
-//                split into TF32 hi and lo parts, and arrives on the stage's
-//                "full" mbarrier; after the last product, the epilogue: each
-//                part reads a third of the accumulator chunks from tensor
-//                memory and forms sum_a Phi_a G_{a,c};
-//   warp 12      lane 0 issues, per K-step and group, the three products
-//                A_hi W_hi, A_hi W_lo, A_lo W_hi (M = 128, kind::tf32) and
-//                commits each stage to its "empty" mbarrier, and the whole
+//                (compensated FP32 inside the box, pairs of floats outside),
+//                then, per ring stage of three K-steps, the K-step p of the
+//                row's operand A split into TF32 hi and lo parts, arriving on
+//                the stage's "full" mbarrier; then a third of the CUDA-core
+//                columns while the products run; then the epilogue: a third
+//                of the accumulator chunks read from tensor memory and
+//                sum_a Phi_a G_{a,c} formed;
+//   warp 12      lane 0 issues, per K-step, the three products
+//                A_hi W_hi, A_hi W_lo, A_lo W_hi (M = 128, kind::tf32),
+//                commits each stage to its "empty" mbarrier and the whole
 //                tile to "done".
-// Every mbarrier wait is bounded; a timeout sets an error flag, the CTA stops
-// and writes NaN for its remaining queries.
+// The next tile's coordinates are loaded and converted while a tile computes;
+// there is no FP64 arithmetic on the path but the output.  Every mbarrier
+// wait is bounded; a timeout sets an error flag, the CTA stops and writes NaN
+// for its remaining queries.
 #include <algorithm>
 #include <array>
 #include <cstring>
@@ -357,7 +366,7 @@ struct SfArgs {
   const double* lo;
   const double* width;
   const float2* xfdf;
-  const unsigned char* meta;   // sops | aops | epi | prog | pstart
+  const unsigned char* meta;   // sops | gops | aops | epi | prog | pstart
   const float* bpack;
   double* out;
   int* err;
@@ -527,9 +536,6 @@ __device__ __forceinline__ void sf_produce(const uint2* __restrict__ ops, const 
   }
 }
 
-// Epilogue of one 16-column accumulator chunk whose first column has index
-// c0 within its group ([a][c] order, K = k columns per a, c0 % K = P):
-// uf[c] += Phi_a G_{a,c} over the chunk's columns.
 // Waits for this thread's tensor-memory loads; r is an operand, so no use of
 // the loaded registers moves above the wait.
 __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[16]) {
@@ -540,6 +546,9 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[16]) {
                : "memory");
 }
 
+// Epilogue of one 16-column accumulator chunk whose first column has index
+// c0 within its group ([a][c] order, K = k columns per a, c0 % K = P):
+// uf[c] += Phi_a G_{a,c} over the chunk's columns.
 // (the chunk's tensor-memory load is in flight on entry: the a-tuple
 // products are formed before waiting for it)
 template <int K, int P, int S>
