@@ -28,6 +28,7 @@ static Workspace carve(void* base, int64_t n, int Nmax, size_t tsize) {
   };
   w.Y = reinterpret_cast<double*>(take(n * P * 12 * sizeof(double)));
   w.D = reinterpret_cast<double*>(take(n * P * 12 * sizeof(double)));
+  w.Y2 = tsize == sizeof(float) ? reinterpret_cast<double*>(take(n * P * 12 * sizeof(double))) : nullptr;
   w.Jm = take(n * P * 144 * tsize);
   w.Res = take(n * int64_t(Nmax) * kResRows * tsize);
   w.Cond = take(n * int64_t(Nmax) * kBlk * tsize);
@@ -255,7 +256,7 @@ static int run_solve(const SolveArgs& a, Workspace w, cudaStream_t st, double* l
       if (h_cnt[0] == 0) break;
     }
     SG_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), st));
-    SG_TIMED("k_update", st, (k_update<<<gupd, 128, 0, st>>>(a, w)));
+    if (!a.jac_in_trial) SG_TIMED("k_update", st, (k_update<<<gupd, 128, 0, st>>>(a, w)));   // else the accepted trial point
     SG_TIMED("k_after_update", st, (k_after_update<<<gnode_thr, 128, 0, st>>>(a, w)));
     SG_LAUNCH_CHECK("update kernels");
     if ((rc = read_counters()) != SG_OK) return rc;
@@ -384,7 +385,8 @@ static cudaError_t build_solve_graph(const SolveArgs& a, const Workspace& w, dou
   cudaGraph_t ls_body;
   nb.loop(hl, &ls_body);
   nb.memset0(w.counters, 2 * sizeof(int));
-  nb.kernel(k_update, static_cast<unsigned>(ceil_div(a.n * npts(a.Nmax) * kUpdPer, 128)), 128, 0, a, w);
+  if (!a.jac_in_trial)   // else the accepted trial point is the iterate
+    nb.kernel(k_update, static_cast<unsigned>(ceil_div(a.n * npts(a.Nmax) * kUpdPer, 128)), 128, 0, a, w);
   nb.kernel(k_after_update, gnt, 128, 0, a, w);
   nb.kernel(k_set_cond, 1, 1, 0, hn, static_cast<const int*>(w.counters + 1));
   if (nb.err != cudaSuccess) return nb.err;

@@ -56,7 +56,7 @@ struct NodeState {
   int singular;    // a zero pivot was met this iteration
   int iters;
   int status;
-  int _pad;
+  int ybuf;        // 1: the current iterate is in Y2 (see Workspace)
 };
 
 constexpr int kCols = 49;        // 24 interior + 12 (y_i) + 12 (y_{i+1}) + rhs
@@ -75,6 +75,9 @@ __host__ __device__ __forceinline__ int seg_count(int N) { return (N + kSegLen -
 struct Workspace {
   double* Y;       // n x P x 12, current iterate
   double* D;       // n x P x 12, Newton direction
+  double* Y2;      // n x P x 12 (FP32-direction forms): with the Jacobian from the residual
+                   // kernel, each trial point goes here (or to Y), and an accepted step only
+                   // flips the node's ybuf: no update pass
   void* Jm;        // n x P x 144 (T), Jacobians
   void* Res;       // n x Nmax x 36 (T), stage residuals at the iterate
   void* Cond;      // n x Nmax x kBlk (T), condensed block rows
@@ -235,7 +238,8 @@ __global__ void __launch_bounds__(128, kJac ? 5 : 1) k_trial(SolveArgs a, Worksp
   float yf[12];   // kJac: the point rounded to FP32
 #pragma unroll
   for (int c = 0; c < 12; ++c) yf[c] = 0.0f;
-  auto ypoint = [&](int64_t pt, int c) { return __fma_rn(alpha, w.D[pt * 12 + c], w.Y[pt * 12 + c]); };
+  const double* Ycur = s.ybuf ? w.Y2 : w.Y;
+  auto ypoint = [&](int64_t pt, int c) { return __fma_rn(alpha, w.D[pt * 12 + c], Ycur[pt * 12 + c]); };
   // the stage coefficients h a_kj once per block (the last 12 threads)
   if (tid >= 128 - 12) {
     const int e = tid - (128 - 12), k = e / 4 + 1, jj = e % 4;
@@ -272,6 +276,11 @@ __global__ void __launch_bounds__(128, kJac ? 5 : 1) k_trial(SolveArgs a, Worksp
       if constexpr (kJac) {
 #pragma unroll
         for (int c = 0; c < 12; ++c) yf[c] = f32_rn_bits(y[c]);
+        // the trial point to the other iterate buffer: if the step is
+        // accepted it becomes the iterate (the same fma as an update pass)
+        double2* alt = reinterpret_cast<double2*>((s.ybuf ? w.Y : w.Y2) + (base + tid) * 12);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) alt[c] = make_double2(y[2 * c], y[2 * c + 1]);
       }
     }
   }
@@ -447,6 +456,7 @@ __global__ void k_ls_reduce(SolveArgs a, Workspace w, int mode) {
       s.fnorm2 = ss;
       s.fmax = mx;
       s.searching = 0;
+      if (a.jac_in_trial) s.ybuf ^= 1;   // the trial point is the iterate
     } else {
       s.alpha *= 0.5;
       atomicAdd(&w.counters[0], 1);
@@ -952,7 +962,7 @@ __device__ __forceinline__ bool abd_staircase(const SolveArgs& a, const Workspac
                                               const T* __restrict__ cond, int nblk, int pt_stride,
                                               T* __restrict__ abd, int lane) {
   const int64_t pb = node * npts(a.Nmax);
-  const double* Y = w.Y + pb * 12;
+  const double* Y = (w.ns[node].ybuf ? w.Y2 : w.Y) + pb * 12;
   const double* x0 = a.x0 + node * 6;
   double* D = w.D + pb * 12;
   const bool rowlane = lane < 18;
@@ -1584,7 +1594,7 @@ __device__ __forceinline__ void node_outputs(const SolveArgs& a, const Workspace
                                              int lane, double* lambda0, double* u0, double* V, int32_t* status,
                                              int32_t* iters) {
   const NodeState s = w.ns[node];
-  const double* Y = w.Y + node * npts(a.Nmax) * 12;
+  const double* Y = (s.ybuf ? w.Y2 : w.Y) + node * npts(a.Nmax) * 12;
   if (s.status == SG_BADINPUT) {
     if (lane == 0) {
       for (int c = 0; c < 6; ++c) lambda0[row * 6 + c] = NAN;
@@ -1631,8 +1641,9 @@ __global__ void k_copy_Y(SolveArgs a, Workspace w, double* out) {
   if (t >= a.n * P) return;
   const int64_t node = t / P;
   if (t % P > 3 * int64_t(a.N[node])) return;
+  const double* Yb = w.ns[node].ybuf ? w.Y2 : w.Y;
 #pragma unroll
-  for (int c = 0; c < 12; ++c) out[t * 12 + c] = w.Y[t * 12 + c];
+  for (int c = 0; c < 12; ++c) out[t * 12 + c] = Yb[t * 12 + c];
 }
 
 }  // namespace sg
