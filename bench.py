@@ -375,7 +375,7 @@ def gpu_arm(args):
                "status": torch.empty((n_loc,), dtype=torch.int32, device=dev),
                "iters": torch.empty((n_loc,), dtype=torch.int32, device=dev)}
 
-    def step(events=None):
+    def step(events=None, queries_ready=None):
         if events:
             events[0].record(stream)
         g = sg.Grid(D, LEVEL, lo, hi)
@@ -389,6 +389,8 @@ def gpu_arm(args):
         S = sg.Surplus(g, res["u0"])
         if events:
             events[3].record(stream)
+        if queries_ready is not None:
+            stream.wait_event(queries_ready)
         sg.eval_feedback(S, xq_d, mode=eval_mode, out=u_out)
         if events:
             events[4].record(stream)
@@ -472,11 +474,19 @@ def gpu_arm(args):
                 for k, shp, dt in (("lambda0", (6,), torch.float64), ("u0", (3,), torch.float64),
                                    ("V", (), torch.float64), ("status", (), torch.int32))}
 
+    # the queries are uploaded on a second stream while the grid, the solves and
+    # the surpluses run; the evaluation waits for them
+    up_stream = torch.cuda.Stream(device=dev)
+    xq_ready = torch.cuda.Event()
+
     def e2e_step():
         T_d.copy_(T_pin, non_blocking=True)
         N_d.copy_(N_pin, non_blocking=True)
-        xq_d.copy_(xq_pin, non_blocking=True)
-        r = step()
+        up_stream.wait_stream(stream)   # the previous step's evaluation has read xq_d
+        with torch.cuda.stream(up_stream):
+            xq_d.copy_(xq_pin, non_blocking=True)
+            xq_ready.record(up_stream)
+        r = step(queries_ready=xq_ready)
         u_pin.copy_(u_out, non_blocking=True)
         for k in node_pin:
             node_pin[k].copy_(r[k], non_blocking=True)

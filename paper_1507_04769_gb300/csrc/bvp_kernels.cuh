@@ -210,7 +210,7 @@ constexpr int kTrialJLd = 40;   // staged rows of one point in the fused Jacobia
 // (kJac: five blocks per SM, 96 registers with a few spilled dual values,
 // against 126 registers and four blocks; 2 % faster)
 template <typename T, bool kPair, bool kJac>
-__global__ void __launch_bounds__(128, kJac ? 5 : 1) k_trial(SolveArgs a, Workspace w) {
+__global__ void __launch_bounds__(128, 5) k_trial(SolveArgs a, Workspace w) {
   // kPair = false: points and rows in FP64 (the FP64 and mixed forms).
   // kPair = true (the mixed-pair form): the right-hand side and the stage rows
   // in pair-of-floats arithmetic (about 48 bits, on the FP32 pipe); the
