@@ -583,6 +583,23 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
 
+// 1/pivot in the eliminations.  FP32: the approximate reciprocal instruction
+// (rcp.approx.ftz, within about one unit in the last place; a subnormal pivot
+// flushes to zero): the FP32 eliminations only give a Newton direction whose
+// residual is evaluated in FP64, so the last bit of 1/pivot carries no
+// weight.  FP64: correctly rounded.  `good` is false for a zero, subnormal
+// (FP32) or non-finite pivot, whose reciprocal is then 0.
+__device__ __forceinline__ float pivot_recip(float p, bool& good) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
+  good = fabsf(r) < INFINITY && r != 0.0f;
+  return good ? r : 0.0f;
+}
+__device__ __forceinline__ double pivot_recip(double p, bool& good) {
+  good = p != 0.0 && isfinite(p);
+  return good ? __drcp_rn(p) : 0.0;
+}
+
 // 40-entry rows (F | Y | Z | rhs and padding) loaded as 16-byte vectors.
 template <typename T>
 __device__ __forceinline__ void load_row40(const T* __restrict__ src, T (&r)[40]) {
@@ -614,9 +631,9 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
     const int p = warp_pivot_lane<T>(r[k], cand && !done, lane);
     plane[k] = p;
     const T piv = __shfl_sync(0xffffffffu, r[k], p);
-    const bool good = piv != T(0) && isfinite(piv);
+    bool good;
+    const T inv = pivot_recip(piv, good);
     ok = ok && good;
-    const T inv = good ? recip_rn(piv) : T(0);
     const bool is_p = lane == p;
     const T l = (cand && !done && !is_p) ? r[k] * inv : T(0);
 #pragma unroll
@@ -755,12 +772,12 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     }
     __syncwarp();
     const float4* src = reinterpret_cast<const float4*>(U_s + (k & 7) * kCondLd);
-    // every lane forms 1/pivot from the published row (the same correctly
-    // rounded reciprocal; zero for a zero or non-finite pivot)
-    const float pv = U_s[(k & 7) * kCondLd + k];
-    const float inv = (pv != 0.0f && isfinite(pv)) ? __frcp_rn(pv) : 0.0f;
+    // every lane forms 1/pivot from the published row (the same value in
+    // every lane; zero for an unusable pivot)
+    bool good;
+    const float inv = pivot_recip(U_s[(k & 7) * kCondLd + k], good);
     if (lane == (k & 7)) inv_keep = inv;
-    bad = bad || inv == 0.0f;
+    bad = bad || !good;
     const float la = ra[k] * (inv * live);
 #pragma unroll
     for (int q = q0; q < 6; ++q) {
@@ -1288,12 +1305,11 @@ __global__ void __launch_bounds__(32 * seg_warps<T>()) k_abd_seg(SolveArgs a, Wo
       T inv = u[k];
       if constexpr (sizeof(T) == sizeof(float)) {
         // FP32: the row is published with its raw pivot and every lane forms
-        // the same correctly rounded 1/pivot (off the pivot lane's path);
-        // lane k keeps it for the diagonal of the stored row
-        const T piv = inv;
-        const bool good = piv != T(0) && isfinite(piv);
+        // the same 1/pivot (off the pivot lane's path); lane k keeps it for
+        // the diagonal of the stored row
+        bool good;
+        inv = pivot_recip(inv, good);
         bad = bad || !good;
-        inv = good ? recip_rn(piv) : T(0);
         if (lane == k) inv_keep = inv;
       }
       const T la = ktag != 0u ? ya[k] * inv : T(0);
