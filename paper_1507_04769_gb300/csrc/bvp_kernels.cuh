@@ -583,12 +583,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
 
-// 1/pivot in the eliminations.  FP32: the approximate reciprocal instruction
-// (rcp.approx.ftz, within about one unit in the last place; a subnormal pivot
-// flushes to zero): the FP32 eliminations only give a Newton direction whose
-// residual is evaluated in FP64, so the last bit of 1/pivot carries no
-// weight.  FP64: correctly rounded.  `good` is false for a zero, subnormal
-// (FP32) or non-finite pivot, whose reciprocal is then 0.
+// 1/pivot in the condensation and segment eliminations.  FP32: the
+// approximate reciprocal instruction (rcp.approx.ftz, within about one unit
+// in the last place; a subnormal pivot flushes to zero): the FP32
+// eliminations only give a Newton direction whose residual is evaluated in
+// FP64, so the last bit of 1/pivot carries no weight.  FP64: correctly
+// rounded.  `good` is false for a zero, subnormal (FP32) or non-finite pivot,
+// whose reciprocal is then 0.
 __device__ __forceinline__ float pivot_recip(float p, bool& good) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
@@ -631,9 +632,11 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
     const int p = warp_pivot_lane<T>(r[k], cand && !done, lane);
     plane[k] = p;
     const T piv = __shfl_sync(0xffffffffu, r[k], p);
-    bool good;
-    const T inv = pivot_recip(piv, good);
+    // (the correctly rounded reciprocal: on this serial chain the approximate
+    // instruction measured 19 % slower)
+    const bool good = piv != T(0) && isfinite(piv);
     ok = ok && good;
+    const T inv = good ? recip_rn(piv) : T(0);
     const bool is_p = lane == p;
     const T l = (cand && !done && !is_p) ? r[k] * inv : T(0);
 #pragma unroll
@@ -761,7 +764,7 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     const int q0 = k / 4;
     const unsigned key = ((__float_as_uint(ra[k]) << 1) & kmask) | ktag;
     const unsigned best = __reduce_max_sync(0xffffffffu, key);
-    if ((best & 31u) == itag && ktag != 0u) {
+    if (key == best) {   // candidates' keys are nonzero and differ in the tag; the others are 0
       float4* dst = reinterpret_cast<float4*>(U_s + (k & 7) * kCondLd);
 #pragma unroll
       for (int q = q0; q < 6; ++q) dst[q] = make_float4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
@@ -1288,7 +1291,7 @@ __global__ void __launch_bounds__(32 * seg_warps<T>()) k_abd_seg(SolveArgs a, Wo
       const int q0 = k / V;
       const unsigned key = (mag_key(ya[k]) & kmask) | ktag;
       const unsigned best = __reduce_max_sync(0xffffffffu, key);
-      if ((best & 31u) == itag && ktag != 0u) {
+      if (key == best) {   // candidates' keys are nonzero and differ in the tag; the others are 0
         if constexpr (sizeof(T) == sizeof(double)) {   // FP64: the pivot lane publishes 1/pivot
           const T piv = ya[k];
           const bool good = piv != T(0) && isfinite(piv);
