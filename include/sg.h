@@ -127,8 +127,8 @@ typedef struct sg_solve_opts {
                           1: batched persistent form: one warp per node runs the
                           whole Newton iteration, nodes taken from a device queue
                           (converged nodes retire and the warp takes the next);
-                          no host round trip, but the call still synchronises
-                          `stream` before returning                              */
+                          no host round trip; run as a graph (graph != 0) the
+                          call returns without waiting, as below                 */
   int32_t blocks_per_sm; /* persistent form: cap on resident 128-thread blocks per
                           SM (0 = as many as fit)                                 */
   int32_t graph;       /* 1: run the solve as a cached CUDA graph.  In the launch-
@@ -147,7 +147,10 @@ typedef struct sg_solve_opts {
                           d_work cannot hold the sub-batches' layouts (it can
                           whenever some N is below n_max_intervals, by a wide
                           margin).  Results are bitwise those of graph = 1 with
-                          the same n_max_intervals                               */
+                          the same n_max_intervals.
+                          With graph != 0 the call returns once the work is
+                          queued: the results are ready in `stream` order (read
+                          them on `stream`, or after synchronising it)            */
   int32_t warm_start;  /* 1: start Newton from the iterate in d_Y (which must then
                           be given) instead of the zero-control guess; d_Y
                           receives the final iterate as usual                    */
@@ -214,8 +217,10 @@ size_t sg_solve_workspace_bytes(int64_t n, int n_max_intervals, int precision);
  * The initial guess is lambda = 0 (zero control) with x held at x0, or with
  * opts->warm_start the iterate read from d_Y (for continuation: e.g. the
  * solution from a scaled initial state, Example III).
- * The call returns when every node has converged or hit max_iter (the host
- * reads one counter per iteration), so it synchronises `stream`.
+ * Without a graph (opts->graph == 0) the call returns when every node has
+ * converged or hit max_iter (the launch-per-phase form reads counters on the
+ * way, the persistent form waits at the end), so it synchronises `stream`;
+ * the graph forms return once the work is queued.
  * Errors: SG_EINVAL (sizes, workspace too small, misaligned), SG_ECUDA. */
 int sg_solve_bvps(const sg_problem* prob, const double* d_x0, int64_t n,
                   const double* d_T, const int32_t* d_N, int n_max_intervals,
@@ -370,7 +375,11 @@ int sg_attitude_targets(const sg_problem* prob, const double* d_x0, int64_t n, d
  * depend only on the grid's node structure and k; the library keeps them for
  * the last 8 (d, level, k) it saw and reuses them for grids with the same
  * levels and indices (a grid rebuilt every step).
- * Synchronises `stream` before returning.  Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA. */
+ * Asynchronous on `stream` (with the host tables cached, nothing waits for
+ * the stream): the handle is ready in `stream` order, and use on another
+ * stream needs an event or a synchronisation first.
+ * Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA (a fault in the build's kernels is
+ * reported by a later call that synchronises). */
 typedef struct sg_surplus sg_surplus;
 int sg_build_surpluses(const sg_grid* g, const double* d_values, int k,
                        sg_surplus** out, void* stream);
@@ -389,7 +398,8 @@ void sg_surplus_free(sg_surplus* s);
  *          split-TF32 operands; error bound stated with the kernel)
  *   d_out  Q x k doubles
  * Asynchronous on `stream`; the handle is read-only, so concurrent calls on
- * different streams are safe.  Errors: SG_EINVAL, SG_EUNSUPPORTED, SG_ECUDA. */
+ * different streams are safe once its build is complete (a build is queued
+ * on its own stream).  Errors: SG_EINVAL, SG_EUNSUPPORTED, SG_ECUDA. */
 int sg_eval_feedback(const sg_surplus* s, const double* d_xq, int64_t Q, int mode,
                      double* d_out, void* stream);
 

@@ -430,10 +430,16 @@ struct GraphKey {
 // launch it: the executable is destroyed when the last holder lets go, so an
 // entry evicted by one host thread stays valid for another thread that has
 // already looked it up and is launching it on its own stream.
+// The graph forms return without waiting for their graphs, so an executable
+// may still be running when its last reference goes (an entry evicted from
+// the cache): the device is synchronised before it is destroyed.
 struct GraphExec {
   cudaGraphExec_t exec = nullptr;
   ~GraphExec() {
-    if (exec) cudaGraphExecDestroy(exec);
+    if (exec) {
+      cudaDeviceSynchronize();
+      cudaGraphExecDestroy(exec);
+    }
   }
 };
 using GraphExecPtr = std::shared_ptr<GraphExec>;
@@ -527,11 +533,8 @@ static int launch_solve_graph(const SolveArgs& a, Workspace w, cudaStream_t st, 
 template <typename T>
 static int run_solve_graph(const SolveArgs& a, Workspace w, cudaStream_t st, double* lambda0, double* u0,
                            double* V, int32_t* status, int32_t* iters, double* Yout) {
-  GraphExecPtr held;
-  const int rc = launch_solve_graph<T>(a, w, st, lambda0, u0, V, status, iters, Yout, &held);
-  if (rc != SG_OK) return rc;
-  SG_CUDA_TRY(cudaStreamSynchronize(st));
-  return SG_OK;
+  GraphExecPtr held;   // the cache keeps the executable (see GraphExec)
+  return launch_solve_graph<T>(a, w, st, lambda0, u0, V, status, iters, Yout, &held);
 }
 
 // ---------------------------------------------------------------- a graph per mesh size
@@ -671,8 +674,7 @@ static int run_solve_mesh_groups(const SolveArgs& a, void* work, size_t work_byt
   SG_TIMED("k_group_scatter", st,
            (k_group_scatter<<<gb, 128, 0, st>>>(idx, a.n, glam, gu, gV, gst, git, lambda0, u0, V, status, iters)));
   SG_LAUNCH_CHECK("k_group_scatter");
-  SG_CUDA_TRY(cudaStreamSynchronize(st));
-  *ran = true;
+  *ran = true;   // queued on st (which waits for every sub-batch); not waited for here
   return SG_OK;
 }
 

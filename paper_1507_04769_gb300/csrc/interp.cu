@@ -41,11 +41,18 @@ int function_id(int l, int kidx) {
   return off + j;
 }
 
+// The grid's box (lo, then hi - lo), passed by value so that no host copy
+// waits for the stream.
+struct SurplusBox {
+  double v[2 * kMaxDim];
+};
+
 // Points of the finest set X^{L+1} on [0, 1]: x_p = (1 - cos(p pi / 2^L)) / 2
-// = sin^2(p pi / 2^(L+1)) (Eq. CGL).
-__global__ void k_fine_coords(int level, double* xf) {
+// = sin^2(p pi / 2^(L+1)) (Eq. CGL).  The first 2d threads also store the box.
+__global__ void k_fine_coords(int level, double* xf, SurplusBox box, int nbox, double* dbox) {
   const int fine_n = 1 << level;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nbox) dbox[p] = box.v[p];
   if (p > fine_n) return;
   if (level == 0) {
     xf[p] = 0.5;
@@ -267,11 +274,25 @@ struct SurplusHost {
   std::vector<int64_t> level_start;
   int64_t grp[kMaxDim + 2] = {};
   bool sf_ok = false, tcoff_ok = false;
-  SfPlan sf;                    // scalar fields (its tables are in `staging`)
+  SfPlan sf;                    // scalar fields (its tables are in the staged bytes)
   size_t npack = 0, off = 0, ohost = 0;
   size_t oW = 0, oWs = 0, oWdf = 0, oxf = 0, oxfdf = 0, otab1 = 0, obp = 0, oerr = 0, osfb = 0;
   size_t obox = 0, onact = 0, oops = 0, otcoff = 0, ofid = 0, ofpt = 0, oorder = 0, ometa = 0, obmap = 0;
   std::vector<unsigned char> staging;   // bytes [ohost, off) of the allocation, box zero
+  // The same bytes in page-locked memory when it could be had (then
+  // `staging` is emptied): a copy from it is queued without waiting for the
+  // stream, where a copy from pageable memory first synchronises it.
+  unsigned char* pinned = nullptr;
+  const unsigned char* bytes() const { return pinned ? pinned : staging.data(); }
+  SurplusHost() = default;
+  SurplusHost(const SurplusHost&) = delete;
+  SurplusHost& operator=(const SurplusHost&) = delete;
+  ~SurplusHost() {
+    if (pinned) {
+      cudaDeviceSynchronize();   // a build may still be copying from it
+      cudaFreeHost(pinned);
+    }
+  }
 };
 
 std::shared_ptr<const SurplusHost> make_surplus_host(const sg_grid* g, int k) {
@@ -393,6 +414,14 @@ std::shared_ptr<const SurplusHost> make_surplus_host(const sg_grid* g, int k) {
     h->sf.bmap.clear();
     h->sf.bmap.shrink_to_fit();
   }
+  if (cudaHostAlloc(reinterpret_cast<void**>(&h->pinned), st.size(), cudaHostAllocDefault) == cudaSuccess) {
+    std::memcpy(h->pinned, st.data(), st.size());
+    st.clear();
+    st.shrink_to_fit();
+  } else {
+    h->pinned = nullptr;
+    (void)cudaGetLastError();   // pageable staging still works, the copy then waits
+  }
   return h;
 }
 
@@ -490,18 +519,17 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   };
 #define SG_TRY_CLEAN(expr)                                  \
   if ((e = (expr)) != cudaSuccess) return cleanup(e, #expr);
-  {
-    // the host-made tables (cached), then this grid's box over their zero
-    // bytes; copies from pageable memory are staged before the calls return
-    double box[2 * kMaxDim];
-    for (int dim = 0; dim < d; ++dim) {
-      box[dim] = g->h_lo[dim];
-      box[d + dim] = g->h_hi[dim] - g->h_lo[dim];
-    }
-    SG_TRY_CLEAN(cudaMemcpyAsync(base + h.ohost, h.staging.data(), h.off - h.ohost, cudaMemcpyHostToDevice, st));
-    SG_TRY_CLEAN(cudaMemcpyAsync(base + h.obox, box, 2 * d * sizeof(double), cudaMemcpyHostToDevice, st));
+  // the host-made tables (cached), then this grid's box over their zero
+  // bytes (written by k_fine_coords from its arguments)
+  SurplusBox box{};
+  for (int dim = 0; dim < d; ++dim) {
+    box.v[dim] = g->h_lo[dim];
+    box.v[d + dim] = g->h_hi[dim] - g->h_lo[dim];
   }
-  SG_TIMED("k_fine_coords", st, (k_fine_coords<<<static_cast<unsigned>(ceil_div(fine_n + 1, 64)), 64, 0, st>>>(L, s->xf)));
+  SG_TRY_CLEAN(cudaMemcpyAsync(base + h.ohost, h.bytes(), h.off - h.ohost, cudaMemcpyHostToDevice, st));
+  SG_TIMED("k_fine_coords", st,
+           (k_fine_coords<<<static_cast<unsigned>(ceil_div(fine_n + 1 > 2 * d ? fine_n + 1 : 2 * d, 64)), 64, 0, st>>>(
+               L, s->xf, box, 2 * d, s->box)));
   SG_TIMED("k_fine_table", st, (k_fine_table<<<static_cast<unsigned>(ceil_div(fine_n + 1, 64)), 64, 0, st>>>(L, s->xf, d_tab1)));
   SG_TRY_CLEAN(cudaGetLastError());
   for (size_t lv = 0; lv + 1 < h.level_start.size(); ++lv) {
@@ -519,7 +547,6 @@ extern "C" int sg_build_surpluses(const sg_grid* g, const double* d_values, int 
   SG_TRY_CLEAN(cudaMemsetAsync(s->tc_err, 0, sizeof(int), st));
   if (pack_tf32(s, st) != SG_OK) return cleanup(cudaGetLastError(), "pack_tf32");
   if (sf_pack(s, st) != SG_OK) return cleanup(cudaGetLastError(), "sf_pack");
-  SG_TRY_CLEAN(cudaStreamSynchronize(st));
 #undef SG_TRY_CLEAN
   *out = s;
   return SG_OK;

@@ -136,10 +136,12 @@ class Server:
         """Solves the full grid of `level` for horizon T and stores its model."""
         g = self.grid(level)
         N = horizon_mesh(T)
-        with torch.cuda.stream(stream or torch.cuda.current_stream()):
+        st = stream or torch.cuda.current_stream()
+        with torch.cuda.stream(st):
             res = sg.solve_bvps(self.problem, g.coords, T, N, tol=self.tol, precision=self.precision,
                                 n_max=self.pool_nmax)
             S = sg.Surplus(g, res["u0"])
+        st.synchronize()   # built before other streams can use the model
         self.models[(level, T)] = Model(g, S, T)
         return res
 

@@ -113,6 +113,17 @@ def _ptr(t: torch.Tensor):
     return C.c_void_p(t.data_ptr())
 
 
+def _keep_for(stream, *tensors):
+    """The library queues work on `stream` and may return before it runs: when
+    that is not the current stream, keep PyTorch's allocator from handing these
+    tensors' blocks to the current stream's next allocations until then."""
+    if stream is None or stream == torch.cuda.current_stream(stream.device):
+        return
+    for t in tensors:
+        if t is not None:
+            t.record_stream(stream)
+
+
 def _dev(t, dtype, device="cuda"):
     t = torch.as_tensor(t, dtype=dtype, device=device)
     return t.contiguous()
@@ -237,6 +248,7 @@ def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=5
                              _ptr(workspace), workspace.numel(), _ptr(out["lambda0"]), _ptr(out["u0"]),
                              _ptr(out["V"]), _ptr(out["status"]), _ptr(out["iters"]),
                              _ptr(Y) if Y is not None else None, _stream(stream)))
+    _keep_for(stream, x0, T, N, workspace, Y, *out.values())
     if Y is not None:
         out["Y"] = Y
     return out
@@ -356,6 +368,7 @@ class Surplus:
         h = C.c_void_p()
         _check(LIB.sg_build_surpluses(grid.handle, _ptr(values), values.shape[1], C.byref(h),
                                       _stream(stream)))
+        _keep_for(stream, values)
         self._h = h
         n, k, pw = C.c_int64(), C.c_int(), C.c_void_p()
         _check(LIB.sg_surplus_info(h, C.byref(n), C.byref(k), C.byref(pw)))
@@ -381,6 +394,7 @@ def eval_feedback(surplus: Surplus, xq: torch.Tensor, mode: int = EVAL_FP64,
     if out is None:
         out = torch.empty((Q, surplus.k), dtype=torch.float64, device=xq.device)
     _check(LIB.sg_eval_feedback(surplus.handle, _ptr(xq), Q, mode, _ptr(out), _stream(stream)))
+    _keep_for(stream, xq, out)
     return out
 
 
