@@ -44,6 +44,7 @@ METRIC = "converged BVP solves/s at 1e-8 residual"
 UNIT = "solves/s"
 LEVEL, D = 4, 6
 N_QUERIES = 1_000_000
+E2E_EVAL_CHUNKS = 4        # e2e step: evaluation calls whose results go down while the next evaluates
 TOL = 1e-8
 SEG_LEN = 16   # intervals per segment of the library's segmented staircase
 
@@ -53,7 +54,7 @@ SEG_LEN = 16   # intervals per segment of the library's segmented staircase
 # solver_kernels_attitude6d_600nodes.md).  An entry is removed when its kernel
 # changes, until it is captured again.
 DRAM_BYTES_PER_UNIT = {
-    "k_condense_reg_fp32": ((295.598848e6 + 469.412096e6) / 88064, "interval"),
+    "k_condense_reg_fp32": ((295.767552e6 + 469.892352e6) / 88064, "interval"),
 }
 WORKLOAD = ("attitude6d_L4_1457nodes_T{10,20,40}_N{64,128,256}_mixedprec"
             "+surplus+1e6queries_tf32x3")
@@ -375,7 +376,7 @@ def gpu_arm(args):
                "status": torch.empty((n_loc,), dtype=torch.int32, device=dev),
                "iters": torch.empty((n_loc,), dtype=torch.int32, device=dev)}
 
-    def step(events=None, queries_ready=None):
+    def step(events=None, queries_ready=None, eval_chunks=1, after_chunk=None):
         if events:
             events[0].record(stream)
         g = sg.Grid(D, LEVEL, lo, hi)
@@ -391,7 +392,13 @@ def gpu_arm(args):
             events[3].record(stream)
         if queries_ready is not None:
             stream.wait_event(queries_ready)
-        sg.eval_feedback(S, xq_d, mode=eval_mode, out=u_out)
+        # the queries in eval_chunks consecutive calls (after_chunk(a, b) is
+        # told of each one as it is queued)
+        for c in range(eval_chunks):
+            a, b = q_loc * c // eval_chunks, q_loc * (c + 1) // eval_chunks
+            sg.eval_feedback(S, xq_d[a:b], mode=eval_mode, out=u_out[a:b])
+            if after_chunk is not None:
+                after_chunk(a, b)
         if events:
             events[4].record(stream)
         return res
@@ -474,10 +481,20 @@ def gpu_arm(args):
                 for k, shp, dt in (("lambda0", (6,), torch.float64), ("u0", (3,), torch.float64),
                                    ("V", (), torch.float64), ("status", (), torch.int32))}
 
-    # the queries are uploaded on a second stream while the grid, the solves and
-    # the surpluses run; the evaluation waits for them
+    # The queries are uploaded on a second stream while the grid, the solves and
+    # the surpluses run; the evaluation waits for them.  It runs in E2E_EVAL_CHUNKS
+    # calls, and each chunk's feedback goes down on a third stream while the next
+    # one evaluates; the step ends when the last copy has landed.
     up_stream = torch.cuda.Stream(device=dev)
+    down_stream = torch.cuda.Stream(device=dev)
     xq_ready = torch.cuda.Event()
+
+    def chunk_down(a, b):
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        down_stream.wait_event(ev)
+        with torch.cuda.stream(down_stream):
+            u_pin[a:b].copy_(u_out[a:b], non_blocking=True)
 
     def e2e_step():
         T_d.copy_(T_pin, non_blocking=True)
@@ -486,10 +503,10 @@ def gpu_arm(args):
         with torch.cuda.stream(up_stream):
             xq_d.copy_(xq_pin, non_blocking=True)
             xq_ready.record(up_stream)
-        r = step(queries_ready=xq_ready)
-        u_pin.copy_(u_out, non_blocking=True)
+        r = step(queries_ready=xq_ready, eval_chunks=E2E_EVAL_CHUNKS, after_chunk=chunk_down)
         for k in node_pin:
             node_pin[k].copy_(r[k], non_blocking=True)
+        stream.wait_stream(down_stream)
         return r
 
     for _ in range(2):
