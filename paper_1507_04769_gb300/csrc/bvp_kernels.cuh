@@ -658,8 +658,10 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
 // The 36 x 49 system splits into the 24 interior columns (stages 2 and 3,
 // eliminated) and the 25 passive columns [y_i | y_{i+1} | rhs].
 //   Phase A (rows on lanes): lane r holds interior row r (r < 24) or stage-4
-//   row r (24..31); lanes 24..27 also hold stage-4 rows 32..35.  Only the 24
-//   interior columns live in registers.  Partial pivoting over the interior
+//   row r (24..31); stage-4 rows 32..35 are spread over the warp for the first
+//   four pivot steps and then move into the lanes of the first four pivot
+//   rows, which are free by then.  Only the 24 interior columns live in
+//   registers.  Partial pivoting over the interior
 //   rows; at step k the pivot lane publishes its row in the
 //   shared-memory table U (16-byte broadcast reads), every lane forms
 //   1/pivot from it, and every row records its multiplier l(r, k) in L.
@@ -671,6 +673,7 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
 // Rows never move.  The stored recovery rows are [U_k | Q_k] in pivot order
 // (raw pivot on the diagonal), the condensed block row is [S | T | rhs].
 constexpr int kCondLd = 28;                          // row stride of P, L and U (floats)
+constexpr int kSpreadSteps = 4;                      // pivot steps before rows 32..35 move into lanes
 constexpr int kCondSmemFloats = 36 * kCondLd * 2 + 8 * kCondLd + 32;    // P, L, U (ring of 8 rows), pivot order
 
 // (sm is not __restrict__: lanes exchange pivot rows through it across
@@ -724,9 +727,10 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
 
   float ra[24];
   build(lane, ra);
-  // rows 32..35 (stage 4, components 8..11) are spread over the warp: lane
+  // rows 32..35 (stage 4, components 8..11) start spread over the warp: lane
   // group g = lane / 8 holds row 32 + g, lane sub = lane % 8 holds columns
   // sub, sub + 8 and sub + 16 of its interior part and of its passive part
+  // (the passive part stays there: it goes to P)
   const int g = lane >> 3, sub = lane & 7;
   const int r2 = 32 + g, comp2 = 8 + g;
   float rb[3];
@@ -758,7 +762,8 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
   float live = 1.0f;                        // 0 once the row is a pivot row
   bool bad = false;                         // a zero or non-finite pivot (the same in every lane)
   float inv_keep = 0.0f;                    // lane j < 8: 1/pivot of the last step k with k % 8 == j
-  float lbk[3] = {0.f, 0.f, 0.f};           // multipliers of row r2 at columns sub, sub + 8, sub + 16
+  float lbk = 0.f;                          // multiplier of row r2 at column sub (steps 0..3)
+  int myrow = lane;                         // the row this lane holds (32..35 once moved in)
 #pragma unroll
   for (int k = 0; k < 24; ++k) {
     const int q0 = k / 4;
@@ -794,16 +799,45 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     }
     // column k is done: row `lane` keeps its multiplier there
     ra[k] = la;
-    // rows 32..35: column k sits on lane k % 8 of each group, register k / 8
-    const float lb = __shfl_sync(0xffffffffu, rb[k >> 3], k & 7, 8) * inv;
+    if (k < kSpreadSteps) {
+      // rows 32..35: column k sits on lane k % 8 of each group, register k / 8
+      const float lb = __shfl_sync(0xffffffffu, rb[k >> 3], k & 7, 8) * inv;
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      if (8 * m + 7 > k) {
-        const int c = sub + 8 * m;
-        if (c > k) rb[m] = fmaf(-lb, U_s[(k & 7) * kCondLd + c], rb[m]);
+      for (int m = 0; m < 3; ++m) {
+        if (8 * m + 7 > k) {
+          const int c = sub + 8 * m;
+          if (c > k) rb[m] = fmaf(-lb, U_s[(k & 7) * kCondLd + c], rb[m]);
+        }
+      }
+      if (k == sub) lbk = lb;   // row r2's multiplier of column k, kept by lane sub
+    }
+    if (k == kSpreadSteps - 1) {
+      // The lanes of the first pivot rows are free now: rows 32..35 move into
+      // them (the row's remaining columns from its group's registers, its
+      // multipliers so far from lbk) and take part in the row updates from
+      // here on.  The pivot rows' own multipliers go to L first (phase B
+      // reads them).
+      int gm = -1;
+#pragma unroll
+      for (int j = 0; j < kSpreadSteps; ++j)
+        if (perm_s[j] == lane) gm = j;
+      if (gm >= 0) {
+        float4* d4 = reinterpret_cast<float4*>(L_s + lane * kCondLd);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) d4[q] = make_float4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
+      }
+      const int src = (gm >= 0 ? gm : 0) * 8;
+#pragma unroll
+      for (int c = 0; c < 24; ++c) {
+        const float v = c < kSpreadSteps ? __shfl_sync(0xffffffffu, lbk, src + c)
+                                         : __shfl_sync(0xffffffffu, rb[c >> 3], src + (c & 7));
+        if (gm >= 0) ra[c] = v;
+      }
+      if (gm >= 0) {
+        live = 1.0f;
+        myrow = 32 + gm;
       }
     }
-    if ((k & 7) == sub) lbk[k >> 3] = lb;   // row r2's multiplier of column k, kept by lane sub
     if ((k & 7) == 7) {
       // the ring is full: rows k - 7 .. k to the recovery rows (at and right
       // of the diagonal chunk) with 1/pivot
@@ -818,11 +852,10 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     }
   }
   if (bad && lane == 0) w.ns[node].singular = 1;
-#pragma unroll
-  for (int m = 0; m < 3; ++m) L_s[r2 * kCondLd + sub + 8 * m] = lbk[m];
-  // multipliers to L (a pivot row's entries from its own step on are never read)
+  // multipliers to L (a pivot row's entries from its own step on are never
+  // read; the first pivot rows were stored when rows 32..35 moved in)
   {
-    float4* d4 = reinterpret_cast<float4*>(L_s + lane * kCondLd);
+    float4* d4 = reinterpret_cast<float4*>(L_s + myrow * kCondLd);
 #pragma unroll
     for (int q = 0; q < 6; ++q) d4[q] = make_float4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
   }
