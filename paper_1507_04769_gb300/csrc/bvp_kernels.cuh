@@ -1318,7 +1318,6 @@ __global__ void __launch_bounds__(32 * seg_warps<T>()) k_abd_seg(SolveArgs a, Wo
     // to the lower lane); rows that are no candidates have zero mask and tag
     unsigned kmask = lane < 24 ? ~31u : 0u;
     unsigned ktag = lane < 24 ? itag : 0u;
-    T inv_keep = T(0);   // FP32: lane k < 12 keeps 1/pivot of step k
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       const int q0 = k / V;
@@ -1341,14 +1340,14 @@ __global__ void __launch_bounds__(32 * seg_warps<T>()) k_abd_seg(SolveArgs a, Wo
       T inv = u[k];
       if constexpr (sizeof(T) == sizeof(float)) {
         // FP32: the row is published with its raw pivot and every lane forms
-        // the same 1/pivot (off the pivot lane's path); lane k keeps it for
-        // the diagonal of the stored row
+        // the same 1/pivot (off the pivot lane's path)
         bool good;
         inv = pivot_recip(inv, good);
         bad = bad || !good;
-        if (lane == k) inv_keep = inv;
       }
-      const T la = ktag != 0u ? ya[k] * inv : T(0);
+      // (lanes that are no candidate update rows whose entries from here on
+      // are never read)
+      const T la = ya[k] * inv;
 #pragma unroll
       for (int q = q0; q < 12 / V; ++q) {
         T uv[V];
@@ -1369,7 +1368,10 @@ __global__ void __launch_bounds__(32 * seg_warps<T>()) k_abd_seg(SolveArgs a, Wo
     }
     if (lane < 24) store_row12_from<T>(L_s + lane * 12, ya, 0);   // a pivot row's entries from its step on are never read
     if constexpr (sizeof(T) == sizeof(float)) {
-      if (lane < 12) U_s[lane * 12 + lane] = inv_keep;   // 1/pivot on the diagonal of the stored rows
+      if (lane < 12) {   // 1/pivot on the diagonal of the stored rows (formed again: the same value)
+        bool gd;
+        U_s[lane * 12 + lane] = pivot_recip(U_s[lane * 12 + lane], gd);
+      }
     }
     const unsigned cmask = __ballot_sync(0xffffffffu, ktag != 0u);   // the 12 rows that were no pivot
     if (ktag != 0u) cslot_s[__popc(cmask & lt_mask)] = lane;
