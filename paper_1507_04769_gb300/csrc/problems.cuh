@@ -56,34 +56,33 @@ __device__ __forceinline__ dfnum pconst<dfnum>(double, float2 f) { return dfnum(
 
 // ------------------------------------------------------------------ duals
 // FP64 sine and cosine.  On |a| <= pi/4 (where the Euler angles of the
-// attitude problem stay) they are the Taylor polynomials of sin and cos about
-// 0, through a^17 and a^18, evaluated by Horner's rule in a^2; the first
-// omitted terms are below 1e-19 there, so the result is within a few units in
-// the last place.  Larger arguments take the CUDA library sincos.
+// attitude problem stay), with z = a^2,
+//   sin a = a + a z P(z),  cos a = 1 + z (-1/2 + z Q(z)),
+// P and Q of degree 5 being the weighted minimax polynomials for the relative
+// error of sin and cos on that interval (the Remez exchange algorithm; the
+// derivation, and its check of these literals, are in sincos_coeffs.py beside
+// this package's sources).  The rounded polynomials are within 1.3e-17
+// (sin) and 6e-19 (cos) of the functions; with the fused Horner evaluation
+// the results are within about one unit in the last place.  Larger arguments
+// take the CUDA library sincos.
 __device__ __forceinline__ void dsincos(double a, double* s, double* c) {
   if (fabs(a) <= 0.78539816339744831) {
     const double z = a * a;
-    // sin a = a (1 - z/3! + z^2/5! - ... + z^8/17!)
-    double ps = 1.0 / 355687428096000.0;                  // 1/17!
-    ps = fma(ps, z, -1.0 / 1307674368000.0);              // 1/15!
-    ps = fma(ps, z, 1.0 / 6227020800.0);                  // 1/13!
-    ps = fma(ps, z, -1.0 / 39916800.0);                   // 1/11!
-    ps = fma(ps, z, 1.0 / 362880.0);                      // 1/9!
-    ps = fma(ps, z, -1.0 / 5040.0);                       // 1/7!
-    ps = fma(ps, z, 1.0 / 120.0);                         // 1/5!
-    ps = fma(ps, z, -1.0 / 6.0);                          // 1/3!
+    double ps = 0x1.5d8773e0ff40dp-33;
+    ps = fma(ps, z, -0x1.ae5e4c58b3d0ap-26);
+    ps = fma(ps, z, 0x1.71de356f7490ap-19);
+    ps = fma(ps, z, -0x1.a01a019c30bb6p-13);
+    ps = fma(ps, z, 0x1.111111110fb50p-7);
+    ps = fma(ps, z, -0x1.555555555554dp-3);
     *s = fma(a * z, ps, a);
-    // cos a = 1 - z/2! + z^2/4! - ... + z^9/18!
-    double pc = 1.0 / 6402373705728000.0;                 // 1/18!
-    pc = fma(pc, z, -1.0 / 20922789888000.0);             // 1/16!
-    pc = fma(pc, z, 1.0 / 87178291200.0);                 // 1/14!
-    pc = fma(pc, z, -1.0 / 479001600.0);                  // 1/12!
-    pc = fma(pc, z, 1.0 / 3628800.0);                     // 1/10!
-    pc = fma(pc, z, -1.0 / 40320.0);                      // 1/8!
-    pc = fma(pc, z, 1.0 / 720.0);                         // 1/6!
-    pc = fma(pc, z, -1.0 / 24.0);                         // 1/4!
-    pc = fma(pc, z, 0.5);                                 // 1/2!
-    *c = fma(-z, pc, 1.0);
+    double pc = -0x1.8ff9dcba514eep-37;
+    pc = fma(pc, z, 0x1.1eea895d2f6e9p-29);
+    pc = fma(pc, z, -0x1.27e4f9040bb84p-22);
+    pc = fma(pc, z, 0x1.a01a019e24efcp-16);
+    pc = fma(pc, z, -0x1.6c16c16c16134p-10);
+    pc = fma(pc, z, 0x1.5555555555553p-5);
+    pc = fma(pc, z, -0.5);
+    *c = fma(z, pc, 1.0);
   } else {
     sincos(a, s, c);
   }

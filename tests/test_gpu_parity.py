@@ -503,7 +503,7 @@ def test_tf32x3_full_size_sampled():
 
 @pytest.mark.gpu
 def test_library_sincos_within_few_ulp():
-    """The FP64 sine/cosine inside the right-hand side (Taylor polynomials on
+    """The FP64 sine/cosine inside the right-hand side (minimax polynomials on
     |x| <= pi/4, the CUDA library beyond) against numpy's, within 4 ulp."""
     rng = np.random.default_rng(7)
     x = np.concatenate([rng.uniform(-np.pi / 4, np.pi / 4, 200_000),
