@@ -140,7 +140,9 @@ extern "C" int sg_build_grid(int d, int level, const double* h_lo, const double*
     std::memcpy(h.data() + (obox - ohost) + d * sizeof(double), h_hi, d * sizeof(double));
     std::memcpy(h.data() + (olev - ohost), g->h_lev.data(), total * sizeof(int8_t));
     std::memcpy(h.data() + (okidx - ohost), g->h_kidx.data(), total * sizeof(int16_t));
-    if ((e = cudaMemcpy(base + ohost, h.data(), off - ohost, cudaMemcpyHostToDevice)) != cudaSuccess)
+    // (a copy from pageable memory is staged before the call returns, so h
+    // may go; the kernel follows it on the same stream, and one wait covers both)
+    if ((e = cudaMemcpyAsync(base + ohost, h.data(), off - ohost, cudaMemcpyHostToDevice, nullptr)) != cudaSuccess)
       return cleanup(SG_ECUDA, "copy grid tables", e);
   }
   SG_TIMED("grid_coords_kernel", nullptr, (grid_coords_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256>>>(total, d, g->lev, g->kidx, d_box, d_box + d, g->coords)));

@@ -187,10 +187,19 @@ class Grid:
                                 C.byref(pc), C.byref(pl), C.byref(pi)))
         self.M, self.d, self.level = n.value, dd.value, ll.value
         self.lo, self.hi = lo.copy(), hi.copy()
-        dev = torch.device("cuda", torch.cuda.current_device())
-        self.coords = torch.as_tensor(_DevView(pc.value, (self.M, self.d), "<f8"), device=dev)
-        self.levels = torch.as_tensor(_DevView(pl.value, (self.M, self.d), "|i1"), device=dev)
-        self.index = torch.as_tensor(_DevView(pi.value, (self.M, self.d), "<i2"), device=dev)
+        self._dev = torch.device("cuda", torch.cuda.current_device())
+        self._pl, self._pi = pl.value, pi.value
+        self.coords = torch.as_tensor(_DevView(pc.value, (self.M, self.d), "<f8"), device=self._dev)
+
+    @property
+    def levels(self) -> torch.Tensor:
+        """Borrowed (M, d) int8 view of the nodes' levels i_k."""
+        return torch.as_tensor(_DevView(self._pl, (self.M, self.d), "|i1"), device=self._dev)
+
+    @property
+    def index(self) -> torch.Tensor:
+        """Borrowed (M, d) int16 view of each coordinate's index in X^{i_k}."""
+        return torch.as_tensor(_DevView(self._pi, (self.M, self.d), "<i2"), device=self._dev)
 
     @property
     def handle(self):
