@@ -63,6 +63,10 @@ constexpr int kCols = 49;        // 24 interior + 12 (y_i) + 12 (y_{i+1}) + rhs
 constexpr int kRecLd = 52;       // row stride of a stored interior pivot row (16-byte multiple)
 constexpr int kRecInv = 49;      // column of a stored pivot row holding 1/pivot
 constexpr int kRec = 24 * kRecLd;
+// FP32 recovery rows are stored chunk-major: the 16-byte chunk q (columns
+// 4q..4q+3) of rows 0..23 lie side by side, so a warp reading chunk q of its
+// 24 rows reads 384 contiguous bytes.  Float offset of (row r, column c):
+__host__ __device__ __forceinline__ int rec_at(int r, int c) { return ((c >> 2) * 24 + r) * 4 + (c & 3); }
 constexpr int kBlkLd = 28;       // row stride of a 12-row block of 25 columns
 constexpr int kBlk = 12 * kBlkLd;
 constexpr int kResRows = 36;     // stage residual rows per interval
@@ -81,7 +85,7 @@ struct Workspace {
   void* Jm;        // n x P x 144 (T), Jacobians
   void* Res;       // n x Nmax x 36 (T), stage residuals at the iterate
   void* Cond;      // n x Nmax x kBlk (T), condensed block rows
-  void* Rec;       // n x Nmax x kRec (T), interior pivot rows
+  void* Rec;       // n x Nmax x kRec (T), interior pivot rows (FP32: chunk-major, rec_at)
   void* Abd;       // n x Nmax x kBlk (T), staircase pivot rows
   void* Seg;       // n x Nmax x kSegBlk (T), pivot rows of the segment eliminations
   void* Red;       // n x seg_count(Nmax) x kBlk (T), reduced block rows of the segments
@@ -674,7 +678,7 @@ __device__ __forceinline__ void panel_eliminate12(T (&r)[25], bool cand, bool& d
 // (raw pivot on the diagonal), the condensed block row is [S | T | rhs].
 constexpr int kCondLd = 28;                          // row stride of P, L and U (floats)
 constexpr int kSpreadSteps = 4;                      // pivot steps before rows 32..35 move into lanes
-constexpr int kCondSmemFloats = 36 * kCondLd * 2 + 8 * kCondLd + 32;    // P, L, U (ring of 8 rows), pivot order
+constexpr int kCondSmemFloats = 36 * kCondLd * 2 + 8 * kCondLd + 32 + 24;   // P, L, U (ring of 8 rows), pivot order, 1/pivot
 
 // (sm is not __restrict__: lanes exchange pivot rows through it across
 // __syncwarp, and a no-alias promise would let the compiler read it before
@@ -690,6 +694,7 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
   float* L_s = sm + 36 * kCondLd;          // [36][kCondLd] multipliers l(r, k)
   float* U_s = sm + 72 * kCondLd;          // [8][kCondLd] pivot row of step k at k % 8, 1/pivot at 24
   int* perm_s = reinterpret_cast<int*>(sm + 80 * kCondLd);   // [24] pivot row of step k
+  float* inv_s = sm + 80 * kCondLd + 32;   // [24] 1/pivot of step k (for the stored rows)
   const int64_t blk = node * a.Nmax + i;
   float* rec = static_cast<float*>(w.Rec) + blk * kRec;
 
@@ -842,12 +847,12 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
       // the ring is full: rows k - 7 .. k to the recovery rows (at and right
       // of the diagonal chunk) with 1/pivot
       const int k0 = k - 7;
-      for (int e = lane; e < 48; e += 32) {
-        const int kk = k0 + e / 6, q = e % 6;
+      for (int e = lane; e < 48; e += 32) {   // eight consecutive lanes: one chunk of the eight rows
+        const int q = e >> 3, kk = k0 + (e & 7);
         if (q >= kk / 4)
-          reinterpret_cast<float4*>(rec + kk * kRecLd)[q] = reinterpret_cast<const float4*>(U_s + (kk & 7) * kCondLd)[q];
+          reinterpret_cast<float4*>(rec)[q * 24 + kk] = reinterpret_cast<const float4*>(U_s + (kk & 7) * kCondLd)[q];
       }
-      if (lane < 8) rec[(k0 + lane) * kRecLd + kRecInv] = inv_keep;
+      if (lane < 8) inv_s[k0 + lane] = inv_keep;
       __syncwarp();
     }
   }
@@ -886,7 +891,6 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     }
     x += y;
     Q[k] = x;
-    if (col) rec[k * kRecLd + 24 + lane] = x;
   }
 #pragma unroll 4
   for (int r = 24; r < 36; ++r) {
@@ -902,6 +906,23 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
     }
     if (col) cond[(r - 24) * kBlkLd + lane] = f;
   }
+  // the passive parts Q_k and 1/pivot to the stored rows: through P's rows
+  // 0..23 (read for the last time in the Q loop) so that the stores of each
+  // chunk are contiguous (rec_at)
+  float* T_s = P_s;   // [24][kCondLd]: row k = Q_k (columns 24..48 of the stored row)
+  __syncwarp();
+  if (col) {
+#pragma unroll
+    for (int k = 0; k < 24; ++k) T_s[k * kCondLd + lane] = Q[k];
+  }
+  __syncwarp();
+  float4* rec4 = reinterpret_cast<float4*>(rec);
+  for (int e = lane; e < 24 * 6; e += 32) {   // chunks 6..11 (columns 24..47), 24 rows each
+    const int q = e / 24, k = e - 24 * q;
+    rec4[(6 + q) * 24 + k] = *reinterpret_cast<const float4*>(T_s + k * kCondLd + 4 * q);
+  }
+  if (lane < 24)   // chunk 12: column 48 (rhs) and 49 (1/pivot)
+    rec4[12 * 24 + lane] = make_float4(T_s[lane * kCondLd + 24], inv_s[lane], 0.0f, 0.0f);
   __syncwarp();   // the tables are reused by the warp's next interval
 }
 
@@ -1539,11 +1560,11 @@ __device__ __forceinline__ void recover_interval(const SolveArgs& a, const Works
   for (int c = 0; c < kRecLd; ++c) row[c] = T(0);
   if (lane < 24) {
     if constexpr (sizeof(T) == 4) {
-      const float4* s4 = reinterpret_cast<const float4*>(rec + lane * kRecLd);
+      const float4* s4 = reinterpret_cast<const float4*>(rec) + lane;   // chunk-major (rec_at)
 #pragma unroll
       for (int q = 0; q < kRecLd / 4; ++q) {
         if (4 * q + 3 < lane) continue;
-        const float4 v = s4[q];
+        const float4 v = s4[q * 24];
         row[4 * q] = v.x; row[4 * q + 1] = v.y; row[4 * q + 2] = v.z; row[4 * q + 3] = v.w;
       }
     } else {
