@@ -552,18 +552,23 @@ __device__ __forceinline__ void load_row25(const T* __restrict__ src, T (&r)[25]
   r[24] = src[24];
 }
 
+// A 25-entry row into a kBlkLd (28) slot, the 3 pad entries zeroed: whole
+// 32-byte sectors are written, so the memory system need not read the slot
+// first.
 template <typename T>
 __device__ __forceinline__ void store_row25(T* __restrict__ dst, const T (&r)[25]) {
   if constexpr (sizeof(T) == 4) {
     float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
     for (int q = 0; q < 6; ++q) d4[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    d4[6] = make_float4(r[24], 0.0f, 0.0f, 0.0f);
   } else {
     double2* d2 = reinterpret_cast<double2*>(dst);
 #pragma unroll
     for (int q = 0; q < 12; ++q) d2[q] = make_double2(r[2 * q], r[2 * q + 1]);
+    d2[12] = make_double2(r[24], 0.0);
+    d2[13] = make_double2(0.0, 0.0);
   }
-  dst[24] = r[24];
 }
 
 // Pivot-search key: the magnitude bits (sign shifted out; for doubles the
@@ -904,7 +909,7 @@ __device__ __forceinline__ void condense_interval_reg(const SolveArgs& a, const 
       f = fmaf(-lv.z, Q[4 * q + 2], f);
       f = fmaf(-lv.w, Q[4 * q + 3], f);
     }
-    if (col) cond[(r - 24) * kBlkLd + lane] = f;
+    if (lane < kBlkLd) cond[(r - 24) * kBlkLd + lane] = col ? f : 0.0f;   // pad zeroed: whole sectors
   }
   // the passive parts Q_k and 1/pivot to the stored rows: through P's rows
   // 0..23 (read for the last time in the Q loop) so that the stores of each
