@@ -427,17 +427,19 @@ std::shared_ptr<const SurplusHost> make_surplus_host(const sg_grid* g, int k) {
 
 std::shared_ptr<const SurplusHost> surplus_host(const sg_grid* g, int k) {
   static std::mutex mu;
-  static std::vector<std::shared_ptr<const SurplusHost>> cache;   // most recent last
+  // most recent last; never destroyed (its entries' page-locked memory is not
+  // handed back to a CUDA runtime that may already be shut down at exit)
+  static auto* cache = new std::vector<std::shared_ptr<const SurplusHost>>();
   {
     std::lock_guard<std::mutex> lk(mu);
-    for (auto& c : cache)
+    for (auto& c : *cache)
       if (c->d == g->d && c->L == g->level && c->k == k && c->M == g->M && c->lev == g->h_lev && c->kidx == g->h_kidx)
         return c;
   }
   auto h = make_surplus_host(g, k);
   std::lock_guard<std::mutex> lk(mu);
-  if (cache.size() >= 8) cache.erase(cache.begin());
-  cache.push_back(h);
+  if (cache->size() >= 8) cache->erase(cache->begin());
+  cache->push_back(h);
   return h;
 }
 }  // namespace
