@@ -174,6 +174,9 @@ const char* sg_last_error(void);
  * Nodes are ordered by |i|, then i lexicographically, then the 1-D indices
  * lexicographically; node 0 is the box centre.  Increment sets: dX^1 = {1/2},
  * dX^2 = {0, 1}, dX^i = the even-indexed points of X^i for i >= 3.
+ * The nodes' integer structure is a function of (d, level) only: the library
+ * enumerates it once per (d, level) (the last 8 seen are kept) and copies it
+ * into each new handle; the coordinates are computed at every call.
  * Synchronous (the coordinates are computed by a kernel on the default stream
  * and the call waits for it).  Errors: SG_EINVAL, SG_EUNSUPPORTED, SG_ENOMEM, SG_ECUDA. */
 typedef struct sg_grid sg_grid;

@@ -1,7 +1,12 @@
 // Step I: Smolyak sparse grid on nested Chebyshev-Gauss-Lobatto sets
 // (Section 3.2, Eq. CGL).  The multi-index enumeration is integer work done
-// once on the host; node coordinates are computed on the device.
+// on the host once per (d, level); node coordinates are computed on the device
+// at every build.
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -79,14 +84,72 @@ __device__ __forceinline__ double cgl_coord(int i, int k) {
   return s * s;
 }
 
+// The box, passed by value (no host copy to wait for).
+struct GridBox {
+  double lo[kMaxDim], hi[kMaxDim];
+};
+
 __global__ void grid_coords_kernel(int64_t total, int d, const int8_t* __restrict__ lev,
-                                   const int16_t* __restrict__ kidx, const double* __restrict__ lo,
-                                   const double* __restrict__ hi, double* __restrict__ coords) {
+                                   const int16_t* __restrict__ kidx, GridBox box, double* __restrict__ coords) {
   int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (e >= total) return;
   int k = static_cast<int>(e % d);
   double u = cgl_coord(lev[e], kidx[e]);
-  coords[e] = lo[k] + (hi[k] - lo[k]) * u;
+  coords[e] = box.lo[k] + (box.hi[k] - box.lo[k]) * u;
+}
+
+// The host-made part of a grid, a function of (d, level) only: the nodes'
+// levels and 1-D indices, and the same bytes in the device layout (levels,
+// then indices at a 256-byte boundary) for the copy, in page-locked memory
+// when it could be had (a copy from it needs no staging).  Kept for the life
+// of the process, for at most 8 (d, level).
+struct GridHost {
+  std::vector<int8_t> lev;
+  std::vector<int16_t> kidx;
+  size_t okidx = 0, bytes = 0;   // offsets from the start of the levels
+  std::vector<unsigned char> staging;
+  unsigned char* pinned = nullptr;
+  const unsigned char* data() const { return pinned ? pinned : staging.data(); }
+  GridHost() = default;
+  GridHost(const GridHost&) = delete;
+  GridHost& operator=(const GridHost&) = delete;
+  // (a build holds its entry until it has waited for its copy, so the last
+  // reference goes with no copy from these bytes in flight)
+  ~GridHost() {
+    if (pinned) cudaFreeHost(pinned);
+  }
+};
+
+static std::shared_ptr<const GridHost> grid_host(int d, int level) {
+  static std::mutex mu;
+  static auto* cache = new std::vector<std::pair<std::pair<int, int>, std::shared_ptr<const GridHost>>>();
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& e : *cache)
+      if (e.first == std::make_pair(d, level)) return e.second;
+  }
+  auto h = std::make_shared<GridHost>();
+  enumerate_nodes(d, level, h->lev, h->kidx);
+  const size_t nl = h->lev.size();
+  h->okidx = (nl + 255) & ~size_t(255);
+  h->bytes = h->okidx + h->kidx.size() * sizeof(int16_t);
+  h->staging.assign(h->bytes, 0);
+  std::memcpy(h->staging.data(), h->lev.data(), nl);
+  std::memcpy(h->staging.data() + h->okidx, h->kidx.data(), h->kidx.size() * sizeof(int16_t));
+  if (cudaHostAlloc(reinterpret_cast<void**>(&h->pinned), h->bytes, cudaHostAllocDefault) == cudaSuccess) {
+    std::memcpy(h->pinned, h->staging.data(), h->bytes);
+    h->staging.clear();
+    h->staging.shrink_to_fit();
+  } else {
+    h->pinned = nullptr;
+    (void)cudaGetLastError();
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& e : *cache)   // another thread made it meanwhile
+    if (e.first == std::make_pair(d, level)) return e.second;
+  if (cache->size() >= 8) cache->erase(cache->begin());
+  cache->emplace_back(std::make_pair(d, level), h);
+  return h;
 }
 
 }  // namespace sg
@@ -102,27 +165,26 @@ extern "C" int sg_build_grid(int d, int level, const double* h_lo, const double*
   for (int k = 0; k < d; ++k)
     if (!(h_lo[k] < h_hi[k])) return fail(SG_EINVAL, "sg_build_grid: need lo < hi in every dimension");
 
+  std::shared_ptr<const GridHost> hp;
+  try {
+    hp = grid_host(d, level);
+  } catch (const std::bad_alloc&) {
+    return fail(SG_ENOMEM, "sg_build_grid: host memory");
+  }
   auto* g = new sg_grid();
   g->d = d;
   g->level = level;
-  enumerate_nodes(d, level, g->h_lev, g->h_kidx);
+  g->h_lev = hp->lev;
+  g->h_kidx = hp->kidx;
   g->M = static_cast<int64_t>(g->h_lev.size()) / d;
   g->h_lo.assign(h_lo, h_lo + d);
   g->h_hi.assign(h_hi, h_hi + d);
   const int64_t total = g->M * d;
 
-  // one device allocation (coordinates, levels, indices, box); the host-made
-  // parts go in with one copy
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    const size_t o = off;
-    off += (bytes + 255) & ~size_t(255);
-    return o;
-  };
-  const size_t ocoords = take(total * sizeof(double));
-  const size_t ohost = off;
-  const size_t obox = take(2 * d * sizeof(double)), olev = take(total * sizeof(int8_t));
-  const size_t okidx = take(total * sizeof(int16_t));
+  // one device allocation: coordinates, then the levels and indices in the
+  // layout of the host-made bytes, which go in with one copy
+  const size_t olev = (total * sizeof(double) + 255) & ~size_t(255);
+  const size_t off = olev + hp->bytes;
   auto cleanup = [&](int code, const char* what, cudaError_t e) {
     sg_grid_free(g);
     return e == cudaSuccess ? fail(code, what) : cuda_fail(e, what);
@@ -130,23 +192,20 @@ extern "C" int sg_build_grid(int d, int level, const double* h_lo, const double*
   cudaError_t e;
   if ((e = block_alloc(&g->block, off, nullptr)) != cudaSuccess) return cleanup(SG_ENOMEM, "device allocation of the grid", e);
   char* base = static_cast<char*>(g->block);
-  g->coords = reinterpret_cast<double*>(base + ocoords);
+  g->coords = reinterpret_cast<double*>(base);
   g->lev = reinterpret_cast<int8_t*>(base + olev);
-  g->kidx = reinterpret_cast<int16_t*>(base + okidx);
-  double* d_box = reinterpret_cast<double*>(base + obox);
-  {
-    std::vector<unsigned char> h(off - ohost);
-    std::memcpy(h.data() + (obox - ohost), h_lo, d * sizeof(double));
-    std::memcpy(h.data() + (obox - ohost) + d * sizeof(double), h_hi, d * sizeof(double));
-    std::memcpy(h.data() + (olev - ohost), g->h_lev.data(), total * sizeof(int8_t));
-    std::memcpy(h.data() + (okidx - ohost), g->h_kidx.data(), total * sizeof(int16_t));
-    // (a copy from pageable memory is staged before the call returns, so h
-    // may go; the kernel follows it on the same stream, and one wait covers both)
-    if ((e = cudaMemcpyAsync(base + ohost, h.data(), off - ohost, cudaMemcpyHostToDevice, nullptr)) != cudaSuccess)
-      return cleanup(SG_ECUDA, "copy grid tables", e);
+  g->kidx = reinterpret_cast<int16_t*>(base + olev + hp->okidx);
+  if ((e = cudaMemcpyAsync(base + olev, hp->data(), hp->bytes, cudaMemcpyHostToDevice, nullptr)) != cudaSuccess)
+    return cleanup(SG_ECUDA, "copy grid tables", e);
+  GridBox box{};
+  for (int k = 0; k < d; ++k) {
+    box.lo[k] = h_lo[k];
+    box.hi[k] = h_hi[k];
   }
-  SG_TIMED("grid_coords_kernel", nullptr, (grid_coords_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256>>>(total, d, g->lev, g->kidx, d_box, d_box + d, g->coords)));
+  SG_TIMED("grid_coords_kernel", nullptr, (grid_coords_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256>>>(total, d, g->lev, g->kidx, box, g->coords)));
   if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(SG_ECUDA, "grid_coords_kernel launch", e);
+  // (the copy and the kernel are on the default stream; one wait covers both,
+  // and the host-made bytes are kept, so nothing on the host is freed early)
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup(SG_ECUDA, "grid_coords_kernel", e);
   *out = g;
   return SG_OK;
