@@ -225,7 +225,9 @@ def solve_bvps(problem: Problem, x0: torch.Tensor, T, N, *, tol=1e-8, max_iter=5
     iters); reusing them (and the workspace) lets graph=True replay one graph.
     graph: 0 host loop, 1 (or True) one cached graph, 2 one graph per mesh size.
     Y0 (n, 3 n_max + 1, 12) f64: warm start from this iterate; it is
-    overwritten with the final iterate (and returned as "Y")."""
+    overwritten with the final iterate (and returned as "Y").
+    With graph != 0 the call returns once the work is queued on `stream`
+    (default: the current stream): read the outputs in that stream's order."""
     x0 = _dev(x0, torch.float64).reshape(-1, 6)
     n = x0.shape[0]
     dev = x0.device
@@ -370,7 +372,9 @@ class SolverPool:
 
 # --------------------------------------------------------------- Step III
 class Surplus:
-    """sg_build_surpluses handle: hierarchical surpluses of values at the nodes."""
+    """sg_build_surpluses handle: hierarchical surpluses of values at the nodes.
+    The build is queued on `stream` (default: the current stream); use the
+    handle on another stream only after an event or a synchronisation."""
 
     def __init__(self, grid: Grid, values: torch.Tensor, stream=None):
         values = _dev(values, torch.float64).reshape(grid.M, -1)
